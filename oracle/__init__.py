@@ -1,0 +1,304 @@
+"""Textbook-BFV oracle (plain single-threaded C++), wrapped with ctypes.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  The CUDA library never calls it, and it never calls the CUDA library.
+
+The C++ source (``bfv_oracle.cpp``) restates the paper's equality predicate
+(Sec. 2.1.6, Eq. (equality): EQ(x, y) = 1 - (x - y)^(p-1)), computed by
+exponentiation by squaring (Sec. 3.3.1: ceil(log2(p-1)) = 16 multiplications for
+p = 65537), over textbook BFV with the parameters of Sec. 4.1 (N = 32768,
+log QP = 881, p = 65537).  Every function below states which operation it
+exposes; the arithmetic lives in the C++ file.
+
+Array conventions (numpy):
+  ciphertext  uint64 [2][L][N]  residues mod q_0..q_{L-1}, coefficient domain
+  relin key   uint64 [L][2][L+1][N]  residues mod q_0..q_{L-1}, P
+  secret key  int8 [N] in {-1, 0, 1}
+  slots       uint32 [N] values mod t
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bfv_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with g++ (no CUDA involved)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    V = ctypes.c_void_p
+    sig = {
+        "orc_default_primes": (ctypes.c_int, [ctypes.c_int, _u64p, _u64p]),
+        "orc_create": (V, [ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_uint64, ctypes.c_uint64]),
+        "orc_destroy": (None, [V]),
+        "orc_export_big": (ctypes.c_int, [V, ctypes.c_int, _u64p, ctypes.c_int]),
+        "orc_philox": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u32p]),
+        "orc_philox_raw": (None, [_u32p, _u32p, _u32p]),
+        "orc_ntt_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, _u64p]),
+        "orc_ntt_inverse": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, _u64p]),
+        "orc_polymul_small": (ctypes.c_int, [V, _i64p, _i64p, _i64p]),
+        "orc_encode": (ctypes.c_int, [V, _u32p, _u64p]),
+        "orc_decode": (ctypes.c_int, [V, _u64p, _u32p]),
+        "orc_keygen": (ctypes.c_int, [V, ctypes.c_uint64, _i8p, _u64p]),
+        "orc_encrypt": (ctypes.c_int, [V, _i8p, _u32p, ctypes.c_uint64, ctypes.c_uint32, _u64p]),
+        "orc_decrypt": (ctypes.c_int, [V, _i8p, _u64p, _u32p, ctypes.POINTER(ctypes.c_double)]),
+        "orc_sub": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
+        "orc_sub_const": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
+        "orc_one_minus": (ctypes.c_int, [V, _u64p, _u64p]),
+        "orc_mul_relin": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
+        "orc_eq": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_uint64, ctypes.c_int, _u64p]),
+        "orc_square_chain": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p]),
+        "orc_tensor_round": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
+        "orc_relin": (ctypes.c_int, [V, _u64p, _u64p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+T_DEFAULT = 65537
+L_DEFAULT = 15
+
+
+def default_primes(L: int = L_DEFAULT):
+    """Data primes q_0 > ... > q_{L-1} (largest below 2^55, = 1 mod 2^16) and the
+    special prime P (largest below 2^56, = 1 mod 2^16).  log2(Q P) ~ 881 for
+    L = 15 (paper Sec. 4.1)."""
+    lib = _load()
+    q = np.zeros(L, dtype=np.uint64)
+    P = np.zeros(1, dtype=np.uint64)
+    if lib.orc_default_primes(L, _p(q, ctypes.c_uint64), _p(P, ctypes.c_uint64)) != 0:
+        raise RuntimeError("prime search failed")
+    return [int(x) for x in q], int(P[0])
+
+
+def philox(seed: int, k: int, j: int, obj: int, dom: int):
+    """Philox4x32-10 output for counter (k, j, obj, dom), key = 64-bit seed."""
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox(seed, k, j, obj, dom, _p(out, ctypes.c_uint32))
+    return [int(x) for x in out]
+
+
+def philox_raw(ctr4, key2):
+    ctr = _c(ctr4, np.uint32)
+    key = _c(key2, np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox_raw(_p(ctr, ctypes.c_uint32), _p(key, ctypes.c_uint32), _p(out, ctypes.c_uint32))
+    return [int(x) for x in out]
+
+
+def ntt_forward(logn: int, m: int, a) -> np.ndarray:
+    """Negacyclic transform A_j = sum_k a_k psi^((2j+1)k) mod m (natural order)."""
+    x = _c(a, np.uint64).copy()
+    _load().orc_ntt_forward(logn, m, _p(x, ctypes.c_uint64))
+    return x
+
+
+def ntt_inverse(logn: int, m: int, a) -> np.ndarray:
+    x = _c(a, np.uint64).copy()
+    _load().orc_ntt_inverse(logn, m, _p(x, ctypes.c_uint64))
+    return x
+
+
+class Oracle:
+    """One BFV parameter set (ring degree 2^logn, data primes q, special prime P,
+    plaintext modulus t).  Holds the relinearisation key after keygen()."""
+
+    def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT):
+        if q is None:
+            q, P = default_primes(L)
+        self.lib = _load()
+        self.logn = logn
+        self.N = 1 << logn
+        self.q = [int(x) for x in q]
+        self.L = len(self.q)
+        self.P = int(P)
+        self.t = int(t)
+        qa = np.array(self.q, dtype=np.uint64)
+        self.h = self.lib.orc_create(logn, self.L, _p(qa, ctypes.c_uint64), self.P, self.t)
+        if not self.h:
+            raise RuntimeError("orc_create failed")
+        self.s = None
+        self.rk = None
+
+    def close(self):
+        if self.h:
+            self.lib.orc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- constants ---------------------------------------------------------
+    def export_big(self, which: int) -> int:
+        buf = np.zeros(40, dtype=np.uint64)
+        n = self.lib.orc_export_big(self.h, which, _p(buf, ctypes.c_uint64), 40)
+        return sum(int(buf[i]) << (64 * i) for i in range(n))
+
+    @property
+    def Q(self) -> int:
+        return self.export_big(0)
+
+    @property
+    def QP(self) -> int:
+        return self.export_big(1)
+
+    @property
+    def Delta(self) -> int:
+        return self.export_big(2)
+
+    # -- encoding ------------------------------------------------------------
+    def encode(self, slots) -> np.ndarray:
+        s = _c(slots, np.uint32)
+        m = np.zeros(self.N, dtype=np.uint64)
+        self.lib.orc_encode(self.h, _p(s, ctypes.c_uint32), _p(m, ctypes.c_uint64))
+        return m
+
+    def decode(self, m) -> np.ndarray:
+        mm = _c(m, np.uint64)
+        s = np.zeros(self.N, dtype=np.uint32)
+        self.lib.orc_decode(self.h, _p(mm, ctypes.c_uint64), _p(s, ctypes.c_uint32))
+        return s
+
+    def polymul_small(self, a, b) -> np.ndarray:
+        A = _c(a, np.int64)
+        B = _c(b, np.int64)
+        out = np.zeros(self.N, dtype=np.int64)
+        if self.lib.orc_polymul_small(self.h, _p(A, ctypes.c_int64), _p(B, ctypes.c_int64), _p(out, ctypes.c_int64)) != 0:
+            raise OverflowError("product does not fit int64")
+        return out
+
+    # -- keys and encryption ---------------------------------------------------
+    def keygen(self, seed: int):
+        """Secret key and relinearisation key from `seed` (stored for later ops)."""
+        s = np.zeros(self.N, dtype=np.int8)
+        rk = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
+        self.lib.orc_keygen(self.h, seed, _p(s, ctypes.c_int8), _p(rk, ctypes.c_uint64))
+        self.s, self.rk = s, rk
+        return s, rk
+
+    def encrypt(self, slots, seed: int, ct_index: int = 0, s=None) -> np.ndarray:
+        s = self.s if s is None else _c(s, np.int8)
+        sl = _c(slots, np.uint32)
+        ct = np.zeros((2, self.L, self.N), dtype=np.uint64)
+        self.lib.orc_encrypt(self.h, _p(s, ctypes.c_int8), _p(sl, ctypes.c_uint32), seed, ct_index, _p(ct, ctypes.c_uint64))
+        return ct
+
+    def decrypt(self, ct, s=None, with_noise: bool = False):
+        s = self.s if s is None else _c(s, np.int8)
+        c = _c(ct, np.uint64)
+        out = np.zeros(self.N, dtype=np.uint32)
+        nb = ctypes.c_double(0.0)
+        self.lib.orc_decrypt(self.h, _p(s, ctypes.c_int8), _p(c, ctypes.c_uint64), _p(out, ctypes.c_uint32), ctypes.byref(nb))
+        return (out, nb.value) if with_noise else out
+
+    # -- homomorphic operations --------------------------------------------------
+    def _ct_out(self, shape=None):
+        return np.zeros(shape or (2, self.L, self.N), dtype=np.uint64)
+
+    def sub(self, x, y):
+        X, Y, out = _c(x, np.uint64), _c(y, np.uint64), self._ct_out()
+        self.lib.orc_sub(self.h, _p(X, ctypes.c_uint64), _p(Y, ctypes.c_uint64), _p(out, ctypes.c_uint64))
+        return out
+
+    def sub_const(self, x, v: int):
+        X, out = _c(x, np.uint64), self._ct_out()
+        self.lib.orc_sub_const(self.h, _p(X, ctypes.c_uint64), v, _p(out, ctypes.c_uint64))
+        return out
+
+    def one_minus(self, x):
+        X, out = _c(x, np.uint64), self._ct_out()
+        self.lib.orc_one_minus(self.h, _p(X, ctypes.c_uint64), _p(out, ctypes.c_uint64))
+        return out
+
+    def mul_relin(self, a, b):
+        A, B, out = _c(a, np.uint64), _c(b, np.uint64), self._ct_out()
+        if self.lib.orc_mul_relin(self.h, _p(A, ctypes.c_uint64), _p(B, ctypes.c_uint64), _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("relinearisation key not set")
+        return out
+
+    def eq(self, x, y=None, const_val: int = 0, squarings: int = 16):
+        """EQ(x, y) = 1 - (x - y)^(2^squarings); y None => compare with const_val."""
+        X, out = _c(x, np.uint64), self._ct_out()
+        yp = None
+        if y is not None:
+            Y = _c(y, np.uint64)
+            yp = _p(Y, ctypes.c_uint64)
+        if self.lib.orc_eq(self.h, _p(X, ctypes.c_uint64), yp, const_val, squarings, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("relinearisation key not set")
+        return out
+
+    def square_chain(self, x, squarings: int):
+        X, out = _c(x, np.uint64), self._ct_out()
+        if self.lib.orc_square_chain(self.h, _p(X, ctypes.c_uint64), squarings, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("relinearisation key not set")
+        return out
+
+    def tensor_round(self, a, b):
+        """round(t d_j / Q) mod Q for the tensor (d0, d1, d2) of a and b."""
+        A, B = _c(a, np.uint64), _c(b, np.uint64)
+        out = np.zeros((3, self.L, self.N), dtype=np.uint64)
+        self.lib.orc_tensor_round(self.h, _p(A, ctypes.c_uint64), _p(B, ctypes.c_uint64), _p(out, ctypes.c_uint64))
+        return out
+
+    def relin(self, d3):
+        D, out = _c(d3, np.uint64), self._ct_out()
+        if self.lib.orc_relin(self.h, _p(D, ctypes.c_uint64), _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("relinearisation key not set")
+        return out
+
+
+def crt_to_int(residues, moduli) -> int:
+    """Plain CRT of one coefficient (Python integers) — a helper for tests."""
+    M = 1
+    for m in moduli:
+        M *= m
+    x = 0
+    for r, m in zip(residues, moduli):
+        Mi = M // m
+        x += int(r) * Mi * pow(Mi, -1, m)
+    return x % M

@@ -1,0 +1,350 @@
+"""Pins of the textbook-BFV oracle to things other than itself (CPU only).
+
+Each test names what fixes the expected value: a published known-answer
+vector, a closed form from the paper, a number-theoretic invariant, or a
+brute-force computation on tiny inputs with Python's own big integers and a
+schoolbook negacyclic product (a different algorithm from the oracle's
+multi-modular transform + CRT).
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy
+
+import oracle
+from tests.conftest import golden_path, read_golden_kv
+
+T = 65537
+
+
+# --------------------------------------------------------------------------
+# helpers: plain Python big-integer reference pieces for tiny N
+# --------------------------------------------------------------------------
+def negacyclic_schoolbook(a, b, N):
+    r = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                r[k] += a[i] * b[j]
+            else:
+                r[k - N] -= a[i] * b[j]
+    return r
+
+
+def to_ints(res, moduli):
+    """residues [len(moduli)][N] -> list of integers in [0, prod)"""
+    N = res.shape[-1]
+    return [oracle.crt_to_int([int(res[i][j]) for i in range(len(moduli))], moduli) for j in range(N)]
+
+
+def brv(x, bits):
+    return int(format(x, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# --------------------------------------------------------------------------
+def test_philox_known_answer_vectors():
+    rows = []
+    with open(golden_path("philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert oracle.philox_raw(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_philox_draw_uses_seed_as_key_and_counter_fields():
+    seed = 0x0123456789ABCDEF
+    w = oracle.philox(seed, 5, 6, 7, 8)
+    assert w == oracle.philox_raw([5, 6, 7, 8], [seed & 0xFFFFFFFF, seed >> 32])
+
+
+# --------------------------------------------------------------------------
+# parameters (Sec. 4.1)
+# --------------------------------------------------------------------------
+def test_default_primes_match_their_definition_and_the_paper():
+    q, P = oracle.default_primes(15)
+    assert len(q) == 15 and len(set(q)) == 15
+    step = 1 << 16
+    for x in q:
+        assert sympy.isprime(x) and x < 2**55 and x % step == 1
+    assert sympy.isprime(P) and P < 2**56 and P % step == 1 and P >= 2**55
+    assert q == sorted(q, reverse=True)
+    # "largest": every skipped candidate k*2^16 + 1 between q_14 and 2^55 is composite
+    cands = [k * step + 1 for k in range(q[-1] // step, (2**55 - 2) // step + 1)]
+    primes_found = [c for c in cands if sympy.isprime(c)]
+    assert primes_found == sorted(q)
+    cands_P = [k * step + 1 for k in range(P // step, (2**56 - 2) // step + 1)]
+    assert [c for c in cands_P if sympy.isprime(c)] == [P]
+    g = read_golden_kv("paper_parameters.txt")
+    logqp = sum(math.log2(x) for x in q) + math.log2(P)
+    assert round(logqp) == g["log2_QP"]
+    # every prime supports the negacyclic transform of the paper's ring degree
+    for x in q + [P]:
+        assert (x - 1) % (2 * g["ring_degree"]) == 0
+    assert (g["plaintext_modulus"] - 1) % (2 * g["ring_degree"]) == 0
+    # ciphertext size: 2 polynomials x 15 limbs x N words of 8 bytes ~ the paper's 7.4 MB
+    size_mb = 2 * 15 * g["ring_degree"] * 8 / 2**20
+    assert abs(size_mb - g["ciphertext_megabytes"]) / g["ciphertext_megabytes"] < 0.05
+
+
+def test_oracle_constants(orc16):
+    o = orc16
+    Q = math.prod(o.q)
+    assert o.Q == Q
+    assert o.QP == Q * o.P
+    assert o.Delta == Q // T
+    assert Q % 2 == 1 and math.gcd(Q, T) == 1  # no rounding ties (t d / Q never half-integral)
+
+
+# --------------------------------------------------------------------------
+# the method's arithmetic fact: 16 squarings give the Fermat exponent
+# --------------------------------------------------------------------------
+def test_fermat_sixteen_squarings_exhaustive():
+    g = read_golden_kv("paper_parameters.txt")
+    p = g["plaintext_modulus"]
+    assert math.ceil(math.log2(p - 1)) == g["eq_multiplications"]
+    a = np.arange(p, dtype=np.int64)
+    for _ in range(g["eq_multiplications"]):
+        a = (a * a) % p
+    assert a[0] == 0 and np.all(a[1:] == 1)  # a^(p-1) = [a != 0]
+
+
+# --------------------------------------------------------------------------
+# negacyclic transform
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("logn", [3, 4, 6])
+def test_ntt_product_matches_schoolbook(logn):
+    N = 1 << logn
+    m = 2305843009213554689  # a 61-bit prime = 1 mod 2^17 (checked below)
+    assert sympy.isprime(m) and (m - 1) % (2 * N) == 0
+    rng = np.random.default_rng(logn)
+    a = [int(x) for x in rng.integers(0, m, N, dtype=np.uint64)]
+    b = [int(x) for x in rng.integers(0, m, N, dtype=np.uint64)]
+    A = oracle.ntt_forward(logn, m, a)
+    B = oracle.ntt_forward(logn, m, b)
+    C = [(int(x) * int(y)) % m for x, y in zip(A, B)]
+    c = oracle.ntt_inverse(logn, m, C)
+    ref = [v % m for v in negacyclic_schoolbook(a, b, N)]
+    assert [int(x) for x in c] == ref
+    assert [int(x) for x in oracle.ntt_inverse(logn, m, A)] == a
+
+
+def test_ntt_is_evaluation_at_odd_powers():
+    logn, N, m = 3, 8, 65537
+    g = 3  # smallest quadratic non-residue mod 65537
+    assert pow(2, (m - 1) // 2, m) == 1 and pow(3, (m - 1) // 2, m) == m - 1
+    psi = pow(g, (m - 1) // (2 * N), m)
+    a = list(range(1, N + 1))
+    A = oracle.ntt_forward(logn, m, a)
+    for j in range(N):
+        assert int(A[j]) == sum(a[k] * pow(psi, (2 * j + 1) * k, m) for k in range(N)) % m
+
+
+# --------------------------------------------------------------------------
+# batch encoding (slots <-> plaintext polynomial mod t)
+# --------------------------------------------------------------------------
+def test_encoding_closed_forms(orc16):
+    o = orc16
+    N = o.N
+    ones = np.ones(N, dtype=np.uint32)
+    m = o.encode(ones)
+    assert int(m[0]) == 1 and not np.any(m[1:])  # all-ones slots = constant polynomial 1
+    c = np.full(N, 4242, dtype=np.uint32)
+    m = o.encode(c)
+    assert int(m[0]) == 4242 and not np.any(m[1:])
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, T, N).astype(np.uint32)
+    assert np.array_equal(o.decode(o.encode(x)), x)
+    # slot j is the evaluation at psi^(2 brv(j) + 1), psi = 3^((t-1)/2N)
+    psi = pow(3, (T - 1) // (2 * N), T)
+    mm = [int(v) for v in o.encode(x)]
+    for j in range(N):
+        e = 2 * brv(j, o.logn) + 1
+        assert sum(mm[k] * pow(psi, e * k, T) for k in range(N)) % T == int(x[j])
+    # ring homomorphism: slot-wise product <-> negacyclic product mod t
+    y = rng.integers(0, T, N).astype(np.uint32)
+    prod = [v % T for v in negacyclic_schoolbook([int(v) for v in o.encode(x)], [int(v) for v in o.encode(y)], N)]
+    assert np.array_equal(o.decode(np.array(prod, dtype=np.uint64)), (x.astype(np.int64) * y % T).astype(np.uint32))
+
+
+# --------------------------------------------------------------------------
+# keys, encryption, decryption
+# --------------------------------------------------------------------------
+def test_keygen_relation_bruteforce(orc16):
+    o = orc16
+    N, L, P = o.N, o.L, o.P
+    s, rk = o.s, o.rk
+    assert set(np.unique(s)).issubset({-1, 0, 1})
+    Q = math.prod(o.q)
+    QP = Q * P
+    sl = [int(v) for v in s]
+    s2 = negacyclic_schoolbook(sl, sl, N)
+    for i in range(L):
+        rk0 = to_ints(rk[i][0], o.q + [P])
+        rk1 = to_ints(rk[i][1], o.q + [P])
+        qh = Q // o.q[i]
+        g_i = qh * pow(qh, -1, o.q[i])
+        lhs = [(a + b) % QP for a, b in zip(rk0, negacyclic_schoolbook(rk1, sl, N))]
+        err = [(v - P * g_i * w) % QP for v, w in zip(lhs, s2)]
+        err = [e - QP if e > QP // 2 else e for e in err]
+        assert max(abs(e) for e in err) <= 21  # centred binomial, eta = 21
+
+
+def test_encrypt_relation_bruteforce(orc16):
+    o = orc16
+    N = o.N
+    Q = math.prod(o.q)
+    x = np.arange(N, dtype=np.uint32) * 977 % T
+    ct = o.encrypt(x, seed=99, ct_index=3)
+    c0, c1 = to_ints(ct[0], o.q), to_ints(ct[1], o.q)
+    sl = [int(v) for v in o.s]
+    m = [int(v) for v in o.encode(x)]
+    ph = [(a + b) % Q for a, b in zip(c0, negacyclic_schoolbook(c1, sl, N))]
+    err = [(v - (Q // T) * mm) % Q for v, mm in zip(ph, m)]
+    err = [e - Q if e > Q // 2 else e for e in err]
+    assert max(abs(e) for e in err) <= 21
+    assert np.array_equal(o.decrypt(ct), x)
+    # different ciphertext index -> different randomness, same plaintext
+    ct2 = o.encrypt(x, seed=99, ct_index=4)
+    assert not np.array_equal(ct, ct2) and np.array_equal(o.decrypt(ct2), x)
+
+
+# --------------------------------------------------------------------------
+# textbook multiplication and relinearisation: brute force on N = 16
+# --------------------------------------------------------------------------
+def _centered(v, Q):
+    return v - Q if v > (Q - 1) // 2 else v
+
+
+def test_tensor_and_rounding_bruteforce(orc16):
+    o = orc16
+    N, Q = o.N, math.prod(o.q)
+    rng = np.random.default_rng(5)
+    a = o.encrypt(rng.integers(0, T, N).astype(np.uint32), seed=1, ct_index=0)
+    b = o.encrypt(rng.integers(0, T, N).astype(np.uint32), seed=1, ct_index=1)
+    # also an adversarial pair: coefficients at the centring boundary (Q +- 1)/2
+    edge = np.zeros_like(a)
+    for i, qi in enumerate(o.q):
+        edge[0, i, :] = ((Q - 1) // 2) % qi
+        edge[1, i, :] = ((Q + 1) // 2) % qi
+    for (x, y) in [(a, b), (a, a), (edge, a), (edge, edge)]:
+        got = o.tensor_round(x, y)
+        A0 = [_centered(v, Q) for v in to_ints(x[0], o.q)]
+        A1 = [_centered(v, Q) for v in to_ints(x[1], o.q)]
+        B0 = [_centered(v, Q) for v in to_ints(y[0], o.q)]
+        B1 = [_centered(v, Q) for v in to_ints(y[1], o.q)]
+        d = [negacyclic_schoolbook(A0, B0, N),
+             [u + v for u, v in zip(negacyclic_schoolbook(A0, B1, N), negacyclic_schoolbook(A1, B0, N))],
+             negacyclic_schoolbook(A1, B1, N)]
+        for k in range(3):
+            # round(t d / Q) with exact rationals (no ties: Q odd, gcd(Q, t) = 1)
+            ref = []
+            for v in d[k]:
+                n2, den = 2 * T * v + Q, 2 * Q
+                ref.append((n2 // den) % Q)
+            assert to_ints(got[k], o.q) == ref
+
+
+def test_relinearisation_bruteforce(orc16):
+    o = orc16
+    N, L, P = o.N, o.L, o.P
+    Q = math.prod(o.q)
+    QP = Q * P
+    rng = np.random.default_rng(6)
+    d3 = np.stack([np.stack([rng.integers(0, qi, N, dtype=np.uint64) for qi in o.q]) for _ in range(3)])
+    got = o.relin(d3)
+    D = [to_ints(d3[k], o.q) for k in range(3)]
+    RK = [[to_ints(o.rk[i][c], o.q + [P]) for c in range(2)] for i in range(L)]
+    out = []
+    for c in range(2):
+        u = [0] * N
+        for i in range(L):
+            dig = [v % o.q[i] for v in D[2]]
+            u = [x + y for x, y in zip(u, negacyclic_schoolbook(dig, RK[i][c], N))]
+        u = [v % QP for v in u]
+        ks = []
+        for v in u:
+            r = v % P
+            r = r - P if r > (P - 1) // 2 else r
+            assert (v - r) % P == 0
+            ks.append((v - r) // P)
+        out.append([(a + b) % Q for a, b in zip(D[c], ks)])
+    assert to_ints(got[0], o.q) == out[0]
+    assert to_ints(got[1], o.q) == out[1]
+
+
+def test_homomorphic_product_closed_form(orc16):
+    o = orc16
+    rng = np.random.default_rng(8)
+    x = rng.integers(0, T, o.N).astype(np.uint32)
+    y = rng.integers(0, T, o.N).astype(np.uint32)
+    cx, cy = o.encrypt(x, 3, 0), o.encrypt(y, 3, 1)
+    got, nb = o.decrypt(o.mul_relin(cx, cy), with_noise=True)
+    assert np.array_equal(got, (x.astype(np.int64) * y % T).astype(np.uint32))
+    assert nb > 700
+
+
+# --------------------------------------------------------------------------
+# EQ (Eq. equality) against the closed form [x == y]
+# --------------------------------------------------------------------------
+def _edge_pairs(N, rng):
+    x = rng.integers(0, 2**16, N).astype(np.int64)
+    y = np.where(rng.random(N) < 0.5, x, rng.integers(0, 2**16, N))
+    cases = [(5, 5), (0, 0), (T - 1, T - 1), (6, 5), (5, 6), (0, T - 1), (T - 1, 0),
+             ((T - 1) // 2, 0), (0, (T - 1) // 2), ((T + 1) // 2, 0), (1, 0), (0, 1), (65535, 65536)]
+    for i, (a, b) in enumerate(cases):
+        x[i], y[i] = a, b
+    return x.astype(np.uint32), y.astype(np.uint32)
+
+
+def test_eq_closed_form_n4096(orc4096):
+    o = orc4096
+    rng = np.random.default_rng(0)
+    x, y = _edge_pairs(o.N, rng)
+    cx, cy = o.encrypt(x, 10, 0), o.encrypt(y, 10, 1)
+    ce = o.eq(cx, cy)
+    got, nb = o.decrypt(ce, with_noise=True)
+    assert np.array_equal(got, (x == y).astype(np.uint32))
+    assert nb > 100  # 16 squarings stay well inside the budget (no bootstrapping)
+
+
+def test_eq_const_closed_form(orc16):
+    o = orc16
+    x = np.array([7, 8, 7, 0, T - 1, 7, 6, 7] * (o.N // 8), dtype=np.uint32)
+    cx = o.encrypt(x, 10, 0)
+    got = o.decrypt(o.eq(cx, None, const_val=7))
+    assert np.array_equal(got, (x == 7).astype(np.uint32))
+
+
+def test_eq_depth_is_sixteen(orc16):
+    """Fewer squarings do not give the predicate: (x - y)^(2^k) for k < 16."""
+    o = orc16
+    x = np.full(o.N, 3, dtype=np.uint32)
+    y = np.full(o.N, 1, dtype=np.uint32)
+    cx, cy = o.encrypt(x, 4, 0), o.encrypt(y, 4, 1)
+    got = o.decrypt(o.eq(cx, cy, squarings=4))
+    assert np.all(got == (1 - pow(2, 16, T)) % T)
+    got = o.decrypt(o.eq(cx, cy, squarings=16))
+    assert np.all(got == 0)
+
+
+def test_depth_overflow_decrypts_wrongly():
+    """With a 3-prime modulus the noise budget runs out after a few squarings and
+    decryption stops matching the plaintext closed form (leveled HE, Sec. 2.1.2)."""
+    q, P = oracle.default_primes(15)
+    o = oracle.Oracle(4, q=q[:3], P=P)
+    o.keygen(3)
+    x = np.arange(o.N, dtype=np.uint32) + 2
+    cx = o.encrypt(x, 5, 0)
+    ok_at = {}
+    for k in [1, 2, 8]:
+        got, nb = o.decrypt(o.square_chain(cx, k), with_noise=True)
+        ok_at[k] = np.array_equal(got, np.array([pow(int(v), 2**k, T) for v in x], dtype=np.uint32))
+    assert ok_at[1] and ok_at[2]
+    assert not ok_at[8]
