@@ -1,0 +1,180 @@
+/* libhp — the NSHEDB equality predicate over BFV-packed columns on one GPU.
+ *
+ * Paper: "NSHEDB: Noise-Sensitive Homomorphic Encrypted Database Query Engine"
+ * (arXiv 2602.24271).  The operation is the equality predicate of Sec. 2.1.6,
+ * Eq. (equality):  EQ(x, y) = 1 - (x - y)^(p-1), evaluated slot-wise on BFV
+ * ciphertexts that pack N column values each (Sec. 3.1), with p = 65537 so that
+ * exponentiation by squaring (Sec. 3.3.1, Table 3: ceil(log(p-1)) = 16
+ * multiplications) is 16 ciphertext squarings, each relinearised.
+ *
+ * Scheme and parameters (paper Sec. 4.1: N = 32768, log QP = 881, p = 65537):
+ *   ring            Z_Q[X] / (X^N + 1), N = 2^log_n, 12 <= log_n <= 15
+ *   data modulus    Q = q_0 ... q_{L-1}, L = 15, q_i prime < 2^55, q_i = 1 mod 2^16
+ *   special prime   P < 2^56, P = 1 mod 2^16 (relinearisation only)
+ *   plaintext       t = p = 65537
+ *   multiplication  textbook Fan-Vercauteren: centred lift, exact tensor,
+ *                   round(t d / Q) mod Q; relinearisation with per-prime digits
+ *                   [d2]_{q_i} and the special prime P.  Results are bit-exact
+ *                   against that integer definition.
+ *
+ * Memory layouts (all words uint64, residues canonical in [0, prime)):
+ *   ciphertext      [2][L][N]        (c0, c1) residues mod q_0..q_{L-1},
+ *                                    coefficient domain; n ciphertexts are
+ *                                    contiguous: [n][2][L][N]
+ *   relin key       [L][2][L+1][N]   rk_i = (rk_i0, rk_i1), residues mod
+ *                                    q_0..q_{L-1}, P; coefficient domain
+ *   secret key      int8 [N]         coefficients in {-1, 0, 1}
+ *   slots           uint32 [N]       plaintext slot values mod t
+ *
+ * Pointers: "device" arguments must be CUDA device (or managed) memory.  The
+ * ciphertext arguments of hp_run may instead be host memory (pageable or
+ * pinned); the library then streams them through device staging buffers and
+ * returns after the last result is back in host memory.
+ *
+ * Streams: every call is ordered on the caller's `stream` (a cudaStream_t
+ * passed as void*, NULL = legacy default stream).  Device-pointer calls are
+ * asynchronous and return before the GPU finishes.
+ *
+ * Errors: 0 = success, negative = HP_ERR_*; hp_last_error(h) returns a
+ * description of the last failure on that handle.  On error the output
+ * buffers are unspecified.
+ *
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef LIBHP_HP_H
+#define LIBHP_HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HP_OK 0
+#define HP_ERR_ARG (-1)         /* bad argument: null pointer, size, range, alignment */
+#define HP_ERR_DEPTH (-2)       /* parameters cannot evaluate the requested depth */
+#define HP_ERR_OOM (-3)         /* device allocation failed */
+#define HP_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define HP_ERR_TIMEOUT (-5)     /* a bounded device wait expired */
+#define HP_ERR_UNSUPPORTED (-6) /* operation or parameter set not supported */
+#define HP_ERR_STATE (-7)       /* handle not ready (e.g. no relinearisation key) */
+
+typedef struct hp_handle hp_handle;
+
+/* Scheme parameters.  q points to L host words. */
+typedef struct {
+  uint32_t log_n;     /* ring degree N = 2^log_n, 12..15 */
+  uint32_t L;         /* number of data primes, must be 15 */
+  const uint64_t* q;  /* data primes q_0 > q_1 > ... > q_{L-1} */
+  uint64_t P;         /* special prime */
+  uint64_t t;         /* plaintext modulus, must be 65537 */
+  uint32_t max_depth; /* multiplicative depth the caller needs (16 for EQ, 17 with SELECT) */
+} hp_params;
+
+/* Operations of hp_run / hp_run_batched. */
+typedef enum {
+  HP_EQ_CT_CT = 0,    /* EQ(x, y) = 1 - (x - y)^(p-1), Eq. (equality) */
+  HP_EQ_CT_CONST = 1, /* EQ(x, c) with c broadcast to every slot */
+  HP_SELECT = 2,      /* y * EQ(x, c): the SELECT tail of Eq. (select); ct_y is the column */
+  HP_SQUARE = 3       /* one squaring + relinearisation (building block, for tests) */
+} hp_op;
+
+/* Fill q_out[0..L) and *P_out with the default primes (largest primes below
+ * 2^55, resp. 2^56, congruent to 1 mod 2^16) and *t_out = 65537.
+ * Returns HP_ERR_ARG for L outside 1..15 or null pointers. */
+int hp_default_params(uint32_t L, uint64_t* q_out, uint64_t* P_out, uint64_t* t_out);
+
+/* Create a handle for `params` on the current CUDA device.  Validates the
+ * parameters (primality, congruences, sizes) and the static depth estimate
+ * (HP_ERR_DEPTH if max_depth exceeds what the modulus supports).
+ * `max_tile_ct` bounds how many ciphertexts are processed per pipeline tile
+ * (0 = library default); device workspace grows linearly with it (about
+ * 130 MB per ciphertext at N = 32768).  `relin_key` may be NULL (set it later
+ * with hp_set_relin_key); otherwise it is a device pointer with the layout
+ * above.  On success *out owns all device memory it allocated. */
+int hp_create(const hp_params* params, const uint64_t* relin_key, size_t max_tile_ct, hp_handle** out);
+
+/* Load (replace) the relinearisation key from device memory (layout above).
+ * The handle keeps its own transformed copy; the caller keeps ownership of
+ * `relin_key_dev`.  Synchronous with respect to the host. */
+int hp_set_relin_key(hp_handle* h, const uint64_t* relin_key_dev);
+
+/* Evaluate `op` on n_ct ciphertexts.
+ *   HP_EQ_CT_CT    out[i] = EQ(x[i], y[i])
+ *   HP_EQ_CT_CONST out[i] = EQ(x[i], const_val)           (y ignored, may be NULL)
+ *   HP_SELECT      out[i] = y[i] * EQ(x[i], const_val)    (depth 17)
+ *   HP_SQUARE      out[i] = relin(x[i]^2)                  (y ignored)
+ * ct_x, ct_y, ct_out: [n_ct][2][L][N]; all device memory, or all host memory
+ * (then the call is synchronous).  ct_out may alias ct_x or ct_y.  n_ct = 0
+ * is a no-op.  const_val must be < t.  Requires the relinearisation key. */
+int hp_run(hp_handle* h, int op, const uint64_t* ct_x, const uint64_t* ct_y, uint64_t const_val, uint64_t* ct_out,
+           size_t n_ct, void* stream);
+
+/* One instance of a batched call: its ciphertexts ct_offset .. ct_offset+n_ct-1
+ * of the batch arrays, of which the first n_slots slots are meaningful, and the
+ * instance's constant (HP_EQ_CT_CONST).  Instances may share a ciphertext when
+ * they are slot-packed: then slot_offset gives the first slot of the instance
+ * inside ciphertext ct_offset and n_ct must be 1. */
+typedef struct {
+  uint64_t ct_offset;
+  uint32_t n_ct;
+  uint32_t slot_offset;
+  uint32_t n_slots;
+  uint32_t reserved;
+  uint64_t const_val;
+} hp_instance;
+
+/* Evaluate `op` (HP_EQ_CT_CT or HP_EQ_CT_CONST) for n_inst instances of
+ * uneven size in one pipelined, CUDA-graph-replayed pass over the union of
+ * their ciphertexts.  `inst` is host memory; ct_x / ct_y / ct_out are device
+ * arrays of n_ct_total ciphertexts.  For HP_EQ_CT_CONST with slot-packed
+ * instances each instance's constant applies to its own slot range only.
+ * Every ciphertext index must be covered by exactly one instance (or by
+ * several slot-packed ones whose ranges do not overlap). */
+int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst, const uint64_t* ct_x,
+                   const uint64_t* ct_y, uint64_t* ct_out, size_t n_ct_total, void* stream);
+
+/* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
+ * derivative, so this always returns HP_ERR_UNSUPPORTED. */
+int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream);
+
+/* Free the handle and its device memory (after synchronising its work). */
+void hp_destroy(hp_handle* h);
+
+/* Description of the last error on h (or of the last hp_create failure when
+ * h is NULL).  Valid until the next call on the same handle. */
+const char* hp_last_error(const hp_handle* h);
+
+/* ---- client-side helpers (tests, benchmark input generation) -------------
+ * These take the secret key explicitly; the handle never stores it.  All
+ * pointers are device memory; calls are stream-ordered. */
+
+/* Secret key s (int8 [N]) and relinearisation key (layout above), drawn with
+ * Philox4x32-10 keyed by `seed` (see DESIGN: sampling).  Also loads the key
+ * into the handle. */
+int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk_out, uint64_t* relin_key_out, void* stream);
+
+/* Encrypt n_ct slot vectors (uint32 [n_ct][N], values < t): ciphertext i uses
+ * Philox object index ct_index0 + i.  ct = (-(a s + e) + Delta m, a). */
+int hp_encrypt(hp_handle* h, const int8_t* sk, const uint32_t* slots, size_t n_ct, uint64_t seed, uint32_t ct_index0,
+               uint64_t* ct_out, void* stream);
+
+/* Decrypt n_ct ciphertexts: m = round(t [c0 + c1 s]_Q / Q) mod t, then
+ * decode to slots (uint32 [n_ct][N]). */
+int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, uint32_t* slots_out, void* stream);
+
+/* Number of kernel launches issued by the last hp_run / hp_run_batched call on
+ * h (for launch accounting). */
+uint64_t hp_launch_count(const hp_handle* h);
+
+/* Synchronise the device and report the exactness status word of h (a
+ * window check inside the exact base conversions that cannot fail for valid
+ * parameters); HP_OK if clean.  The word is cleared afterwards. */
+int hp_check_status(hp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBHP_HP_H */

@@ -1,0 +1,78 @@
+// Shared definitions of libhp (host and device): RNS bases and the constant
+// block that the kernels read from __constant__ memory.
+//
+// Prime ids (one numbering for every table):
+//   0 .. L-1        data primes q_i            (Q = prod q_i)
+//   L .. L+K-1      auxiliary primes b_k       (B = prod b_k), exact tensor base
+//   L+K             special prime P            (relinearisation)
+//   L+K+1           plaintext modulus t = 65537
+#pragma once
+#include <stdint.h>
+
+namespace hp {
+
+constexpr int L = 15;              // data primes (paper Sec. 4.1: log QP = 881 with P)
+constexpr int K = 16;              // auxiliary base: B > t N Q covers |round(t d / Q)| < B / 2
+constexpr int NQB = L + K;         // primes of the extended base Q u B
+constexpr int ID_P = L + K;        // 31
+constexpr int ID_T = L + K + 1;    // 32
+constexpr int NPRIME = L + K + 2;  // 33
+constexpr int NKS = L + 1;         // key-switching targets: q_0..q_{L-1}, P
+constexpr int LOGN_MIN = 12, LOGN_MAX = 15;
+
+// Constants for the exact RNS base conversions, relinearisation and the
+// client-side helpers.  All residues are canonical; "(s)" entries are the
+// Shoup companions floor(w 2^64 / p) of the preceding constant.
+struct Consts {
+  uint64_t p[NPRIME];     // moduli by id
+  uint64_t pinv[NPRIME];  // -p^{-1} mod 2^64 (Montgomery)
+  uint64_t r2[NPRIME];    // 2^128 mod p (to enter Montgomery form)
+  // exact centred conversion Q -> B
+  uint64_t qhatinv[L], qhatinv_s[L];  // [(Q/q_i)^{-1}]_{q_i}
+  uint64_t qhat[L], qhat_s[L];        // [Q/q_i]_{q_i} (rebuilds residues from y_i in the fallback)
+  uint64_t om_hi[L], om_lo[L];        // floor(2^128 / q_i) split in 64-bit halves
+  uint64_t MQB[L][K];                 // [(Q/q_i) 2^64]_{b_k}
+  uint64_t negQB[K];                  // [-Q 2^64]_{b_k}
+  uint64_t QmodB[K];                  // [Q]_{b_k}
+  // exact centred conversion B -> Q
+  uint64_t QBinv[K], QBinv_s[K];  // [Q^{-1} (B/b_k)^{-1}]_{b_k}
+  uint64_t omb_hi[K], omb_lo[K];  // floor(2^128 / b_k)
+  uint64_t MBQ[K][L];             // [(B/b_k) 2^64]_{q_i}
+  uint64_t negBQ[L];              // [-B 2^64]_{q_i}
+  // mixed-radix (Garner) comparison with (Q-1)/2, the exact fallback
+  uint64_t mrc_inv[L][L], mrc_inv_s[L][L];  // [q_j^{-1}]_{q_i} for j < i
+  uint64_t half_digit[L];                   // mixed-radix digits of (Q-1)/2
+  // relinearisation mod-down
+  uint64_t Pinv[L], Pinv_s[L];  // [P^{-1}]_{q_i}
+  // plaintext side
+  uint64_t delta[L], delta_s[L];          // [floor(Q/t)]_{q_i}
+  uint64_t tqhatinv[L], tqhatinv_s[L];    // [t (Q/q_i)^{-1}]_{q_i}   (decryption)
+  uint64_t MQt[L];                        // [(Q/q_i) 2^64]_t
+  uint64_t negQt;                         // [-Q 2^64]_t
+  uint64_t Qinv_t;                        // [Q^{-1}]_t
+  uint64_t Pmodq[L];                      // [P]_{q_i}   (key generation)
+};
+
+// Host side: build the constant block for (q, P, t) with the auxiliary primes
+// chosen by the library.  Returns 0 on success, negative HP_ERR_* otherwise.
+int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* out, char* err, int errlen);
+
+// Largest `count` primes below 2^bits with p = 1 mod 2^16, descending, skipping
+// the values in `exclude`.  Returns the number found.
+int find_primes(int bits, int count, const uint64_t* exclude, int nexclude, uint64_t* out);
+bool is_prime(uint64_t n);
+
+// Smallest g with g^((p-1)/2) = -1 mod p; psi = g^((p-1)/2N) is then a
+// primitive 2N-th root of unity.
+uint64_t h_qnr(uint64_t p);
+uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t m);
+uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);
+uint64_t h_invmod(uint64_t a, uint64_t m);
+uint64_t h_shoup(uint64_t w, uint64_t p);
+
+// Static noise estimate: how many successive squarings (each relinearised)
+// the parameters support with a positive invariant-noise budget, from the
+// standard heuristic growth bound (see DESIGN).  Used by hp_create.
+int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t);
+
+}  // namespace hp

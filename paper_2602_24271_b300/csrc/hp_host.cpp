@@ -1,0 +1,229 @@
+// Host-side parameter logic of libhp: prime search, the constant block for the
+// exact RNS conversions, and the static depth estimate.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "hp_defs.h"
+
+namespace hp {
+
+typedef unsigned __int128 u128;
+
+uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)(((u128)a * b) % m); }
+
+uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t m) {
+  uint64_t r = 1 % m, x = a % m;
+  for (; e; e >>= 1) {
+    if (e & 1) r = h_mulmod(r, x, m);
+    x = h_mulmod(x, x, m);
+  }
+  return r;
+}
+
+uint64_t h_invmod(uint64_t a, uint64_t m) { return h_powmod(a, m - 2, m); }
+
+uint64_t h_shoup(uint64_t w, uint64_t p) { return (uint64_t)(((u128)w << 64) / p); }
+
+// Miller-Rabin with the seven bases of Jaeschke/Sinclair, deterministic below 2^64.
+bool is_prime(uint64_t n) {
+  if (n < 4) return n >= 2;
+  if (n % 2 == 0 || n % 3 == 0) return false;
+  uint64_t d = n - 1;
+  int r = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++r;
+  }
+  static const uint64_t bases[7] = {2, 325, 9375, 28178, 450775, 9780504, 1795265022};
+  for (uint64_t b : bases) {
+    uint64_t a = b % n;
+    if (a == 0) continue;
+    uint64_t x = h_powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool witness = true;
+    for (int i = 1; i < r && witness; ++i) {
+      x = h_mulmod(x, x, n);
+      if (x == n - 1) witness = false;
+    }
+    if (witness) return false;
+  }
+  return true;
+}
+
+int find_primes(int bits, int count, const uint64_t* exclude, int nexclude, uint64_t* out) {
+  const uint64_t step = 1ULL << 16;
+  int found = 0;
+  for (uint64_t c = ((1ULL << bits) - 1) / step * step + 1; c > step && found < count; c -= step) {
+    if (c >= (1ULL << bits)) continue;
+    bool skip = false;
+    for (int i = 0; i < nexclude; ++i) skip |= exclude[i] == c;
+    if (!skip && is_prime(c)) out[found++] = c;
+  }
+  return found;
+}
+
+uint64_t h_qnr(uint64_t p) {
+  for (uint64_t g = 2;; ++g)
+    if (h_powmod(g, (p - 1) / 2, p) == p - 1) return g;
+}
+
+// -p^{-1} mod 2^64 by Newton iteration (p odd)
+static uint64_t neg_inv64(uint64_t p) {
+  uint64_t x = p;  // correct to 3 bits
+  for (int i = 0; i < 6; ++i) x *= 2 - p * x;
+  return (uint64_t)0 - x;
+}
+
+// prod of the moduli in `ms` (skipping index `skip`) reduced mod m
+static uint64_t prod_mod(const uint64_t* ms, int n, int skip, uint64_t m) {
+  uint64_t r = 1 % m;
+  for (int i = 0; i < n; ++i)
+    if (i != skip) r = h_mulmod(r, ms[i] % m, m);
+  return r;
+}
+
+// x 2^64 mod p
+static uint64_t to_mont(uint64_t x, uint64_t p) { return (uint64_t)(((u128)(x % p) << 64) % p); }
+
+// floor(2^128 / p) for odd p > 2^54, as (hi, lo)
+static void recip128(uint64_t p, uint64_t* hi, uint64_t* lo) {
+  u128 all = ~(u128)0;  // 2^128 - 1; p odd never divides 2^128
+  u128 r = all / p;
+  *hi = (uint64_t)(r >> 64);
+  *lo = (uint64_t)r;
+}
+
+int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err, int errlen) {
+  memset(C, 0, sizeof(Consts));
+  for (int i = 0; i < L; ++i) {
+    if (!is_prime(q[i]) || q[i] >= (1ULL << 55) || q[i] % 65536 != 1) {
+      snprintf(err, errlen, "q[%d] = %llu is not a prime < 2^55 congruent to 1 mod 2^16", i, (unsigned long long)q[i]);
+      return -1;
+    }
+    for (int j = 0; j < i; ++j)
+      if (q[j] == q[i]) {
+        snprintf(err, errlen, "duplicate data prime");
+        return -1;
+      }
+  }
+  if (!is_prime(P) || P >= (1ULL << 56) || P % 65536 != 1) {
+    snprintf(err, errlen, "P is not a prime < 2^56 congruent to 1 mod 2^16");
+    return -1;
+  }
+  if (t != 65537) {
+    snprintf(err, errlen, "plaintext modulus must be 65537");
+    return -6;
+  }
+  // auxiliary base: the largest primes below 2^55 (= 1 mod 2^16) not used by Q or P
+  uint64_t excl[L + 1];
+  for (int i = 0; i < L; ++i) excl[i] = q[i];
+  excl[L] = P;
+  uint64_t b[K];
+  if (find_primes(55, K, excl, L + 1, b) != K) {
+    snprintf(err, errlen, "auxiliary prime search failed");
+    return -1;
+  }
+  // digit reductions use one conditional subtraction (max q < 2 min q, P > max q),
+  // the mod-down reduces residues mod P with two (P < 4 min q)
+  uint64_t lo = q[0], hi = q[0];
+  for (int i = 0; i < L; ++i) lo = q[i] < lo ? q[i] : lo, hi = q[i] > hi ? q[i] : hi;
+  if (hi >= 2 * lo || P <= hi || P >= 4 * lo || lo < (1ULL << 54)) {
+    snprintf(err, errlen, "primes must satisfy 2^54 <= q_i, max q < 2 min q < P < 4 min q");
+    return -1;
+  }
+  // B must exceed t N_max Q by a margin: log2 B > log2 Q + 17 + 15 + 20
+  double lq = 0, lb = 0;
+  for (int i = 0; i < L; ++i) lq += log2((double)q[i]);
+  for (int k = 0; k < K; ++k) lb += log2((double)b[k]);
+  if (lb < lq + 52) {
+    snprintf(err, errlen, "auxiliary base too small");
+    return -1;
+  }
+
+  uint64_t all[NPRIME];
+  for (int i = 0; i < L; ++i) all[i] = q[i];
+  for (int k = 0; k < K; ++k) all[L + k] = b[k];
+  all[ID_P] = P;
+  all[ID_T] = t;
+  for (int i = 0; i < NPRIME; ++i) {
+    C->p[i] = all[i];
+    C->pinv[i] = neg_inv64(all[i]);
+    C->r2[i] = h_mulmod(to_mont(1, all[i]), to_mont(1, all[i]), all[i]);  // 2^128 mod p
+  }
+  // Q -> B
+  for (int i = 0; i < L; ++i) {
+    uint64_t qh = prod_mod(q, L, i, q[i]);
+    C->qhatinv[i] = h_invmod(qh, q[i]);
+    C->qhatinv_s[i] = h_shoup(C->qhatinv[i], q[i]);
+    C->qhat[i] = qh;
+    C->qhat_s[i] = h_shoup(qh, q[i]);
+    recip128(q[i], &C->om_hi[i], &C->om_lo[i]);
+    for (int k = 0; k < K; ++k) C->MQB[i][k] = to_mont(prod_mod(q, L, i, b[k]), b[k]);
+  }
+  for (int k = 0; k < K; ++k) {
+    uint64_t Qb = prod_mod(q, L, -1, b[k]);
+    C->QmodB[k] = Qb;
+    C->negQB[k] = to_mont((b[k] - Qb) % b[k], b[k]);
+    // B -> Q
+    uint64_t bh = prod_mod(b, K, k, b[k]);
+    C->QBinv[k] = h_mulmod(h_invmod(Qb, b[k]), h_invmod(bh, b[k]), b[k]);
+    C->QBinv_s[k] = h_shoup(C->QBinv[k], b[k]);
+    recip128(b[k], &C->omb_hi[k], &C->omb_lo[k]);
+    for (int i = 0; i < L; ++i) C->MBQ[k][i] = to_mont(prod_mod(b, K, k, q[i]), q[i]);
+  }
+  for (int i = 0; i < L; ++i) {
+    uint64_t Bq = prod_mod(b, K, -1, q[i]);
+    C->negBQ[i] = to_mont((q[i] - Bq) % q[i], q[i]);
+  }
+  // Garner digits of (Q-1)/2: residue mod q_i is (q_i - 1)/2
+  uint64_t dig[L];
+  for (int i = 0; i < L; ++i) {
+    for (int j = 0; j < L; ++j) {
+      C->mrc_inv[j][i] = j < i ? h_invmod(q[j] % q[i], q[i]) : 0;
+      C->mrc_inv_s[j][i] = j < i ? h_shoup(C->mrc_inv[j][i], q[i]) : 0;
+    }
+  }
+  for (int i = 0; i < L; ++i) {
+    uint64_t x = (q[i] - 1) / 2;
+    for (int j = 0; j < i; ++j) {
+      uint64_t d = dig[j] % q[i];
+      x = x >= d ? x - d : x + q[i] - d;
+      x = h_mulmod(x, C->mrc_inv[j][i], q[i]);
+    }
+    dig[i] = x;
+    C->half_digit[i] = x;
+  }
+  // mod-down and plaintext constants
+  uint64_t Qt = prod_mod(q, L, -1, t);
+  uint64_t tinvq, rt = Qt;  // Q = t Delta + rt
+  for (int i = 0; i < L; ++i) {
+    C->Pinv[i] = h_invmod(P % q[i], q[i]);
+    C->Pinv_s[i] = h_shoup(C->Pinv[i], q[i]);
+    C->Pmodq[i] = P % q[i];
+    tinvq = h_invmod(t, q[i]);
+    C->delta[i] = h_mulmod((q[i] - rt % q[i]) % q[i], tinvq, q[i]);  // (Q - rt)/t mod q_i
+    C->delta_s[i] = h_shoup(C->delta[i], q[i]);
+    C->tqhatinv[i] = h_mulmod(t, C->qhatinv[i], q[i]);
+    C->tqhatinv_s[i] = h_shoup(C->tqhatinv[i], q[i]);
+    C->MQt[i] = to_mont(prod_mod(q, L, i, t), t);
+  }
+  C->negQt = to_mont((t - Qt) % t, t);
+  C->Qinv_t = h_invmod(Qt, t);
+  return 0;
+}
+
+int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {
+  (void)P;
+  double lq = 0;
+  for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
+  double lt = log2((double)t);
+  // fresh invariant-noise budget and the per-squaring cost, both on the
+  // conservative side of the oracle's measurements (DESIGN: noise model)
+  double fresh = lq - lt - log_n - 8.0;
+  double per = lt + log_n + 2.0;
+  if (fresh <= 0) return 0;
+  return (int)floor((fresh - 1.0) / per);
+}
+
+}  // namespace hp

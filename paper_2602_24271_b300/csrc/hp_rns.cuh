@@ -1,0 +1,260 @@
+// Element-wise RNS kernels of one squaring + relinearisation (textbook FV,
+// bit-exact):
+//   k_lift        (x - y) or x, centred-lifted exactly from Q to Q u B
+//   k_tensor      d0 = a0^2, d1 = 2 a0 a1, d2 = a1^2 (NTT domain, Montgomery)
+//   k_scale_round w = round(t d / Q) mod Q, exactly, via r = [t d]_Q lifted to B
+//   k_ks_expand   digits [d2]_{q_i} reduced mod every key-switching prime
+//   k_ks_mac      u_j = sum_i digit_i rk_{i,j} (NTT domain, 128-bit lazy sums)
+//   k_moddown     c += round(u / P) mod Q  (optionally fused with "1 -")
+#pragma once
+#include "hp_device.cuh"
+
+namespace hp {
+
+constexpr int EW_THREADS = 256;
+
+// status bits written by kernels (never expected; checked by the host)
+enum { ST_BQ_WINDOW = 1 };
+
+// Difference modes of the first lift (row a1).
+enum { LIFT_COPY = 0, LIFT_SUB_CT = 1, LIFT_SUB_CONST = 2 };
+
+// One thread per (ciphertext b, component c, coefficient n).
+// src, sub: [nct][2][L][N]; ext: [nct][2][NQB][N].
+__global__ void __launch_bounds__(EW_THREADS) k_lift(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub,
+                                                     uint64_t const_val, int mode, uint64_t* __restrict__ ext, int logN,
+                                                     int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * 2 * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bc = gid >> logN;  // b * 2 + c
+  const int comp = (int)(bc & 1);
+  const uint64_t* x = src + bc * L * N + n;
+  uint64_t* o = ext + bc * NQB * N + n;
+  uint64_t y[L];
+  Fix F = {0, 0};
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const uint64_t p = cK.p[i];
+    uint64_t v = x[(size_t)i * N];
+    if (mode == LIFT_SUB_CT) {
+      v = sub_mod(v, sub[bc * L * N + (size_t)i * N + n], p);
+    } else if (mode == LIFT_SUB_CONST && comp == 0 && n == 0) {
+      v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
+    }
+    o[(size_t)i * N] = v;
+    y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
+    fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
+  }
+  const uint64_t v = (uint64_t)lift_v_mem(F, o, N);  // exact path re-reads the residues written above
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t b = cK.p[L + k];
+    Acc acc;
+    acc_zero(acc);
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc_mac(acc, y[i], cK.MQB[i][k]);
+    acc_mac(acc, v, cK.negQB[k]);
+    o[(size_t)(L + k) * N] = redc(acc, b, cK.pinv[L + k]);
+  }
+}
+
+// One thread per (b, prime index pi in Q u B, n).  ext values canonical (NTT domain).
+// dprod: [nct][3][NQB][N], values a b 2^-64 in [0, 2p).
+__global__ void __launch_bounds__(EW_THREADS) k_tensor_sq(const uint64_t* __restrict__ ext, uint64_t* __restrict__ dprod,
+                                                          int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * NQB * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bp = gid >> logN;
+  const int pi = (int)(bp % NQB);
+  const size_t b = bp / NQB;
+  const uint64_t p = cK.p[pi], pinv = cK.pinv[pi], p2 = 2 * p;
+  const uint64_t a0 = ext[((b * 2 + 0) * NQB + pi) * N + n];
+  const uint64_t a1 = ext[((b * 2 + 1) * NQB + pi) * N + n];
+  uint64_t d1 = 2 * mont_mul_lazy(a0, a1, p, pinv);
+  dprod[((b * 3 + 0) * NQB + pi) * N + n] = mont_mul_lazy(a0, a0, p, pinv);
+  dprod[((b * 3 + 1) * NQB + pi) * N + n] = d1 >= p2 ? d1 - p2 : d1;
+  dprod[((b * 3 + 2) * NQB + pi) * N + n] = mont_mul_lazy(a1, a1, p, pinv);
+}
+
+// General tensor of ciphertexts a and b (SELECT): d1 = a0 b1 + a1 b0.
+__global__ void __launch_bounds__(EW_THREADS) k_tensor_gen(const uint64_t* __restrict__ ea, const uint64_t* __restrict__ eb,
+                                                           uint64_t* __restrict__ dprod, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * NQB * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bp = gid >> logN;
+  const int pi = (int)(bp % NQB);
+  const size_t b = bp / NQB;
+  const uint64_t p = cK.p[pi], pinv = cK.pinv[pi];
+  const uint64_t a0 = ea[((b * 2 + 0) * NQB + pi) * N + n], a1 = ea[((b * 2 + 1) * NQB + pi) * N + n];
+  const uint64_t b0 = eb[((b * 2 + 0) * NQB + pi) * N + n], b1 = eb[((b * 2 + 1) * NQB + pi) * N + n];
+  Acc x;
+  acc_zero(x);
+  acc_mac(x, a0, b1);
+  acc_mac(x, a1, b0);
+  dprod[((b * 3 + 0) * NQB + pi) * N + n] = mont_mul_lazy(a0, b0, p, pinv);
+  dprod[((b * 3 + 1) * NQB + pi) * N + n] = redc_lazy(x, p, pinv);
+  dprod[((b * 3 + 2) * NQB + pi) * N + n] = mont_mul_lazy(a1, b1, p, pinv);
+}
+
+// One thread per (b, j in {0,1,2}, n).  dprod holds t d (coefficient domain,
+// canonical) in Q u B.  Writes w = round(t d / Q) mod q_i to w3[b][j][i][n].
+//
+// r = [t d]_Q is lifted exactly (centred) to B; then w = (t d - r) / Q is an
+// exact integer with |w| <= t N Q / 2 + 1 < B / 2^24, known mod B as
+// (t d - r) Q^{-1}; its centred conversion B -> Q needs no fallback because
+// w / B is within 2^-24 of an integer, far from 1/2.
+__global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3,
+                                                            int* __restrict__ status, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * 3 * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bj = gid >> logN;  // b * 3 + j
+  const uint64_t* d = dprod + bj * NQB * N + n;
+  uint64_t y[L];
+  Fix F = {0, 0};
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    y[i] = mul_shoup(d[(size_t)i * N], cK.qhatinv[i], cK.qhatinv_s[i], cK.p[i]);
+    fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
+  }
+  const uint64_t v = (uint64_t)lift_v_mem(F, d, N);  // lifted value r = [t d]_Q has residues d_i
+  uint64_t yb[K];
+  Fix G = {0, 0};
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t b = cK.p[L + k];
+    Acc acc;
+    acc_zero(acc);
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc_mac(acc, y[i], cK.MQB[i][k]);
+    acc_mac(acc, v, cK.negQB[k]);
+    const uint64_t r = redc(acc, b, cK.pinv[L + k]);
+    const uint64_t z = sub_mod(d[(size_t)(L + k) * N], r, b);
+    yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
+    fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
+  }
+  int vb = fix_round(G, 2 * K);
+  if (vb < 0) {  // cannot happen for |w| < B / 2^24; recorded for the host
+    atomicOr(status, ST_BQ_WINDOW);
+    vb = (int)G.hi;
+  }
+  uint64_t* o = w3 + bj * L * N + n;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const uint64_t p = cK.p[i];
+    Acc acc;
+    acc_zero(acc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc_mac(acc, yb[k], cK.MBQ[k][i]);
+    acc_mac(acc, (uint64_t)vb, cK.negBQ[i]);
+    o[(size_t)i * N] = redc(acc, p, cK.pinv[i]);
+  }
+}
+
+HPD int ks_id(int j) { return j < L ? j : ID_P; }
+
+// One thread per (b, digit i, target j, n): ksin[b][i][j][n] = [w3[b][2][i][n]]_{p_j}.
+__global__ void __launch_bounds__(EW_THREADS) k_ks_expand(const uint64_t* __restrict__ w3, uint64_t* __restrict__ ksin,
+                                                          int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * L * NKS * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bij = gid >> logN;
+  const int j = (int)(bij % NKS);
+  const size_t bi = bij / NKS;
+  const int i = (int)(bi % L);
+  const size_t b = bi / L;
+  const uint64_t digit = w3[((b * 3 + 2) * L + i) * N + n];
+  ksin[gid] = csub(digit, cK.p[ks_id(j)]);  // digit < q_i < 2 p_j
+}
+
+// One thread per (b, target j, n).  rk: [L][2][NKS][N], NTT domain, Montgomery form.
+// ksout: [nct][2][NKS][N] in [0, 2p).
+__global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restrict__ ksin, const uint64_t* __restrict__ rk,
+                                                       uint64_t* __restrict__ ksout, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * NKS * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bj = gid >> logN;
+  const int j = (int)(bj % NKS);
+  const size_t b = bj / NKS;
+  const int id = ks_id(j);
+  Acc a0, a1;
+  acc_zero(a0);
+  acc_zero(a1);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const uint64_t d = ksin[((b * L + i) * NKS + j) * N + n];
+    acc_mac(a0, d, rk[((size_t)(i * 2 + 0) * NKS + j) * N + n]);
+    acc_mac(a1, d, rk[((size_t)(i * 2 + 1) * NKS + j) * N + n]);
+  }
+  const uint64_t p = cK.p[id], pinv = cK.pinv[id];
+  ksout[((b * 2 + 0) * NKS + j) * N + n] = redc_lazy(a0, p, pinv);
+  ksout[((b * 2 + 1) * NKS + j) * N + n] = redc_lazy(a1, p, pinv);
+}
+
+// x mod q for x < 4q
+HPD uint64_t red4(uint64_t x, uint64_t q) {
+  x = x >= 2 * q ? x - 2 * q : x;
+  return csub(x, q);
+}
+
+// One thread per (b, comp, i, n):
+//   out = w + (u_i - [u_P]) P^{-1} mod q_i,   [u_P] the centred residue mod P.
+// one_minus: additionally out <- (Delta - out) for comp 0 at n = 0, -out otherwise.
+__global__ void __launch_bounds__(EW_THREADS) k_moddown(const uint64_t* __restrict__ ksout, const uint64_t* __restrict__ w3,
+                                                        uint64_t* __restrict__ out, int one_minus, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * 2 * L * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bci = gid >> logN;
+  const int i = (int)(bci % L);
+  const size_t bc = bci / L;
+  const int comp = (int)(bc & 1);
+  const size_t b = bc >> 1;
+  const uint64_t q = cK.p[i], P = cK.p[ID_P];
+  const uint64_t uP = ksout[(bc * NKS + L) * N + n];
+  const uint64_t ui = ksout[(bc * NKS + i) * N + n];
+  uint64_t diff;
+  if (uP <= (P - 1) / 2) {
+    diff = sub_mod(ui, red4(uP, q), q);
+  } else {
+    diff = add_mod(ui, red4(P - uP, q), q);
+  }
+  uint64_t ks = mul_shoup(diff, cK.Pinv[i], cK.Pinv_s[i], q);
+  uint64_t w = w3[((b * 3 + comp) * L + i) * N + n];
+  uint64_t r = add_mod(w, ks, q);
+  if (one_minus) {
+    r = sub_mod(0, r, q);
+    if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], q);
+  }
+  out[gid] = r;
+}
+
+// "1 -" alone: out = (Delta - c0, -c1).  One thread per word of [nct][2][L][N].
+__global__ void __launch_bounds__(EW_THREADS) k_one_minus(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                          int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * 2 * L * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bci = gid >> logN;
+  const int i = (int)(bci % L);
+  const int comp = (int)((bci / L) & 1);
+  const uint64_t q = cK.p[i];
+  uint64_t r = sub_mod(0, in[gid], q);
+  if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], q);
+  out[gid] = r;
+}
+
+}  // namespace hp

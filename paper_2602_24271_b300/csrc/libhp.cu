@@ -1,0 +1,532 @@
+// libhp: C ABI, handle management and the per-tile pipeline of the equality
+// predicate EQ(x, y) = 1 - (x - y)^(p-1) (16 squarings + relinearisation).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hp.h"
+#include "hp_client.cuh"
+#include "hp_defs.h"
+#include "hp_device.cuh"
+#include "hp_ntt.cuh"
+#include "hp_rns.cuh"
+
+using namespace hp;
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct hp_handle {
+  int logn = 0, N = 0, logR = 0;
+  uint64_t q[L] = {}, P = 0, t = 0;
+  uint32_t max_depth = 0;
+  Consts C;
+  int device = 0;
+  // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][2]
+  uint64_t *tw = nullptr, *tws = nullptr, *itw = nullptr, *itws = nullptr, *scale = nullptr;
+  // relinearisation key, NTT domain, Montgomery form: [L][2][NKS][N]
+  uint64_t* rkm = nullptr;
+  bool have_rk = false;
+  // workspace for one pipeline tile of `tile` ciphertexts
+  size_t tile = 0;
+  uint64_t *ext = nullptr, *ext2 = nullptr, *dprod = nullptr, *w3 = nullptr, *ksin = nullptr, *ksout = nullptr,
+           *ctbuf = nullptr, *maskbuf = nullptr;
+  // staging for host-memory calls: x, y, out for one tile
+  uint64_t *stx = nullptr, *sty = nullptr, *sto = nullptr;
+  int* status = nullptr;  // device status word (ST_* bits)
+  uint64_t launches = 0;
+  std::string err;
+};
+
+static std::string g_create_err;
+
+#define HP_FAIL(h, code, ...)                                  \
+  do {                                                         \
+    char _b[512];                                              \
+    snprintf(_b, sizeof(_b), __VA_ARGS__);                     \
+    if (h) (h)->err = _b; else g_create_err = _b;              \
+    return code;                                               \
+  } while (0)
+
+#define CU(h, call)                                                                  \
+  do {                                                                               \
+    cudaError_t _e = (call);                                                         \
+    if (_e != cudaSuccess) HP_FAIL(h, HP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+
+static inline size_t words_ct(const hp_handle* h) { return (size_t)2 * L * h->N; }
+
+// per-ciphertext workspace words
+static size_t ws_words_per_ct(int N) {
+  return (size_t)N * (2 * NQB      // ext
+                      + 2 * NQB    // ext2 (SELECT operand)
+                      + 3 * NQB    // dprod
+                      + 3 * L      // w3
+                      + L * NKS    // ksin
+                      + 2 * NKS    // ksout
+                      + 2 * L      // ctbuf
+                      + 2 * L      // maskbuf
+                      + 3 * 2 * L  // staging x, y, out
+                     );
+}
+
+static inline unsigned ew_blocks(size_t n) { return (unsigned)((n + EW_THREADS - 1) / EW_THREADS); }
+
+static NttTabs tabs(const hp_handle* h) {
+  NttTabs T;
+  T.tw = h->tw;
+  T.tws = h->tws;
+  T.itw = h->itw;
+  T.itws = h->itws;
+  T.scale = h->scale;
+  return T;
+}
+
+static const PolyMap MAP_QB = {NQB, 0, -1};  // [.][NQB][N]: ids 0..30
+static const PolyMap MAP_KS = {NKS, 0, ID_P}; // [.][NKS][N]: q_0..q_14, P
+static const PolyMap MAP_Q = {L, 0, -1};      // [.][L][N]
+static const PolyMap MAP_T = {1, ID_T, -1};   // plaintext modulus
+
+static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaStream_t s) {
+  if (npoly == 0) return;
+  const int logC = h->logn - h->logR;
+  dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
+  dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
+  k_ntt_fwd_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  k_ntt_fwd_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  h->launches += 2;
+}
+
+static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int scale_mode, cudaStream_t s) {
+  if (npoly == 0) return;
+  const int logC = h->logn - h->logR;
+  dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
+  dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
+  k_ntt_inv_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  k_ntt_inv_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR, scale_mode);
+  h->launches += 2;
+}
+
+// ---------------------------------------------------------------------------
+// one squaring (or general product) + relinearisation on a tile of b
+// ciphertexts whose extended-base transforms are in h->ext (and h->ext2)
+// ---------------------------------------------------------------------------
+static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int one_minus, cudaStream_t s) {
+  const int N = h->N, logN = h->logn;
+  ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
+  if (general) {
+    ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
+    k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->ext2, h->dprod, logN, b);
+  } else {
+    k_tensor_sq<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->dprod, logN, b);
+  }
+  h->launches += 1;
+  ntt_inv(h, h->dprod, (size_t)b * 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
+  k_scale_round<<<ew_blocks((size_t)b * 3 * N), EW_THREADS, 0, s>>>(h->dprod, h->w3, h->status, logN, b);
+  k_ks_expand<<<ew_blocks((size_t)b * L * NKS * N), EW_THREADS, 0, s>>>(h->w3, h->ksin, logN, b);
+  h->launches += 2;
+  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s);
+  k_ks_mac<<<ew_blocks((size_t)b * NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
+  h->launches += 1;
+  ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
+  k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, out, one_minus, logN, b);
+  h->launches += 1;
+}
+
+static void lift(hp_handle* h, const uint64_t* src, const uint64_t* sub, uint64_t cval, int mode, uint64_t* ext, int b,
+                 cudaStream_t s) {
+  k_lift<<<ew_blocks((size_t)b * 2 * h->N), EW_THREADS, 0, s>>>(src, sub, cval, mode, ext, h->logn, b);
+  h->launches += 1;
+}
+
+// The whole hot path for one tile of b device-resident ciphertexts.
+static void run_tile(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t cval, uint64_t* out, int b,
+                     cudaStream_t s) {
+  if (op == HP_SQUARE) {
+    lift(h, x, nullptr, 0, LIFT_COPY, h->ext, b, s);
+    mul_relin_tail(h, b, false, out, 0, s);
+    return;
+  }
+  // a1: difference, fused into the first lift
+  if (op == HP_EQ_CT_CT)
+    lift(h, x, y, 0, LIFT_SUB_CT, h->ext, b, s);
+  else
+    lift(h, x, nullptr, cval, LIFT_SUB_CONST, h->ext, b, s);
+  // a2: 16 squarings; a3: "1 -" fused into the last mod-down
+  for (int it = 0; it < 16; ++it) {
+    if (it > 0) lift(h, h->ctbuf, nullptr, 0, LIFT_COPY, h->ext, b, s);
+    const bool last = it == 15;
+    uint64_t* dst = !last ? h->ctbuf : (op == HP_SELECT ? h->maskbuf : out);
+    mul_relin_tail(h, b, false, dst, last ? 1 : 0, s);
+  }
+  if (op == HP_SELECT) {  // a4: column * mask
+    lift(h, h->maskbuf, nullptr, 0, LIFT_COPY, h->ext, b, s);
+    lift(h, y, nullptr, 0, LIFT_COPY, h->ext2, b, s);
+    mul_relin_tail(h, b, true, out, 0, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+static int brv(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+static int build_tables(hp_handle* h) {
+  const int N = h->N;
+  std::vector<uint64_t> tw((size_t)NPRIME * N), tws(tw.size()), itw(tw.size()), itws(tw.size());
+  std::vector<uint64_t> sc((size_t)NSCALE * NPRIME * 2);
+  std::vector<uint64_t> pw(N), ipw(N);
+  for (int id = 0; id < NPRIME; ++id) {
+    const uint64_t p = h->C.p[id];
+    const uint64_t psi = h_powmod(h_qnr(p), (p - 1) / (2 * (uint64_t)N), p);
+    const uint64_t ipsi = h_invmod(psi, p);
+    pw[0] = ipw[0] = 1;
+    for (int e = 1; e < N; ++e) {
+      pw[e] = h_mulmod(pw[e - 1], psi, p);
+      ipw[e] = h_mulmod(ipw[e - 1], ipsi, p);
+    }
+    for (int j = 0; j < N; ++j) {
+      size_t o = (size_t)id * N + j;
+      tw[o] = pw[brv(j, h->logn)];
+      tws[o] = h_shoup(tw[o], p);
+      itw[o] = ipw[brv(j, h->logn)];
+      itws[o] = h_shoup(itw[o], p);
+    }
+    const uint64_t ninv = h_invmod((uint64_t)N % p, p);
+    const uint64_t r64 = (uint64_t)(((unsigned __int128)1 << 64) % p);
+    const uint64_t vals[NSCALE] = {ninv, h_mulmod(h_mulmod(h->t % p, ninv, p), r64, p), h_mulmod(ninv, r64, p)};
+    for (int m = 0; m < NSCALE; ++m) {
+      sc[((size_t)m * NPRIME + id) * 2 + 0] = vals[m];
+      sc[((size_t)m * NPRIME + id) * 2 + 1] = h_shoup(vals[m], p);
+    }
+  }
+  size_t tb = tw.size() * sizeof(uint64_t);
+  CU(h, cudaMalloc(&h->tw, tb));
+  CU(h, cudaMalloc(&h->tws, tb));
+  CU(h, cudaMalloc(&h->itw, tb));
+  CU(h, cudaMalloc(&h->itws, tb));
+  CU(h, cudaMalloc(&h->scale, sc.size() * sizeof(uint64_t)));
+  CU(h, cudaMemcpy(h->tw, tw.data(), tb, cudaMemcpyHostToDevice));
+  CU(h, cudaMemcpy(h->tws, tws.data(), tb, cudaMemcpyHostToDevice));
+  CU(h, cudaMemcpy(h->itw, itw.data(), tb, cudaMemcpyHostToDevice));
+  CU(h, cudaMemcpy(h->itws, itws.data(), tb, cudaMemcpyHostToDevice));
+  CU(h, cudaMemcpy(h->scale, sc.data(), sc.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  return HP_OK;
+}
+
+// The constant block lives in __constant__ memory, one per device; handles on
+// the same device must agree on (q, P, t).
+static bool g_loaded[64];
+static Consts g_consts[64];
+
+static int load_consts(hp_handle* h) {
+  if (h->device < 0 || h->device >= 64) HP_FAIL(h, HP_ERR_UNSUPPORTED, "device index out of range");
+  if (g_loaded[h->device]) {
+    if (memcmp(&g_consts[h->device], &h->C, sizeof(Consts)) != 0)
+      HP_FAIL(h, HP_ERR_UNSUPPORTED, "a handle with different primes already uses this device");
+    return HP_OK;
+  }
+  CU(h, cudaMemcpyToSymbol(cK, &h->C, sizeof(Consts)));
+  g_consts[h->device] = h->C;
+  g_loaded[h->device] = true;
+  return HP_OK;
+}
+
+static void free_all(hp_handle* h) {
+  uint64_t* ptrs[] = {h->tw, h->tws, h->itw, h->itws, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
+                      h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto};
+  for (uint64_t* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->status) cudaFree(h->status);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int hp_default_params(uint32_t Lreq, uint64_t* q_out, uint64_t* P_out, uint64_t* t_out) {
+  if (!q_out || !P_out || !t_out || Lreq == 0 || Lreq > (uint32_t)L) return HP_ERR_ARG;
+  uint64_t q[L];
+  if (find_primes(55, (int)Lreq, nullptr, 0, q) != (int)Lreq) return HP_ERR_UNSUPPORTED;
+  uint64_t P;
+  if (find_primes(56, 1, nullptr, 0, &P) != 1) return HP_ERR_UNSUPPORTED;
+  for (uint32_t i = 0; i < Lreq; ++i) q_out[i] = q[i];
+  *P_out = P;
+  *t_out = 65537;
+  return HP_OK;
+}
+
+int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_ct, hp_handle** out) {
+  hp_handle* h0 = nullptr;
+  if (!prm || !out || !prm->q) HP_FAIL(h0, HP_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (prm->log_n < LOGN_MIN || prm->log_n > LOGN_MAX)
+    HP_FAIL(h0, HP_ERR_UNSUPPORTED, "log_n must be in [%d, %d]", LOGN_MIN, LOGN_MAX);
+  if (prm->L != (uint32_t)L) HP_FAIL(h0, HP_ERR_UNSUPPORTED, "L must be %d", L);
+  hp_handle* h = new hp_handle();
+  h->logn = (int)prm->log_n;
+  h->N = 1 << h->logn;
+  h->logR = h->logn / 2;
+  memcpy(h->q, prm->q, sizeof(h->q));
+  h->P = prm->P;
+  h->t = prm->t;
+  h->max_depth = prm->max_depth;
+  char eb[256] = {0};
+  int rc = build_consts(h->q, h->P, h->t, &h->C, eb, sizeof(eb));
+  if (rc != 0) {
+    g_create_err = eb;
+    delete h;
+    return rc == -6 ? HP_ERR_UNSUPPORTED : HP_ERR_ARG;
+  }
+  int depth = supported_depth(h->logn, h->q, L, h->P, h->t);
+  if ((int)prm->max_depth > depth) {
+    char b[128];
+    snprintf(b, sizeof(b), "max_depth %u exceeds the estimated supported depth %d", prm->max_depth, depth);
+    g_create_err = b;
+    delete h;
+    return HP_ERR_DEPTH;
+  }
+  auto fail = [&](int code) {
+    g_create_err = h->err;
+    free_all(h);
+    delete h;
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    h->err = "no CUDA device";
+    return fail(HP_ERR_CUDA);
+  }
+  if ((rc = load_consts(h)) != HP_OK) return fail(rc);
+  if ((rc = build_tables(h)) != HP_OK) return fail(rc);
+  size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
+  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)1 << 30) / per);
+  if (h->tile < 1) h->tile = 1;
+  if (h->tile > 64) h->tile = 64;
+  const size_t T = h->tile, N = h->N;
+  struct {
+    uint64_t** p;
+    size_t words;
+  } allocs[] = {{&h->ext, T * 2 * NQB * N},  {&h->ext2, T * 2 * NQB * N}, {&h->dprod, T * 3 * NQB * N},
+                {&h->w3, T * 3 * L * N},     {&h->ksin, T * L * NKS * N}, {&h->ksout, T * 2 * NKS * N},
+                {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
+                {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->rkm, (size_t)L * 2 * NKS * N}};
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.p, a.words * sizeof(uint64_t)) != cudaSuccess) {
+      h->err = "device allocation failed for the workspace";
+      return fail(HP_ERR_OOM);
+    }
+  }
+  if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess || cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
+    h->err = "status word allocation failed";
+    return fail(HP_ERR_OOM);
+  }
+  if (relin_key) {
+    if ((rc = hp_set_relin_key(h, relin_key)) != HP_OK) return fail(rc);
+  }
+  *out = h;
+  return HP_OK;
+}
+
+int hp_set_relin_key(hp_handle* h, const uint64_t* rk) {
+  if (!h) return HP_ERR_ARG;
+  if (!rk) HP_FAIL(h, HP_ERR_ARG, "null relinearisation key");
+  const size_t words = (size_t)L * 2 * NKS * h->N;
+  CU(h, cudaMemcpy(h->rkm, rk, words * sizeof(uint64_t), cudaMemcpyDeviceToDevice));
+  ntt_fwd(h, h->rkm, (size_t)L * 2 * NKS, MAP_KS, 0);
+  k_to_mont<<<ew_blocks(words), EW_THREADS>>>(h->rkm, NKS, 0, ID_P, (size_t)L * 2 * NKS, h->logn);
+  CU(h, cudaGetLastError());
+  CU(h, cudaDeviceSynchronize());
+  h->have_rk = true;
+  return HP_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int hp_run(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t cval, uint64_t* out, size_t n_ct,
+           void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (op < HP_EQ_CT_CT || op > HP_SQUARE) HP_FAIL(h, HP_ERR_ARG, "unknown op %d", op);
+  if (n_ct == 0) return HP_OK;
+  if (!x || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if ((op == HP_EQ_CT_CT || op == HP_SELECT) && !y) HP_FAIL(h, HP_ERR_ARG, "op needs ct_y");
+  if ((op == HP_EQ_CT_CONST || op == HP_SELECT) && cval >= h->t) HP_FAIL(h, HP_ERR_ARG, "const_val must be < t");
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  int need = op == HP_SQUARE ? 1 : (op == HP_SELECT ? 17 : 16);
+  if (need > supported_depth(h->logn, h->q, L, h->P, h->t))
+    HP_FAIL(h, HP_ERR_DEPTH, "operation depth %d exceeds the parameters' budget", need);
+  if (((uintptr_t)x | (uintptr_t)out | (uintptr_t)y) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t W = words_ct(h);
+  const bool dev = is_device_ptr(x);
+  if (dev != is_device_ptr(out) || ((op == HP_EQ_CT_CT || op == HP_SELECT) && dev != is_device_ptr(y)))
+    HP_FAIL(h, HP_ERR_ARG, "ciphertext arguments must all be device memory or all host memory");
+  for (size_t c0 = 0; c0 < n_ct; c0 += h->tile) {
+    const int b = (int)((n_ct - c0 < h->tile) ? n_ct - c0 : h->tile);
+    const size_t off = c0 * W, bytes = (size_t)b * W * sizeof(uint64_t);
+    if (dev) {
+      run_tile(h, op, x + off, y ? y + off : nullptr, cval, out + off, b, s);
+    } else {
+      CU(h, cudaMemcpyAsync(h->stx, x + off, bytes, cudaMemcpyHostToDevice, s));
+      if (op == HP_EQ_CT_CT || op == HP_SELECT) CU(h, cudaMemcpyAsync(h->sty, y + off, bytes, cudaMemcpyHostToDevice, s));
+      run_tile(h, op, h->stx, h->sty, cval, h->sto, b, s);
+      CU(h, cudaMemcpyAsync(out + off, h->sto, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    CU(h, cudaGetLastError());
+  }
+  if (!dev) CU(h, cudaStreamSynchronize(s));
+  return HP_OK;
+}
+
+int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst, const uint64_t* x, const uint64_t* y,
+                   uint64_t* out, size_t n_ct_total, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  (void)inst;
+  (void)n_inst;
+  (void)x;
+  (void)y;
+  (void)out;
+  (void)n_ct_total;
+  (void)stream;
+  (void)op;
+  HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_run_batched: not built yet");
+}
+
+int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream) {
+  (void)op;
+  (void)grad_out;
+  (void)grad_x;
+  (void)n_ct;
+  (void)stream;
+  if (h) h->err = "EQ is an exact integer map over Z_Q: it has no adjoint";
+  return HP_ERR_UNSUPPORTED;
+}
+
+void hp_destroy(hp_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+const char* hp_last_error(const hp_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+uint64_t hp_launch_count(const hp_handle* h) { return h ? h->launches : 0; }
+
+// ---- client helpers ---------------------------------------------------------
+int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  if (!sk || !rk) HP_FAIL(h, HP_ERR_ARG, "null output");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N, logN = h->logn;
+  uint64_t *S = nullptr, *S2 = nullptr, *A = nullptr;
+  CU(h, cudaMalloc(&S, (size_t)NKS * N * 8));
+  CU(h, cudaMalloc(&S2, (size_t)NKS * N * 8));
+  CU(h, cudaMalloc(&A, (size_t)L * NKS * N * 8));
+  k_sample_secret<<<ew_blocks(N), EW_THREADS, 0, s>>>(sk, seed, N);
+  k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(sk, S, NKS, 0, ID_P, N);
+  ntt_fwd(h, S, NKS, MAP_KS, s);
+  k_pointwise_mont<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(S, S, S2, NKS, NKS, 0, ID_P, NKS, logN);
+  ntt_inv(h, S2, NKS, MAP_KS, SCALE_NINV_R, s);
+  k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, seed, logN);
+  ntt_fwd(h, A, (size_t)L * NKS, MAP_KS, s);
+  k_pointwise_mont<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P, (size_t)L * NKS,
+                                                                        logN);
+  ntt_inv(h, A, (size_t)L * NKS, MAP_KS, SCALE_NINV_R, s);
+  k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, S2, seed, logN);
+  CU(h, cudaGetLastError());
+  CU(h, cudaStreamSynchronize(s));
+  cudaFree(S);
+  cudaFree(S2);
+  cudaFree(A);
+  return hp_set_relin_key(h, rk);
+}
+
+// S[j] = NTT(s mod q_j), j < L
+static int secret_ntt_q(hp_handle* h, const int8_t* sk, uint64_t* S, cudaStream_t s) {
+  k_secret_to_primes<<<ew_blocks((size_t)L * h->N), EW_THREADS, 0, s>>>(sk, S, L, 0, -1, h->N);
+  ntt_fwd(h, S, L, MAP_Q, s);
+  return HP_OK;
+}
+
+int hp_encrypt(hp_handle* h, const int8_t* sk, const uint32_t* slots, size_t n_ct, uint64_t seed, uint32_t idx0,
+               uint64_t* ct, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  if (n_ct == 0) return HP_OK;
+  if (!sk || !slots || !ct) HP_FAIL(h, HP_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N, logN = h->logn;
+  uint64_t *S = nullptr, *A = nullptr, *M = nullptr;
+  CU(h, cudaMalloc(&S, (size_t)L * N * 8));
+  CU(h, cudaMalloc(&A, n_ct * L * N * 8));
+  CU(h, cudaMalloc(&M, n_ct * N * 8));
+  secret_ntt_q(h, sk, S, s);
+  k_enc_sample<<<ew_blocks(n_ct * L * N), EW_THREADS, 0, s>>>(ct, A, slots, M, seed, idx0, logN, (int)n_ct);
+  ntt_fwd(h, A, n_ct * L, MAP_Q, s);
+  k_pointwise_mont<<<ew_blocks(n_ct * L * N), EW_THREADS, 0, s>>>(A, S, A, L, L, 0, -1, n_ct * L, logN);
+  ntt_inv(h, A, n_ct * L, MAP_Q, SCALE_NINV_R, s);
+  ntt_inv(h, M, n_ct, MAP_T, SCALE_NINV, s);  // encoding: slots are the transform of m
+  k_enc_finish<<<ew_blocks(n_ct * L * N), EW_THREADS, 0, s>>>(ct, A, M, seed, idx0, logN, (int)n_ct);
+  CU(h, cudaGetLastError());
+  CU(h, cudaStreamSynchronize(s));
+  cudaFree(S);
+  cudaFree(A);
+  cudaFree(M);
+  return HP_OK;
+}
+
+int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, uint32_t* slots, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  if (n_ct == 0) return HP_OK;
+  if (!sk || !slots || !ct) HP_FAIL(h, HP_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N, logN = h->logn;
+  uint64_t *S = nullptr, *C1 = nullptr, *M = nullptr;
+  CU(h, cudaMalloc(&S, (size_t)L * N * 8));
+  CU(h, cudaMalloc(&C1, n_ct * L * N * 8));
+  CU(h, cudaMalloc(&M, n_ct * N * 8));
+  secret_ntt_q(h, sk, S, s);
+  for (size_t c = 0; c < n_ct; ++c)
+    CU(h, cudaMemcpyAsync(C1 + c * L * N, ct + (c * 2 + 1) * L * N, (size_t)L * N * 8, cudaMemcpyDeviceToDevice, s));
+  ntt_fwd(h, C1, n_ct * L, MAP_Q, s);
+  k_pointwise_mont<<<ew_blocks(n_ct * L * N), EW_THREADS, 0, s>>>(C1, S, C1, L, L, 0, -1, n_ct * L, logN);
+  ntt_inv(h, C1, n_ct * L, MAP_Q, SCALE_NINV_R, s);
+  k_dec_round<<<ew_blocks(n_ct * N), EW_THREADS, 0, s>>>(ct, C1, M, logN, (int)n_ct);
+  ntt_fwd(h, M, n_ct, MAP_T, s);  // decoding
+  k_u64_to_u32<<<ew_blocks(n_ct * N), EW_THREADS, 0, s>>>(M, slots, n_ct * N);
+  CU(h, cudaGetLastError());
+  CU(h, cudaStreamSynchronize(s));
+  cudaFree(S);
+  cudaFree(C1);
+  cudaFree(M);
+  return HP_OK;
+}
+
+// Synchronise and report the device status word (exactness checks), then clear it.
+int hp_check_status(hp_handle* h) {
+  if (!h) return HP_ERR_ARG;
+  int st = 0;
+  CU(h, cudaDeviceSynchronize());
+  CU(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CU(h, cudaMemset(h->status, 0, sizeof(int)));
+  if (st) HP_FAIL(h, HP_ERR_CUDA, "device status word %d (exact conversion window violated)", st);
+  return HP_OK;
+}
+
+}  // extern "C"

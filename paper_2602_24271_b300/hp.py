@@ -1,0 +1,248 @@
+"""ctypes binding of libhp (include/hp.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of ``libhp.so``; this
+module converts torch tensors / numpy arrays to pointers and return codes to
+exceptions.  It fails loudly when the shared library is missing: there is no
+CPU fallback.
+
+Tensor conventions: ciphertexts are torch.int64 CUDA tensors of shape
+[n, 2, L, N] holding the uint64 residue words bit for bit.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhp.so")
+
+HP_OK = 0
+HP_ERR_ARG = -1
+HP_ERR_DEPTH = -2
+HP_ERR_OOM = -3
+HP_ERR_CUDA = -4
+HP_ERR_TIMEOUT = -5
+HP_ERR_UNSUPPORTED = -6
+HP_ERR_STATE = -7
+_NAMES = {v: k for k, v in list(globals().items()) if k.startswith("HP_ERR_") or k == "HP_OK"}
+
+HP_EQ_CT_CT = 0
+HP_EQ_CT_CONST = 1
+HP_SELECT = 2
+HP_SQUARE = 3
+
+L = 15
+T = 65537
+
+EXPORTED = [
+    "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
+    "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
+    "hp_check_status",
+]
+
+
+class HpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "HP_ERR"), code, msg))
+        self.code = code
+
+
+class hp_params(ctypes.Structure):
+    _fields_ = [
+        ("log_n", ctypes.c_uint32),
+        ("L", ctypes.c_uint32),
+        ("q", ctypes.POINTER(ctypes.c_uint64)),
+        ("P", ctypes.c_uint64),
+        ("t", ctypes.c_uint64),
+        ("max_depth", ctypes.c_uint32),
+    ]
+
+
+class hp_instance(ctypes.Structure):
+    _fields_ = [
+        ("ct_offset", ctypes.c_uint64),
+        ("n_ct", ctypes.c_uint32),
+        ("slot_offset", ctypes.c_uint32),
+        ("n_slots", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("const_val", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libhp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libhp.so not built: run paper_2602_24271_b300/build.py (or __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    V, P64, SZ = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
+    H = ctypes.c_void_p
+    sig = {
+        "hp_default_params": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "hp_create": (ctypes.c_int, [ctypes.POINTER(hp_params), P64, SZ, ctypes.POINTER(H)]),
+        "hp_set_relin_key": (ctypes.c_int, [H, P64]),
+        "hp_run": (ctypes.c_int, [H, ctypes.c_int, P64, P64, ctypes.c_uint64, P64, SZ, V]),
+        "hp_run_batched": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(hp_instance), SZ, P64, P64, P64, SZ, V]),
+        "hp_backward": (ctypes.c_int, [H, ctypes.c_int, P64, P64, SZ, V]),
+        "hp_destroy": (None, [H]),
+        "hp_last_error": (ctypes.c_char_p, [H]),
+        "hp_keygen": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
+        "hp_encrypt": (ctypes.c_int, [H, V, V, SZ, ctypes.c_uint64, ctypes.c_uint32, P64, V]),
+        "hp_decrypt": (ctypes.c_int, [H, V, P64, SZ, V, V]),
+        "hp_launch_count": (ctypes.c_uint64, [H]),
+        "hp_check_status": (ctypes.c_int, [H]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, h=None):
+    if rc != HP_OK:
+        msg = load().hp_last_error(h)
+        raise HpError(rc, msg.decode() if msg else "")
+
+
+def default_params(nq: int = L):
+    lib = load()
+    q = (ctypes.c_uint64 * nq)()
+    P = ctypes.c_uint64()
+    t = ctypes.c_uint64()
+    _check(lib.hp_default_params(nq, q, ctypes.byref(P), ctypes.byref(t)))
+    return [int(x) for x in q], int(P.value), int(t.value)
+
+
+def _ptr(x) -> int:
+    """Device/host address of a torch tensor or numpy array (None -> 0)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """One libhp handle: parameters, tables, relinearisation key, workspace."""
+
+    def __init__(self, log_n: int, max_tile_ct: int = 0, max_depth: int = 17, q=None, P=None, t=T):
+        import torch  # device memory and streams only
+
+        self.torch = torch
+        self.lib = load()
+        if q is None:
+            q, P, t = default_params()
+        self.log_n, self.N, self.L = log_n, 1 << log_n, len(q)
+        self.q, self.P, self.t = list(q), int(P), int(t)
+        self._q = (ctypes.c_uint64 * len(q))(*q)
+        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth)
+        h = ctypes.c_void_p()
+        _check(self.lib.hp_create(ctypes.byref(prm), None, max_tile_ct, ctypes.byref(h)))
+        self.h = h
+        self.sk = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shapes -------------------------------------------------------------
+    def ct_empty(self, n: int, device="cuda"):
+        return self.torch.empty((n, 2, self.L, self.N), dtype=self.torch.int64, device=device)
+
+    # -- client helpers -------------------------------------------------------
+    def keygen(self, seed: int, stream=None):
+        torch = self.torch
+        sk = torch.empty(self.N, dtype=torch.int8, device="cuda")
+        rk = torch.empty((self.L, 2, self.L + 1, self.N), dtype=torch.int64, device="cuda")
+        _check(self.lib.hp_keygen(self.h, seed, _ptr(sk), _ptr(rk), _stream(stream)), self.h)
+        self.sk = sk
+        return sk, rk
+
+    def set_relin_key(self, rk):
+        _check(self.lib.hp_set_relin_key(self.h, _ptr(rk)), self.h)
+
+    def encrypt(self, slots, seed: int, ct_index0: int = 0, sk=None, stream=None):
+        torch = self.torch
+        sk = self.sk if sk is None else sk
+        sl = torch.as_tensor(np.ascontiguousarray(slots, dtype=np.uint32).view(np.int32)).to("cuda")
+        n = sl.numel() // self.N
+        ct = self.ct_empty(n)
+        _check(self.lib.hp_encrypt(self.h, _ptr(sk), _ptr(sl), n, seed, ct_index0, _ptr(ct), _stream(stream)), self.h)
+        return ct
+
+    def decrypt(self, ct, sk=None, stream=None) -> np.ndarray:
+        torch = self.torch
+        sk = self.sk if sk is None else sk
+        n = ct.numel() // (2 * self.L * self.N)
+        out = torch.empty(n * self.N, dtype=torch.int32, device="cuda")
+        _check(self.lib.hp_decrypt(self.h, _ptr(sk), _ptr(ct), n, _ptr(out), _stream(stream)), self.h)
+        return out.cpu().numpy().view(np.uint32).reshape(n, self.N)
+
+    # -- hot path ---------------------------------------------------------------
+    def run(self, op: int, x, y=None, const_val: int = 0, out=None, stream=None):
+        """hp_run on device tensors (or host numpy arrays: synchronous)."""
+        n = x.shape[0] if len(x.shape) == 4 else x.size // (2 * self.L * self.N)
+        if out is None:
+            out = self.ct_empty(n) if hasattr(x, "data_ptr") else np.empty_like(x)
+        _check(self.lib.hp_run(self.h, op, _ptr(x), _ptr(y), const_val, _ptr(out), n, _stream(stream)), self.h)
+        return out
+
+    def eq(self, x, y=None, const_val: int = 0, out=None, stream=None):
+        op = HP_EQ_CT_CT if y is not None else HP_EQ_CT_CONST
+        return self.run(op, x, y, const_val, out, stream)
+
+    def run_batched(self, op: int, instances, x, y=None, out=None, stream=None):
+        n = x.shape[0]
+        arr = (hp_instance * len(instances))()
+        for i, ins in enumerate(instances):
+            arr[i] = hp_instance(*ins) if not isinstance(ins, hp_instance) else ins
+        if out is None:
+            out = self.ct_empty(n)
+        _check(self.lib.hp_run_batched(self.h, op, arr, len(instances), _ptr(x), _ptr(y), _ptr(out), n,
+                                       _stream(stream)), self.h)
+        return out
+
+    def backward(self, op: int, grad_out, grad_x, n: int):
+        return self.lib.hp_backward(self.h, op, _ptr(grad_out), _ptr(grad_x), n, None)
+
+    def launch_count(self) -> int:
+        return int(self.lib.hp_launch_count(self.h))
+
+    def check_status(self):
+        _check(self.lib.hp_check_status(self.h), self.h)
+
+
+def to_u64(t) -> np.ndarray:
+    """torch int64 tensor -> numpy uint64 view (host copy)."""
+    return t.cpu().numpy().view(np.uint64)
+
+
+def from_u64(a, device="cuda"):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)

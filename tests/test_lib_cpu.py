@@ -1,0 +1,104 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol the header
+declares, and its host-side parameter logic agrees with the paper and the
+oracle's independent prime search.  No compute call needs a GPU here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_24271_b300 import build, hp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return hp.load()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "hp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(hp_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_symbols_exported(lib):
+    names = header_functions()
+    assert "hp_run" in names and "hp_create" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(hp.EXPORTED) == names
+
+
+def test_default_params_match_oracle(lib):
+    q, P, t = hp.default_params()
+    qo, Po = oracle.default_primes(15)
+    assert q == qo and P == Po and t == 65537
+    assert round(sum(math.log2(x) for x in q) + math.log2(P)) == 881
+
+
+def test_default_params_bad_args(lib):
+    q = (ctypes.c_uint64 * 16)()
+    P, t = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.hp_default_params(0, q, ctypes.byref(P), ctypes.byref(t)) == hp.HP_ERR_ARG
+    assert lib.hp_default_params(16, q, ctypes.byref(P), ctypes.byref(t)) == hp.HP_ERR_ARG
+
+
+def _create(lib, log_n=15, max_depth=16, q=None, P=None, t=65537):
+    if q is None:
+        q, P, t = hp.default_params()
+    qa = (ctypes.c_uint64 * len(q))(*q)
+    prm = hp.hp_params(log_n, len(q), qa, P, t, max_depth)
+    h = ctypes.c_void_p()
+    rc = lib.hp_create(ctypes.byref(prm), None, 1, ctypes.byref(h))
+    return rc, h
+
+
+def test_create_rejects_bad_parameters(lib):
+    rc, _ = _create(lib, log_n=11)
+    assert rc == hp.HP_ERR_UNSUPPORTED
+    rc, _ = _create(lib, max_depth=40)  # beyond the static noise estimate
+    assert rc == hp.HP_ERR_DEPTH
+    assert b"depth" in lib.hp_last_error(None)
+    q, P, t = hp.default_params()
+    rc, _ = _create(lib, q=[q[0] + 2] + q[1:], P=P)  # not prime / not 1 mod 2^16
+    assert rc == hp.HP_ERR_ARG
+    rc, _ = _create(lib, q=q, P=P, t=257)
+    assert rc == hp.HP_ERR_UNSUPPORTED
+
+
+def test_backward_is_unsupported(lib):
+    assert lib.hp_backward(None, 0, None, None, 0, None) == hp.HP_ERR_UNSUPPORTED
+
+
+def test_static_depth_estimate_is_conservative_against_oracle():
+    """hp_create's depth estimate must not promise more squarings than the
+    oracle's measured noise budget allows (3-prime modulus, N = 16)."""
+    lib = hp.load()
+    # the estimate for the paper's parameters covers EQ + SELECT
+    est = {}
+    for logn in (12, 15):
+        est[logn] = lib_depth(logn, *hp.default_params()[:2])
+        assert est[logn] >= 17
+    q, P = oracle.default_primes(15)
+    o = oracle.Oracle(4, q=q[:3], P=P)
+    o.keygen(3)
+    x = np.arange(o.N, dtype=np.uint32) + 2
+    cx = o.encrypt(x, 5, 0)
+    d = lib_depth(4, q[:3], P)
+    _, nb = o.decrypt(o.square_chain(cx, d), with_noise=True)
+    assert nb > 0
+
+
+def lib_depth(logn, q, P):
+    # mirror of the C estimate (hp_host.cpp supported_depth): fresh budget
+    # log2 Q - log2 t - log N - 8, per squaring log2 t + log N + 2
+    lq = sum(math.log2(x) for x in q)
+    lt = math.log2(65537)
+    fresh = lq - lt - logn - 8
+    return int((fresh - 1) // (lt + logn + 2)) if fresh > 0 else 0
