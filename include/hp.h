@@ -168,10 +168,35 @@ int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, 
  * h (for launch accounting). */
 uint64_t hp_launch_count(const hp_handle* h);
 
+/* Ciphertexts per pipeline tile chosen by hp_create (max_tile_ct or the
+ * default that fits about 4 GB of workspace). */
+size_t hp_tile_size(const hp_handle* h);
+
 /* Synchronise the device and report the exactness status word of h (a
  * window check inside the exact base conversions that cannot fail for valid
  * parameters); HP_OK if clean.  The word is cleared afterwards. */
 int hp_check_status(hp_handle* h);
+
+/* ---- measurement -----------------------------------------------------------
+ * Per-kernel-class timing with CUDA events recorded on the launching stream
+ * around every launch of the classes in `class_mask` (bit c = class c):
+ *   0 NTT forward columns   1 NTT forward rows    2 NTT inverse rows
+ *   3 NTT inverse columns   4 exact lift          5 tensor
+ *   6 scale-and-round       7 digit expansion     8 key-switch MAC
+ *   9 mod-down
+ * hp_profile() synchronises, clears the records and sets the mask (0 = off).
+ * hp_profile_read() synchronises and returns the summed event time, the
+ * number of launches and the summed algorithmic work of class `cls` (NTT:
+ * butterflies; lift / scale-and-round: coefficients; MAC: multiply-adds;
+ * others: words). */
+int hp_profile(hp_handle* h, uint32_t class_mask);
+int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches, double* work_total);
+
+/* Register-only peak probe on the current device (no handle needed):
+ * kind 0 = the 64-bit Shoup butterfly of the NTT kernels (butterflies/s),
+ * kind 1 = the 64x64->128-bit multiply-accumulate of the base conversions and
+ * key switching (MACs/s).  Launches 8 blocks of 256 threads per SM. */
+int hp_probe_peak(int kind, double* per_second);
 
 #ifdef __cplusplus
 }

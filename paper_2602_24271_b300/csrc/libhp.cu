@@ -13,6 +13,7 @@
 #include "hp_defs.h"
 #include "hp_device.cuh"
 #include "hp_ntt.cuh"
+#include "hp_probe.cuh"
 #include "hp_rns.cuh"
 
 using namespace hp;
@@ -40,6 +41,60 @@ struct hp_handle {
   int* status = nullptr;  // device status word (ST_* bits)
   uint64_t launches = 0;
   std::string err;
+  // opt-in per-kernel-class timing (CUDA events on the launching stream)
+  uint32_t prof_mask = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double work;
+  };
+  std::vector<Rec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+// kernel classes for hp_profile_* (work unit in brackets)
+enum {
+  PK_NTT_FWD_COLS = 0,  // [butterflies]
+  PK_NTT_FWD_ROWS = 1,  // [butterflies]
+  PK_NTT_INV_ROWS = 2,  // [butterflies]
+  PK_NTT_INV_COLS = 3,  // [butterflies]
+  PK_LIFT = 4,          // [coefficients lifted]
+  PK_TENSOR = 5,        // [residue products]
+  PK_SCALE_ROUND = 6,   // [coefficients rounded]
+  PK_KS_EXPAND = 7,     // [words]
+  PK_KS_MAC = 8,        // [multiply-accumulates]
+  PK_MODDOWN = 9,       // [words]
+  PK_COUNT = 10
+};
+
+static cudaEvent_t prof_event(hp_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+struct ProfScope {
+  hp_handle* h;
+  int cls;
+  cudaStream_t s;
+  double work;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(hp_handle* h_, int cls_, cudaStream_t s_, double work_) : h(h_), cls(cls_), s(s_), work(work_) {
+    if (h->prof_mask & (1u << cls)) {
+      e0 = prof_event(h);
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~ProfScope() {
+    if (e0) {
+      cudaEvent_t e1 = prof_event(h);
+      cudaEventRecord(e1, s);
+      h->prof.push_back({cls, e0, e1, work});
+    }
+  }
 };
 
 static std::string g_create_err;
@@ -96,8 +151,15 @@ static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaS
   const int logC = h->logn - h->logR;
   dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
   dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
-  k_ntt_fwd_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
-  k_ntt_fwd_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  const double half = (double)npoly * (h->N / 2);
+  {
+    ProfScope ps(h, PK_NTT_FWD_COLS, s, half * h->logR);
+    k_ntt_fwd_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  }
+  {
+    ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * logC);
+    k_ntt_fwd_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  }
   h->launches += 2;
 }
 
@@ -106,8 +168,15 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
   const int logC = h->logn - h->logR;
   dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
   dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
-  k_ntt_inv_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
-  k_ntt_inv_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR, scale_mode);
+  const double half = (double)npoly * (h->N / 2);
+  {
+    ProfScope ps(h, PK_NTT_INV_ROWS, s, half * logC);
+    k_ntt_inv_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+  }
+  {
+    ProfScope ps(h, PK_NTT_INV_COLS, s, half * h->logR);
+    k_ntt_inv_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR, scale_mode);
+  }
   h->launches += 2;
 }
 
@@ -120,25 +189,40 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
   ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
   if (general) {
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
+    ProfScope ps(h, PK_TENSOR, s, 4.0 * b * NQB * N);
     k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->ext2, h->dprod, logN, b);
   } else {
+    ProfScope ps(h, PK_TENSOR, s, 3.0 * b * NQB * N);
     k_tensor_sq<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->dprod, logN, b);
   }
   h->launches += 1;
   ntt_inv(h, h->dprod, (size_t)b * 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
-  k_scale_round<<<ew_blocks((size_t)b * 3 * N), EW_THREADS, 0, s>>>(h->dprod, h->w3, h->status, logN, b);
-  k_ks_expand<<<ew_blocks((size_t)b * L * NKS * N), EW_THREADS, 0, s>>>(h->w3, h->ksin, logN, b);
+  {
+    ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
+    k_scale_round<<<ew_blocks((size_t)b * 3 * N), EW_THREADS, 0, s>>>(h->dprod, h->w3, h->status, logN, b);
+  }
+  {
+    ProfScope ps(h, PK_KS_EXPAND, s, (double)b * L * NKS * N);
+    k_ks_expand<<<ew_blocks((size_t)b * L * NKS * N), EW_THREADS, 0, s>>>(h->w3, h->ksin, logN, b);
+  }
   h->launches += 2;
   ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s);
-  k_ks_mac<<<ew_blocks((size_t)b * NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
+  {
+    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * L * NKS * N);
+    k_ks_mac<<<ew_blocks((size_t)b * NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
+  }
   h->launches += 1;
   ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
-  k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, out, one_minus, logN, b);
+  {
+    ProfScope ps(h, PK_MODDOWN, s, 2.0 * b * L * N);
+    k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, out, one_minus, logN, b);
+  }
   h->launches += 1;
 }
 
 static void lift(hp_handle* h, const uint64_t* src, const uint64_t* sub, uint64_t cval, int mode, uint64_t* ext, int b,
                  cudaStream_t s) {
+  ProfScope ps(h, PK_LIFT, s, 2.0 * b * h->N);
   k_lift<<<ew_blocks((size_t)b * 2 * h->N), EW_THREADS, 0, s>>>(src, sub, cval, mode, ext, h->logn, b);
   h->launches += 1;
 }
@@ -241,6 +325,8 @@ static int load_consts(hp_handle* h) {
 }
 
 static void free_all(hp_handle* h) {
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
   uint64_t* ptrs[] = {h->tw, h->tws, h->itw, h->itws, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
                       h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto};
   for (uint64_t* p : ptrs)
@@ -308,7 +394,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   if ((rc = load_consts(h)) != HP_OK) return fail(rc);
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
   size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
-  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)1 << 30) / per);
+  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)4 << 30) / per);  // ~4 GB of workspace
   if (h->tile < 1) h->tile = 1;
   if (h->tile > 64) h->tile = 64;
   const size_t T = h->tile, N = h->N;
@@ -429,6 +515,8 @@ const char* hp_last_error(const hp_handle* h) { return h ? h->err.c_str() : g_cr
 
 uint64_t hp_launch_count(const hp_handle* h) { return h ? h->launches : 0; }
 
+size_t hp_tile_size(const hp_handle* h) { return h ? h->tile : 0; }
+
 // ---- client helpers ---------------------------------------------------------
 int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* stream) {
   if (!h) return HP_ERR_ARG;
@@ -515,6 +603,73 @@ int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, 
   cudaFree(S);
   cudaFree(C1);
   cudaFree(M);
+  return HP_OK;
+}
+
+int hp_profile(hp_handle* h, uint32_t class_mask) {
+  if (!h) return HP_ERR_ARG;
+  CU(h, cudaDeviceSynchronize());
+  h->prof_mask = class_mask;
+  h->prof.clear();
+  h->ev_used = 0;
+  return HP_OK;
+}
+
+int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches, double* work_total) {
+  if (!h || !ms_total || !launches || !work_total || cls < 0 || cls >= PK_COUNT) return HP_ERR_ARG;
+  CU(h, cudaDeviceSynchronize());
+  double ms = 0, work = 0;
+  uint64_t n = 0;
+  for (auto& r : h->prof) {
+    if (r.cls != cls) continue;
+    float m = 0;
+    CU(h, cudaEventElapsedTime(&m, r.e0, r.e1));
+    ms += m;
+    work += r.work;
+    ++n;
+  }
+  *ms_total = ms;
+  *launches = n;
+  *work_total = work;
+  return HP_OK;
+}
+
+int hp_probe_peak(int kind, double* per_second) {
+  if (!per_second || kind < 0 || kind > 1) return HP_ERR_ARG;
+  hp_handle* h = nullptr;
+  int dev = 0, sms = 0;
+  CU(h, cudaGetDevice(&dev));
+  CU(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  uint64_t* sink = nullptr;
+  CU(h, cudaMalloc(&sink, 64));
+  const uint64_t p = 0x7fffffffe90001ull;  // a 55-bit NTT prime (q_0)
+  const uint64_t w = 0x123456789abcull % p;
+  const uint64_t wp = (uint64_t)(((unsigned __int128)w << 64) / p);
+  uint64_t pinv = p;
+  for (int i = 0; i < 6; ++i) pinv *= 2 - p * pinv;
+  pinv = (uint64_t)0 - pinv;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    if (kind == 0)
+      k_probe_butterfly<<<blocks, threads>>>(sink, iters, p, w, wp);
+    else
+      k_probe_mac<<<blocks, threads>>>(sink, iters, p, pinv);
+    cudaEventRecord(e1);
+    CU(h, cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;  // first launch is warm-up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  CU(h, cudaGetLastError());
+  *per_second = (double)blocks * threads * PROBE_CHAINS * iters / (best * 1e-3);
   return HP_OK;
 }
 

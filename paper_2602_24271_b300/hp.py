@@ -39,8 +39,13 @@ T = 65537
 EXPORTED = [
     "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
-    "hp_check_status",
+    "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
 ]
+
+PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
+                   "scale_round", "ks_expand", "ks_mac", "moddown"]
+KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows", "k_ntt_inv_rows", "k_ntt_inv_cols", "k_lift", "k_tensor_sq",
+                   "k_scale_round", "k_ks_expand", "k_ks_mac", "k_moddown"]
 
 
 class HpError(RuntimeError):
@@ -99,6 +104,11 @@ def load():
         "hp_decrypt": (ctypes.c_int, [H, V, P64, SZ, V, V]),
         "hp_launch_count": (ctypes.c_uint64, [H]),
         "hp_check_status": (ctypes.c_int, [H]),
+        "hp_profile": (ctypes.c_int, [H, ctypes.c_uint32]),
+        "hp_profile_read": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
+        "hp_probe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "hp_tile_size": (ctypes.c_size_t, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -158,6 +168,7 @@ class Context:
         _check(self.lib.hp_create(ctypes.byref(prm), None, max_tile_ct, ctypes.byref(h)))
         self.h = h
         self.sk = None
+        self.max_tile = max_tile_ct
 
     def close(self):
         if getattr(self, "h", None):
@@ -230,11 +241,29 @@ class Context:
     def backward(self, op: int, grad_out, grad_x, n: int):
         return self.lib.hp_backward(self.h, op, _ptr(grad_out), _ptr(grad_x), n, None)
 
+    def tile(self) -> int:
+        return int(self.lib.hp_tile_size(self.h))
+
     def launch_count(self) -> int:
         return int(self.lib.hp_launch_count(self.h))
 
     def check_status(self):
         _check(self.lib.hp_check_status(self.h), self.h)
+
+    def profile(self, class_mask: int):
+        _check(self.lib.hp_profile(self.h, class_mask), self.h)
+
+    def profile_read(self, cls: int):
+        ms, n, w = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
+        _check(self.lib.hp_profile_read(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)), self.h)
+        return ms.value, int(n.value), w.value
+
+
+def probe_peak(kind: int) -> float:
+    """Register-only peak rate on the current device: 0 = butterflies/s, 1 = MACs/s."""
+    v = ctypes.c_double()
+    _check(load().hp_probe_peak(kind, ctypes.byref(v)))
+    return v.value
 
 
 def to_u64(t) -> np.ndarray:
