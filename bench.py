@@ -127,32 +127,34 @@ def load_traffic(kernel: str):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_sample(squarings_timed: int = 2):
-    """Time the oracle on one ciphertext pair of the workload (N = 32768): the
-    difference and `squarings_timed` of the 16 squarings, extrapolated to one
-    full EQ.  Returns (slots/s, seconds of timed CPU work, description)."""
-    import numpy as np
+class OracleSample:
+    """One ciphertext pair of the workload (N = 32768) on the CPU oracle: keys
+    and encryptions are made once; `time(k)` times the difference, k of the 16
+    squarings and "1 -", extrapolated to one full EQ."""
 
-    import oracle
-    from paper_2602_24271_b300.inputs import eq_pair_columns
+    def __init__(self):
+        import oracle
+        from paper_2602_24271_b300.inputs import eq_pair_columns
 
-    o = oracle.Oracle(LOGN)
-    o.keygen(SEED_KEY)
-    x, y = eq_pair_columns(o.N, seed=SEED_DATA)
-    cx, cy = o.encrypt(x, 7, 0), o.encrypt(y, 7, 1)
-    t0 = time.perf_counter()
-    d = o.sub(cx, cy)
-    t1 = time.perf_counter()
-    for _ in range(squarings_timed):
-        d = o.mul_relin(d, d)
-    t2 = time.perf_counter()
-    o.one_minus(d)
-    t3 = time.perf_counter()
-    per_sq = (t2 - t1) / squarings_timed
-    per_eq = (t1 - t0) + 16 * per_sq + (t3 - t2)
-    desc = ("1 ciphertext pair at N=32768 (32768 slots): difference, %d of the 16 squarings+relinearisations and "
-            "'1 -' timed single-threaded; squarings extrapolated x%d" % (squarings_timed, 16 // squarings_timed))
-    return o.N / per_eq, t3 - t0, desc
+        self.o = oracle.Oracle(LOGN)
+        self.o.keygen(SEED_KEY)
+        x, y = eq_pair_columns(self.o.N, seed=SEED_DATA)
+        self.cx, self.cy = self.o.encrypt(x, 7, 0), self.o.encrypt(y, 7, 1)
+
+    def time(self, squarings_timed: int):
+        o = self.o
+        t0 = time.perf_counter()
+        d = o.sub(self.cx, self.cy)
+        t1 = time.perf_counter()
+        for _ in range(squarings_timed):
+            d = o.mul_relin(d, d)
+        t2 = time.perf_counter()
+        o.one_minus(d)
+        t3 = time.perf_counter()
+        per_eq = (t1 - t0) + 16 * (t2 - t1) / squarings_timed + (t3 - t2)
+        desc = ("1 ciphertext pair at N=32768 (32768 slots): difference, %d of the 16 squarings+relinearisations "
+                "and '1 -' timed single-threaded; squarings extrapolated to 16" % squarings_timed)
+        return o.N / per_eq, t3 - t0, desc
 
 
 def run_reference(args):
@@ -160,14 +162,13 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args.config)
-    times = []
-    import oracle  # noqa: F401  (test infrastructure: the reference arm is the oracle)
-
+    sample = OracleSample()
+    vals, desc = [], ""
     for i in range(args.warmup + args.steps):
-        v, secs, desc = oracle_sample(squarings_timed=1)
+        v, secs, desc = sample.time(1)
         if i >= args.warmup:
-            times.append(v)
-    value = statistics.mean(times)
+            vals.append(v)
+    value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -314,7 +315,7 @@ def run_libhp(args):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:
-        v, secs, desc = oracle_sample(8)
+        v, secs, desc = OracleSample().time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
     if rank == 0:
