@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-region", action="store_true",
+                    help="after warm-up, run one extra step between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -239,6 +241,13 @@ def run_libhp(args):
         step()
     torch.cuda.synchronize()
 
+    if args.ncu_region:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+
     # ---- timed region ----
     ctx.profile(1 << dom)
     if dist:
@@ -298,6 +307,8 @@ def run_libhp(args):
     roof["avg_launch_ms"] = avg_ms
     roof["share_of_step"] = shares[dom] / tot if tot else None
     roof["peak_source"] = "register-only probe of the same arithmetic (hp_probe_peak), measured in this run"
+    roof["probe_butterfly_per_s"] = hp.probe_peak(0)
+    roof["probe_mac_per_s"] = hp.probe_peak(1)
     roof["traffic"] = load_traffic(kernel)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -142,9 +142,10 @@ __global__ void k_dec_round(const uint64_t* ct, const uint64_t* C1S, uint64_t* M
   M[gid] = m;
 }
 
+// decoded slots: forward-transform output (in [0, 8t)) reduced mod t
 __global__ void k_u64_to_u32(const uint64_t* in, uint32_t* out, size_t n) {
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid < n) out[gid] = (uint32_t)in[gid];
+  if (gid < n) out[gid] = (uint32_t)(in[gid] % cK.p[ID_T]);
 }
 
 // Montgomery form of the relinearisation key after its forward transform:

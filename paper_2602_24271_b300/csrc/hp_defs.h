@@ -27,18 +27,23 @@ struct Consts {
   uint64_t p[NPRIME];     // moduli by id
   uint64_t pinv[NPRIME];  // -p^{-1} mod 2^64 (Montgomery)
   uint64_t r2[NPRIME];    // 2^128 mod p (to enter Montgomery form)
+  uint64_t pbar[NPRIME];  // floor(2^64 / p): Shoup companion of 1 (full reduction of any word)
   // exact centred conversion Q -> B
   uint64_t qhatinv[L], qhatinv_s[L];  // [(Q/q_i)^{-1}]_{q_i}
   uint64_t qhat[L], qhat_s[L];        // [Q/q_i]_{q_i} (rebuilds residues from y_i in the fallback)
   uint64_t om_hi[L], om_lo[L];        // floor(2^128 / q_i) split in 64-bit halves
   uint64_t MQB[L][K];                 // [(Q/q_i) 2^64]_{b_k}
   uint64_t negQB[K];                  // [-Q 2^64]_{b_k}
+  uint32_t MQB_l[L][K], MQB_h[L][K];  // MQB in 28-bit limbs: low 28 bits, the rest
+  uint32_t negQB_l[K], negQB_h[K];
   uint64_t QmodB[K];                  // [Q]_{b_k}
   // exact centred conversion B -> Q
   uint64_t QBinv[K], QBinv_s[K];  // [Q^{-1} (B/b_k)^{-1}]_{b_k}
   uint64_t omb_hi[K], omb_lo[K];  // floor(2^128 / b_k)
   uint64_t MBQ[K][L];             // [(B/b_k) 2^64]_{q_i}
   uint64_t negBQ[L];              // [-B 2^64]_{q_i}
+  uint32_t MBQ_l[K][L], MBQ_h[K][L];  // MBQ in 28-bit limbs
+  uint32_t negBQ_l[L], negBQ_h[L];
   // mixed-radix (Garner) comparison with (Q-1)/2, the exact fallback
   uint64_t mrc_inv[L][L], mrc_inv_s[L][L];  // [q_j^{-1}]_{q_i} for j < i
   uint64_t half_digit[L];                   // mixed-radix digits of (Q-1)/2

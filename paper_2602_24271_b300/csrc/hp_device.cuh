@@ -52,6 +52,34 @@ HPD uint64_t mont_mul_lazy(uint64_t a, uint64_t b, uint64_t p, uint64_t pinv) {
   x.hi = __umul64hi(a, b);
   return redc_lazy(x, p, pinv);
 }
+// Multiply-accumulate of 56-bit operands in 28-bit limbs: y = yh 2^28 + yl,
+// m = mh 2^28 + ml; a0 += yl ml, a1 += yl mh + yh ml, a2 += yh mh, each a
+// single 32x32+64 multiply-add.  Up to 17 terms stay below 2^61 per word.
+struct Acc3 {
+  uint64_t a0, a1, a2;
+};
+HPD void acc3_zero(Acc3& a) { a.a0 = a.a1 = a.a2 = 0; }
+HPD void acc3_mac(Acc3& a, uint32_t yl, uint32_t yh, uint32_t ml, uint32_t mh) {
+  a.a0 += (uint64_t)yl * ml;
+  a.a1 += (uint64_t)yl * mh;
+  a.a1 += (uint64_t)yh * ml;
+  a.a2 += (uint64_t)yh * mh;
+}
+// a0 + a1 2^28 + a2 2^56 as a 128-bit value
+HPD Acc acc3_fold(const Acc3& a) {
+  Acc r;
+  const uint64_t t = a.a1 << 28, u = a.a2 << 56;
+  uint64_t lo = a.a0 + t;
+  uint64_t c = lo < t ? 1 : 0;
+  lo += u;
+  c += lo < u ? 1 : 0;
+  r.lo = lo;
+  r.hi = (a.a1 >> 36) + (a.a2 >> 8) + c;
+  return r;
+}
+HPD uint32_t lo28(uint64_t y) { return (uint32_t)(y & 0xFFFFFFFull); }
+HPD uint32_t hi28(uint64_t y) { return (uint32_t)(y >> 28); }
+
 HPD uint64_t add_mod(uint64_t a, uint64_t b, uint64_t p) { return csub(a + b, p); }
 HPD uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t p) { return a >= b ? a - b : a + p - b; }
 

@@ -150,6 +150,7 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->p[i] = all[i];
     C->pinv[i] = neg_inv64(all[i]);
     C->r2[i] = h_mulmod(to_mont(1, all[i]), to_mont(1, all[i]), all[i]);  // 2^128 mod p
+    C->pbar[i] = ~0ull / all[i];
   }
   // Q -> B
   for (int i = 0; i < L; ++i) {
@@ -209,6 +210,23 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->MQt[i] = to_mont(prod_mod(q, L, i, t), t);
   }
   C->negQt = to_mont((t - Qt) % t, t);
+  // 28-bit limb splits of the conversion matrices (device multiply-accumulate)
+  const uint64_t M28 = (1ULL << 28) - 1;
+  for (int i = 0; i < L; ++i)
+    for (int k = 0; k < K; ++k) {
+      C->MQB_l[i][k] = (uint32_t)(C->MQB[i][k] & M28);
+      C->MQB_h[i][k] = (uint32_t)(C->MQB[i][k] >> 28);
+      C->MBQ_l[k][i] = (uint32_t)(C->MBQ[k][i] & M28);
+      C->MBQ_h[k][i] = (uint32_t)(C->MBQ[k][i] >> 28);
+    }
+  for (int k = 0; k < K; ++k) {
+    C->negQB_l[k] = (uint32_t)(C->negQB[k] & M28);
+    C->negQB_h[k] = (uint32_t)(C->negQB[k] >> 28);
+  }
+  for (int i = 0; i < L; ++i) {
+    C->negBQ_l[i] = (uint32_t)(C->negBQ[i] & M28);
+    C->negBQ_h[i] = (uint32_t)(C->negBQ[i] >> 28);
+  }
   C->Qinv_t = h_invmod(Qt, t);
   return 0;
 }

@@ -7,19 +7,32 @@
 // (Gentleman-Sande) undoes the stages in reverse order with psi^{-brv(.)} and
 // scales by N^{-1} (times a per-launch constant).
 //
-// N = R x C (R = 2^logR rows, C = 2^logC columns, element j = r C + k).  Stages
-// s < logR pair elements of the same column; stages s >= logR pair elements of
-// the same row.  Each pass loads one 2048-word tile into shared memory, runs
-// its stages with one barrier per stage, and writes the tile back.  Lazy
-// ranges (Harvey): forward values stay in [0, 4p), inverse values in [0, 2p);
-// the last pass of each direction returns canonical residues.
+// Decomposition: N = R x C (j = r C + k).  Stages s < logR pair elements of
+// one column, stages s >= logR elements of one row.  Each pass is one kernel
+// over a 2048-word tile; every thread keeps 16 residues in registers and runs
+// 4 stages as a radix-16 block (index arithmetic once per element, one twiddle
+// load per butterfly group), then the tile is exchanged once through shared
+// memory for the remaining stages of the pass.
+//
+// Ranges.  The twiddle product uses a Shoup quotient from three 32-bit partial
+// products, which is at most 2 below the exact one, so W Y mod p is returned
+// in [0, 4p) for any 64-bit Y.  Forward (CT) butterflies then need no
+// correction at all: (X + V, X - V + 4p) grows the bound by 4p per stage, at
+// most 61p < 2^62 after 15 stages for every prime here (p < 2^56); the last
+// forward pass brings it to [0, 8p) with conditional subtractions of 32p,
+// 16p, 8p: every consumer of the forward transform (Montgomery products and
+// multiply-accumulates, whose sums stay below p 2^64) accepts that range.
+// Inverse (GS) butterflies keep every value in [0, 4p): (X + Y) - 4p when
+// >= 4p, and W (X - Y + 4p) in [0, 4p).  The integer multiplier (FMA-heavy
+// pipe) is the bottleneck on this GPU, so range control uses only
+// compare/subtract (ALU pipe) instructions.
 #pragma once
 #include "hp_device.cuh"
 
 namespace hp {
 
 constexpr int NTT_TILE = 2048;
-constexpr int NTT_THREADS = 256;
+constexpr int NTT_THREADS = 128;  // 2048 words / 16 per thread
 
 // Which prime each polynomial of a batch uses: polynomial index p has
 // position r = p % period; id = (r == period-1 && last_id >= 0) ? last_id : base + r.
@@ -32,165 +45,269 @@ struct PolyMap {
 };
 
 struct NttTabs {
-  const uint64_t* tw;    // [NPRIME][N] psi^{brv(j)}
-  const uint64_t* tws;   // Shoup companions
-  const uint64_t* itw;   // [NPRIME][N] psi^{-brv(j)}
-  const uint64_t* itws;  // Shoup companions
-  const uint64_t* scale; // [NSCALE][NPRIME][2] (value, Shoup)
+  const ulonglong2* tw;   // [NPRIME][N] (psi^{brv(j)}, Shoup companion)
+  const ulonglong2* itw;  // [NPRIME][N] (psi^{-brv(j)}, Shoup companion)
+  const uint64_t* scale;  // [NSCALE][NPRIME][2] (value, Shoup)
 };
 enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, NSCALE = 3 };
 
-// ---- forward, columns (stages 0 .. logR-1) ----
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* data, PolyMap map, NttTabs T, int logN,
-                                                              int logR) {
+// Optional fused load of the forward column pass: polynomial (b, i, j) of the
+// key-switching batch is digit i of ciphertext b reduced modulo target prime
+// j, read from w3[b][2][i][.] (the digits [d2]_{q_i}).
+struct DigitSrc {
+  const uint64_t* w3;  // nullptr: the pass transforms `data` in place
+};
+
+// ---- modular helpers for the transform ------------------------------------------
+struct PForm {
+  uint64_t p, np;  // p and 2^64 - p
+};
+HPD PForm pform(int id) {
+  PForm f;
+  f.p = cK.p[id];
+  f.np = 0 - f.p;
+  return f;
+}
+// W Y mod p in [0, 4p) for any 64-bit Y; wp = floor(W 2^64 / p).
+// q = yh wh + hi(yh wl) + hi(yl wh) drops the low partial product and two
+// carries, so floor(Y wp / 2^64) - 2 <= q <= floor(Y wp / 2^64);
+// Y W - q p = Y W + q (2^64 - p) is then evaluated mod 2^64.
+HPD uint64_t mul_shoup4(uint64_t y, uint64_t w, uint64_t wp, const PForm& f) {
+  const uint32_t yl = (uint32_t)y, yh = (uint32_t)(y >> 32);
+  const uint32_t wl = (uint32_t)wp, wh = (uint32_t)(wp >> 32);
+  const uint64_t q = (uint64_t)yh * wh + __umulhi(yh, wl) + __umulhi(yl, wh);
+  return y * w + q * f.np;
+}
+// x in [0, 64p) -> [0, 8p) by conditional subtractions (no multiplications)
+HPD uint64_t red64to8(uint64_t x, uint64_t p) {
+  x = csub(x, 32 * p);
+  x = csub(x, 16 * p);
+  return csub(x, 8 * p);
+}
+
+// ---- register blocks --------------------------------------------------------
+// x[u] holds a_{base + (u << (logN - s0 - A))}, u < 2^A; base has zero bits in
+// the u positions.  Runs forward stages s0 .. s0 + A - 1 in registers.
+template <int A>
+HPD void fwd_block(uint64_t (&x)[1 << A], uint32_t base, int s0, int logN, const ulonglong2* __restrict__ tw,
+                   const PForm& f) {
+  const uint64_t p4 = 4 * f.p;
+#pragma unroll
+  for (int l = 0; l < A; ++l) {
+    const int s = s0 + l;
+    const uint32_t tb = (1u << s) + (base >> (logN - s));
+#pragma unroll
+    for (int g = 0; g < (1 << l); ++g) {
+      const ulonglong2 W = __ldg(tw + tb + g);
+#pragma unroll
+      for (int o = 0; o < (1 << (A - l - 1)); ++o) {
+        const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
+        const uint64_t X = x[u];
+        const uint64_t V = mul_shoup4(x[v], W.x, W.y, f);
+        x[u] = X + V;
+        x[v] = X - V + p4;
+      }
+    }
+  }
+}
+
+// Inverse stages s0 + A - 1 .. s0 on the same element set; values in [0, 4p).
+template <int A>
+HPD void inv_block(uint64_t (&x)[1 << A], uint32_t base, int s0, int logN, const ulonglong2* __restrict__ itw,
+                   const PForm& f) {
+  const uint64_t p4 = 4 * f.p;
+#pragma unroll
+  for (int l = A - 1; l >= 0; --l) {
+    const int s = s0 + l;
+    const uint32_t tb = (1u << s) + (base >> (logN - s));
+#pragma unroll
+    for (int g = 0; g < (1 << l); ++g) {
+      const ulonglong2 W = __ldg(itw + tb + g);
+#pragma unroll
+      for (int o = 0; o < (1 << (A - l - 1)); ++o) {
+        const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
+        const uint64_t X = x[u], Y = x[v];
+        x[u] = csub(X + Y, p4);
+        x[v] = mul_shoup4(X - Y + p4, W.x, W.y, f);
+      }
+    }
+  }
+}
+
+// ---- forward, columns (stages 0 .. LOGR-1) -------------------------------------
+// Block: COLS = 2048 / R adjacent columns.  Step A: thread (k, rb) holds rows
+// rb + 16-stride (stages 0..3); step B: groups of 2^(LOGR-4) consecutive rows.
+template <int LOGR, int LOGC>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+                                                              DigitSrc dig) {
+  constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
+  constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
   __shared__ uint64_t s[NTT_TILE];
-  const int N = 1 << logN, logC = logN - logR;
-  const int logCOLS = 11 - logR;  // NTT_TILE = 2^11 = R * COLS
-  const int COLS = 1 << logCOLS;
-  const int poly = blockIdx.y, k0 = blockIdx.x << logCOLS;
+  const int t = threadIdx.x, k = t % COLS, rb = t / COLS;
+  const int poly = blockIdx.y, k0 = blockIdx.x * COLS;
   const int id = map.id(poly);
-  const uint64_t p = cK.p[id], p2 = 2 * p;
+  const PForm f = pform(id);
+  const uint64_t p = f.p;
+  const ulonglong2* tw = T.tw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
-  const uint64_t* tw = T.tw + (size_t)id * N;
-  const uint64_t* tws = T.tws + (size_t)id * N;
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) {
-    int r = e >> logCOLS, c = e & (COLS - 1);
-    s[e] = a[((size_t)r << logC) + k0 + c];
+  const uint64_t* src = a;
+  bool reduce = false;
+  if (dig.w3) {  // key-switching digits: poly = (b * L + i) * NKS + j
+    const int b = poly / (L * NKS), i = (poly / NKS) % L;
+    src = dig.w3 + ((size_t)(b * 3 + 2) * L + i) * N;
+    reduce = true;
   }
+  uint64_t x[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    uint64_t v = src[(size_t)(rb + u * RB) * C + k0 + k];
+    x[u] = reduce ? csub(v, p) : v;  // digit < q_i < 2 p_j
+  }
+  fwd_block<4>(x, (uint32_t)(rb * C + k0 + k), 0, logN, tw, f);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) s[(rb + u * RB) * COLS + k] = x[u];
   __syncthreads();
-  for (int st = 0; st < logR; ++st) {
-    const int logt = logR - st - 1;  // pair distance in rows
-    for (int b = threadIdx.x; b < NTT_TILE / 2; b += NTT_THREADS) {
-      int c = b & (COLS - 1), bb = b >> logCOLS;
-      int g = bb >> logt, o = bb & ((1 << logt) - 1);
-      int r = (g << (logt + 1)) + o;
-      int ti = (1 << st) + g;
-      uint64_t W = tw[ti], Wp = tws[ti];
-      int i0 = (r << logCOLS) + c, i1 = i0 + (1 << (logt + logCOLS));
-      uint64_t X = s[i0], Y = s[i1];
-      X = X >= p2 ? X - p2 : X;
-      uint64_t V = mul_shoup_lazy(Y, W, Wp, p);
-      s[i0] = X + V;
-      s[i1] = X - V + p2;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) {
-    int r = e >> logCOLS, c = e & (COLS - 1);
-    a[((size_t)r << logC) + k0 + c] = s[e];
+#pragma unroll
+  for (int m = 0; m < (16 >> A2); ++m) {
+    const int g = rb + m * RB;  // group of 2^A2 consecutive rows, g < 16
+    uint64_t y[1 << A2];
+#pragma unroll
+    for (int u = 0; u < (1 << A2); ++u) y[u] = s[((g << A2) + u) * COLS + k];
+    fwd_block<A2>(y, (uint32_t)(((g << A2) * C) + k0 + k), 4, logN, tw, f);
+#pragma unroll
+    for (int u = 0; u < (1 << A2); ++u) a[(size_t)((g << A2) + u) * C + k0 + k] = y[u];
   }
 }
 
-// ---- forward, rows (stages logR .. logN-1); canonical output ----
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* data, PolyMap map, NttTabs T, int logN,
-                                                              int logR) {
-  __shared__ uint64_t s[NTT_TILE];
-  const int N = 1 << logN, logC = logN - logR;
-  const int logROWS = 11 - logC;
-  const int poly = blockIdx.y, row0 = blockIdx.x << logROWS;
+// ---- forward, rows (stages LOGR .. logN-1); output in [0, 8p) ----------------------
+// Block: ROWS = 2048 / C rows; padded shared rows (one word per 16) avoid bank
+// conflicts of the contiguous groups of step B.
+template <int LOGR, int LOGC>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restrict__ data, PolyMap map, NttTabs T) {
+  constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
+  constexpr int ROWS = NTT_TILE >> LOGC, TPR = C / 16, B2 = LOGC - 4, PADC = C + C / 16;
+  __shared__ uint64_t s[ROWS * PADC];
+  const int t = threadIdx.x, r = t / TPR, kb = t % TPR;
+  const int poly = blockIdx.y, row0 = blockIdx.x * ROWS, row = row0 + r;
   const int id = map.id(poly);
-  const uint64_t p = cK.p[id], p2 = 2 * p;
-  uint64_t* a = data + (size_t)poly * N + ((size_t)row0 << logC);
-  const uint64_t* tw = T.tw + (size_t)id * N;
-  const uint64_t* tws = T.tws + (size_t)id * N;
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) s[e] = a[e];
-  __syncthreads();
-  for (int st = logR; st < logN; ++st) {
-    const int logt = logN - st - 1;  // pair distance in elements (< C)
-    for (int b = threadIdx.x; b < NTT_TILE / 2; b += NTT_THREADS) {
-      int rr = b >> (logC - 1), bb = b & ((1 << (logC - 1)) - 1);
-      int g = bb >> logt, o = bb & ((1 << logt) - 1);
-      int k = (g << (logt + 1)) + o;
-      int ti = (1 << st) + (((row0 + rr) << (logC - logt - 1)) + g);
-      uint64_t W = tw[ti], Wp = tws[ti];
-      int i0 = (rr << logC) + k, i1 = i0 + (1 << logt);
-      uint64_t X = s[i0], Y = s[i1];
-      X = X >= p2 ? X - p2 : X;
-      uint64_t V = mul_shoup_lazy(Y, W, Wp, p);
-      s[i0] = X + V;
-      s[i1] = X - V + p2;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) {
-    uint64_t x = s[e];
-    x = x >= p2 ? x - p2 : x;
-    a[e] = csub(x, p);
-  }
-}
-
-// ---- inverse, rows (stages logN-1 .. logR); input in [0, 2p) ----
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* data, PolyMap map, NttTabs T, int logN,
-                                                              int logR) {
-  __shared__ uint64_t s[NTT_TILE];
-  const int N = 1 << logN, logC = logN - logR;
-  const int logROWS = 11 - logC;
-  const int poly = blockIdx.y, row0 = blockIdx.x << logROWS;
-  const int id = map.id(poly);
-  const uint64_t p = cK.p[id], p2 = 2 * p;
-  uint64_t* a = data + (size_t)poly * N + ((size_t)row0 << logC);
-  const uint64_t* tw = T.itw + (size_t)id * N;
-  const uint64_t* tws = T.itws + (size_t)id * N;
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) s[e] = a[e];
-  __syncthreads();
-  for (int st = logN - 1; st >= logR; --st) {
-    const int logt = logN - st - 1;
-    for (int b = threadIdx.x; b < NTT_TILE / 2; b += NTT_THREADS) {
-      int rr = b >> (logC - 1), bb = b & ((1 << (logC - 1)) - 1);
-      int g = bb >> logt, o = bb & ((1 << logt) - 1);
-      int k = (g << (logt + 1)) + o;
-      int ti = (1 << st) + (((row0 + rr) << (logC - logt - 1)) + g);
-      uint64_t W = tw[ti], Wp = tws[ti];
-      int i0 = (rr << logC) + k, i1 = i0 + (1 << logt);
-      uint64_t X = s[i0], Y = s[i1];
-      uint64_t U = X + Y;
-      s[i0] = U >= p2 ? U - p2 : U;
-      s[i1] = mul_shoup_lazy(X - Y + p2, W, Wp, p);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) a[e] = s[e];
-}
-
-// ---- inverse, columns (stages logR-1 .. 0) and scaling; canonical output ----
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* data, PolyMap map, NttTabs T, int logN,
-                                                              int logR, int scale_mode) {
-  __shared__ uint64_t s[NTT_TILE];
-  const int N = 1 << logN, logC = logN - logR;
-  const int logCOLS = 11 - logR;
-  const int COLS = 1 << logCOLS;
-  const int poly = blockIdx.y, k0 = blockIdx.x << logCOLS;
-  const int id = map.id(poly);
-  const uint64_t p = cK.p[id], p2 = 2 * p;
+  const PForm f = pform(id);
+  const uint64_t p = f.p;
+  const ulonglong2* tw = T.tw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
-  const uint64_t* tw = T.itw + (size_t)id * N;
-  const uint64_t* tws = T.itws + (size_t)id * N;
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) {
-    int r = e >> logCOLS, c = e & (COLS - 1);
-    s[e] = a[((size_t)r << logC) + k0 + c];
+  uint64_t x[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) x[u] = a[(size_t)row * C + kb + u * TPR];
+  fwd_block<4>(x, (uint32_t)(row * C + kb), LOGR, logN, tw, f);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int kk = kb + u * TPR;
+    s[r * PADC + kk + (kk >> 4)] = x[u];
   }
   __syncthreads();
-  for (int st = logR - 1; st >= 0; --st) {
-    const int logt = logR - st - 1;
-    for (int b = threadIdx.x; b < NTT_TILE / 2; b += NTT_THREADS) {
-      int c = b & (COLS - 1), bb = b >> logCOLS;
-      int g = bb >> logt, o = bb & ((1 << logt) - 1);
-      int r = (g << (logt + 1)) + o;
-      int ti = (1 << st) + g;
-      uint64_t W = tw[ti], Wp = tws[ti];
-      int i0 = (r << logCOLS) + c, i1 = i0 + (1 << (logt + logCOLS));
-      uint64_t X = s[i0], Y = s[i1];
-      uint64_t U = X + Y;
-      s[i0] = U >= p2 ? U - p2 : U;
-      s[i1] = mul_shoup_lazy(X - Y + p2, W, Wp, p);
+#pragma unroll
+  for (int m = 0; m < (16 / TPR); ++m) {
+    const int g = kb + m * TPR;  // group of 2^B2 consecutive columns, g < 16
+    uint64_t y[1 << B2];
+#pragma unroll
+    for (int u = 0; u < (1 << B2); ++u) {
+      const int kk = (g << B2) + u;
+      y[u] = s[r * PADC + kk + (kk >> 4)];
     }
-    __syncthreads();
+    fwd_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, tw, f);
+#pragma unroll
+    for (int u = 0; u < (1 << B2); ++u) {
+      const int kk = (g << B2) + u;
+      s[r * PADC + kk + (kk >> 4)] = red64to8(y[u], p);
+    }
   }
+  __syncthreads();
+  for (int e = t; e < NTT_TILE; e += NTT_THREADS) {
+    const int rr = e / C, kk = e % C;
+    a[(size_t)(row0 + rr) * C + kk] = s[rr * PADC + kk + (kk >> 4)];
+  }
+}
+
+// ---- inverse, rows (stages logN-1 .. LOGR); input in [0, 2p) --------------------
+template <int LOGR, int LOGC>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restrict__ data, PolyMap map, NttTabs T) {
+  constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
+  constexpr int ROWS = NTT_TILE >> LOGC, TPR = C / 16, B2 = LOGC - 4, PADC = C + C / 16;
+  __shared__ uint64_t s[ROWS * PADC];
+  const int t = threadIdx.x, r = t / TPR, kb = t % TPR;
+  const int poly = blockIdx.y, row0 = blockIdx.x * ROWS, row = row0 + r;
+  const int id = map.id(poly);
+  const PForm f = pform(id);
+  const uint64_t p = f.p;
+  const ulonglong2* itw = T.itw + (size_t)id * N;
+  uint64_t* a = data + (size_t)poly * N;
+  for (int e = t; e < NTT_TILE; e += NTT_THREADS) {
+    const int rr = e / C, kk = e % C;
+    s[rr * PADC + kk + (kk >> 4)] = a[(size_t)(row0 + rr) * C + kk];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < (16 / TPR); ++m) {
+    const int g = kb + m * TPR;
+    uint64_t y[1 << B2];
+#pragma unroll
+    for (int u = 0; u < (1 << B2); ++u) {
+      const int kk = (g << B2) + u;
+      y[u] = s[r * PADC + kk + (kk >> 4)];
+    }
+    inv_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, itw, f);
+#pragma unroll
+    for (int u = 0; u < (1 << B2); ++u) {
+      const int kk = (g << B2) + u;
+      s[r * PADC + kk + (kk >> 4)] = y[u];
+    }
+  }
+  __syncthreads();
+  uint64_t x[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int kk = kb + u * TPR;
+    x[u] = s[r * PADC + kk + (kk >> 4)];
+  }
+  inv_block<4>(x, (uint32_t)(row * C + kb), LOGR, logN, itw, f);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) a[(size_t)row * C + kb + u * TPR] = x[u];
+}
+
+// ---- inverse, columns (stages LOGR-1 .. 0) and scaling; canonical output --------
+template <int LOGR, int LOGC>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+                                                              int scale_mode) {
+  constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
+  constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
+  __shared__ uint64_t s[NTT_TILE];
+  const int t = threadIdx.x, k = t % COLS, rb = t / COLS;
+  const int poly = blockIdx.y, k0 = blockIdx.x * COLS;
+  const int id = map.id(poly);
+  const PForm f = pform(id);
+  const uint64_t p = f.p;
+  const ulonglong2* itw = T.itw + (size_t)id * N;
+  uint64_t* a = data + (size_t)poly * N;
+#pragma unroll
+  for (int m = 0; m < (16 >> A2); ++m) {
+    const int g = rb + m * RB;
+    uint64_t y[1 << A2];
+#pragma unroll
+    for (int u = 0; u < (1 << A2); ++u) y[u] = a[(size_t)((g << A2) + u) * C + k0 + k];
+    inv_block<A2>(y, (uint32_t)(((g << A2) * C) + k0 + k), 4, logN, itw, f);
+#pragma unroll
+    for (int u = 0; u < (1 << A2); ++u) s[((g << A2) + u) * COLS + k] = y[u];
+  }
+  __syncthreads();
+  uint64_t x[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) x[u] = s[(rb + u * RB) * COLS + k];
+  inv_block<4>(x, (uint32_t)(rb * C + k0 + k), 0, logN, itw, f);
   const uint64_t* sc = T.scale + ((size_t)scale_mode * NPRIME + id) * 2;
   const uint64_t w = sc[0], wp = sc[1];
-  for (int e = threadIdx.x; e < NTT_TILE; e += NTT_THREADS) {
-    int r = e >> logCOLS, c = e & (COLS - 1);
-    a[((size_t)r << logC) + k0 + c] = mul_shoup(s[e], w, wp, p);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const uint64_t y = mul_shoup4(x[u], w, wp, f);  // [0, 4p)
+    a[(size_t)(rb + u * RB) * C + k0 + k] = csub(csub(y, 2 * p), p);
   }
 }
 

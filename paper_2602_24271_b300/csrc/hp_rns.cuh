@@ -47,21 +47,25 @@ __global__ void __launch_bounds__(EW_THREADS) k_lift(const uint64_t* __restrict_
     y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
     fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
   }
-  const uint64_t v = (uint64_t)lift_v_mem(F, o, N);  // exact path re-reads the residues written above
+  const uint32_t v = (uint32_t)lift_v_mem(F, o, N);  // exact path re-reads the residues written above
+  uint32_t yl[L], yh[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) yl[i] = lo28(y[i]), yh[i] = hi28(y[i]);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint64_t b = cK.p[L + k];
-    Acc acc;
-    acc_zero(acc);
+    Acc3 a;
+    acc3_zero(a);
 #pragma unroll
-    for (int i = 0; i < L; ++i) acc_mac(acc, y[i], cK.MQB[i][k]);
-    acc_mac(acc, v, cK.negQB[k]);
-    o[(size_t)(L + k) * N] = redc(acc, b, cK.pinv[L + k]);
+    for (int i = 0; i < L; ++i) acc3_mac(a, yl[i], yh[i], cK.MQB_l[i][k], cK.MQB_h[i][k]);
+    acc3_mac(a, v, 0, cK.negQB_l[k], cK.negQB_h[k]);
+    o[(size_t)(L + k) * N] = redc(acc3_fold(a), b, cK.pinv[L + k]);
   }
 }
 
-// One thread per (b, prime index pi in Q u B, n).  ext values canonical (NTT domain).
-// dprod: [nct][3][NQB][N], values a b 2^-64 in [0, 2p).
+// One thread per (b, prime index pi in Q u B, n).  ext values in [0, 8p) (NTT
+// domain), so every product is below 64 p^2 < p 2^64 as Montgomery reduction
+// requires.  dprod: [nct][3][NQB][N], values a b 2^-64 in [0, 2p).
 __global__ void __launch_bounds__(EW_THREADS) k_tensor_sq(const uint64_t* __restrict__ ext, uint64_t* __restrict__ dprod,
                                                           int logN, int nct) {
   const int N = 1 << logN;
@@ -124,18 +128,21 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
     y[i] = mul_shoup(d[(size_t)i * N], cK.qhatinv[i], cK.qhatinv_s[i], cK.p[i]);
     fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
   }
-  const uint64_t v = (uint64_t)lift_v_mem(F, d, N);  // lifted value r = [t d]_Q has residues d_i
+  const uint32_t v = (uint32_t)lift_v_mem(F, d, N);  // lifted value r = [t d]_Q has residues d_i
+  uint32_t yl[L], yh[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) yl[i] = lo28(y[i]), yh[i] = hi28(y[i]);
   uint64_t yb[K];
   Fix G = {0, 0};
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint64_t b = cK.p[L + k];
-    Acc acc;
-    acc_zero(acc);
+    Acc3 a;
+    acc3_zero(a);
 #pragma unroll
-    for (int i = 0; i < L; ++i) acc_mac(acc, y[i], cK.MQB[i][k]);
-    acc_mac(acc, v, cK.negQB[k]);
-    const uint64_t r = redc(acc, b, cK.pinv[L + k]);
+    for (int i = 0; i < L; ++i) acc3_mac(a, yl[i], yh[i], cK.MQB_l[i][k], cK.MQB_h[i][k]);
+    acc3_mac(a, v, 0, cK.negQB_l[k], cK.negQB_h[k]);
+    const uint64_t r = redc(acc3_fold(a), b, cK.pinv[L + k]);
     const uint64_t z = sub_mod(d[(size_t)(L + k) * N], r, b);
     yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
     fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
@@ -146,15 +153,18 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
     vb = (int)G.hi;
   }
   uint64_t* o = w3 + bj * L * N + n;
+  uint32_t bl[K], bh[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) bl[k] = lo28(yb[k]), bh[k] = hi28(yb[k]);
 #pragma unroll
   for (int i = 0; i < L; ++i) {
     const uint64_t p = cK.p[i];
-    Acc acc;
-    acc_zero(acc);
+    Acc3 a;
+    acc3_zero(a);
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc_mac(acc, yb[k], cK.MBQ[k][i]);
-    acc_mac(acc, (uint64_t)vb, cK.negBQ[i]);
-    o[(size_t)i * N] = redc(acc, p, cK.pinv[i]);
+    for (int k = 0; k < K; ++k) acc3_mac(a, bl[k], bh[k], cK.MBQ_l[k][i], cK.MBQ_h[k][i]);
+    acc3_mac(a, (uint32_t)vb, 0, cK.negBQ_l[i], cK.negBQ_h[i]);
+    o[(size_t)i * N] = redc(acc3_fold(a), p, cK.pinv[i]);
   }
 }
 
@@ -176,30 +186,38 @@ __global__ void __launch_bounds__(EW_THREADS) k_ks_expand(const uint64_t* __rest
   ksin[gid] = csub(digit, cK.p[ks_id(j)]);  // digit < q_i < 2 p_j
 }
 
-// One thread per (b, target j, n).  rk: [L][2][NKS][N], NTT domain, Montgomery form.
+// One thread per (target j, n), looping over the tile's ciphertexts so that
+// each key word is read once per launch.  rk: [L][2][NKS][N], NTT domain,
+// Montgomery form (canonical); digits in [0, 8p): sums < 15 8 p^2 < p 2^64.
 // ksout: [nct][2][NKS][N] in [0, 2p).
 __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restrict__ ksin, const uint64_t* __restrict__ rk,
                                                        uint64_t* __restrict__ ksout, int logN, int nct) {
   const int N = 1 << logN;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)nct * NKS * N) return;
+  if (gid >= (size_t)NKS * N) return;
   const int n = (int)(gid & (N - 1));
-  const size_t bj = gid >> logN;
-  const int j = (int)(bj % NKS);
-  const size_t b = bj / NKS;
+  const int j = (int)(gid >> logN);
   const int id = ks_id(j);
-  Acc a0, a1;
-  acc_zero(a0);
-  acc_zero(a1);
+  const uint64_t p = cK.p[id], pinv = cK.pinv[id];
+  uint64_t k0[L], k1[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) {
-    const uint64_t d = ksin[((b * L + i) * NKS + j) * N + n];
-    acc_mac(a0, d, rk[((size_t)(i * 2 + 0) * NKS + j) * N + n]);
-    acc_mac(a1, d, rk[((size_t)(i * 2 + 1) * NKS + j) * N + n]);
+    k0[i] = rk[((size_t)(i * 2 + 0) * NKS + j) * N + n];
+    k1[i] = rk[((size_t)(i * 2 + 1) * NKS + j) * N + n];
   }
-  const uint64_t p = cK.p[id], pinv = cK.pinv[id];
-  ksout[((b * 2 + 0) * NKS + j) * N + n] = redc_lazy(a0, p, pinv);
-  ksout[((b * 2 + 1) * NKS + j) * N + n] = redc_lazy(a1, p, pinv);
+  for (int b = 0; b < nct; ++b) {
+    Acc a0, a1;
+    acc_zero(a0);
+    acc_zero(a1);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      const uint64_t d = ksin[(((size_t)b * L + i) * NKS + j) * N + n];
+      acc_mac(a0, d, k0[i]);
+      acc_mac(a1, d, k1[i]);
+    }
+    ksout[(((size_t)b * 2 + 0) * NKS + j) * N + n] = redc_lazy(a0, p, pinv);
+    ksout[(((size_t)b * 2 + 1) * NKS + j) * N + n] = redc_lazy(a1, p, pinv);
+  }
 }
 
 // x mod q for x < 4q

@@ -28,7 +28,8 @@ struct hp_handle {
   Consts C;
   int device = 0;
   // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][2]
-  uint64_t *tw = nullptr, *tws = nullptr, *itw = nullptr, *itws = nullptr, *scale = nullptr;
+  ulonglong2 *tw = nullptr, *itw = nullptr;  // (value, Shoup) pairs
+  uint64_t* scale = nullptr;
   // relinearisation key, NTT domain, Montgomery form: [L][2][NKS][N]
   uint64_t* rkm = nullptr;
   bool have_rk = false;
@@ -134,9 +135,7 @@ static inline unsigned ew_blocks(size_t n) { return (unsigned)((n + EW_THREADS -
 static NttTabs tabs(const hp_handle* h) {
   NttTabs T;
   T.tw = h->tw;
-  T.tws = h->tws;
   T.itw = h->itw;
-  T.itws = h->itws;
   T.scale = h->scale;
   return T;
 }
@@ -146,38 +145,58 @@ static const PolyMap MAP_KS = {NKS, 0, ID_P}; // [.][NKS][N]: q_0..q_14, P
 static const PolyMap MAP_Q = {L, 0, -1};      // [.][L][N]
 static const PolyMap MAP_T = {1, ID_T, -1};   // plaintext modulus
 
-static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaStream_t s) {
-  if (npoly == 0) return;
-  const int logC = h->logn - h->logR;
-  dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
-  dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
+template <int LR, int LC>
+static void ntt_fwd_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, DigitSrc dig, cudaStream_t s) {
+  const dim3 gc((1u << LC) / (NTT_TILE >> LR), (unsigned)npoly), gr((1u << LR) / (NTT_TILE >> LC), (unsigned)npoly);
   const double half = (double)npoly * (h->N / 2);
   {
-    ProfScope ps(h, PK_NTT_FWD_COLS, s, half * h->logR);
-    k_ntt_fwd_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+    ProfScope ps(h, PK_NTT_FWD_COLS, s, half * LR);
+    k_ntt_fwd_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
   }
   {
-    ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * logC);
-    k_ntt_fwd_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+    ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * LC);
+    k_ntt_fwd_rows<LR, LC><<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h));
   }
   h->launches += 2;
 }
 
-static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int scale_mode, cudaStream_t s) {
-  if (npoly == 0) return;
-  const int logC = h->logn - h->logR;
-  dim3 gc(1u << (logC - (11 - h->logR)), (unsigned)npoly);
-  dim3 gr(1u << (h->logR - (11 - logC)), (unsigned)npoly);
+template <int LR, int LC>
+static void ntt_inv_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int scale_mode, cudaStream_t s) {
+  const dim3 gc((1u << LC) / (NTT_TILE >> LR), (unsigned)npoly), gr((1u << LR) / (NTT_TILE >> LC), (unsigned)npoly);
   const double half = (double)npoly * (h->N / 2);
   {
-    ProfScope ps(h, PK_NTT_INV_ROWS, s, half * logC);
-    k_ntt_inv_rows<<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR);
+    ProfScope ps(h, PK_NTT_INV_ROWS, s, half * LC);
+    k_ntt_inv_rows<LR, LC><<<gr, NTT_THREADS, 0, s>>>(data, m, tabs(h));
   }
   {
-    ProfScope ps(h, PK_NTT_INV_COLS, s, half * h->logR);
-    k_ntt_inv_cols<<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), h->logn, h->logR, scale_mode);
+    ProfScope ps(h, PK_NTT_INV_COLS, s, half * LR);
+    k_ntt_inv_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), scale_mode);
   }
   h->launches += 2;
+}
+
+// N = R x C with log R = floor(log N / 2)
+static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaStream_t s,
+                    const uint64_t* digits = nullptr) {
+  if (npoly == 0) return;
+  DigitSrc d;
+  d.w3 = digits;
+  switch (h->logn) {
+    case 12: ntt_fwd_t<6, 6>(h, data, npoly, m, d, s); break;
+    case 13: ntt_fwd_t<6, 7>(h, data, npoly, m, d, s); break;
+    case 14: ntt_fwd_t<7, 7>(h, data, npoly, m, d, s); break;
+    default: ntt_fwd_t<7, 8>(h, data, npoly, m, d, s); break;
+  }
+}
+
+static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int scale_mode, cudaStream_t s) {
+  if (npoly == 0) return;
+  switch (h->logn) {
+    case 12: ntt_inv_t<6, 6>(h, data, npoly, m, scale_mode, s); break;
+    case 13: ntt_inv_t<6, 7>(h, data, npoly, m, scale_mode, s); break;
+    case 14: ntt_inv_t<7, 7>(h, data, npoly, m, scale_mode, s); break;
+    default: ntt_inv_t<7, 8>(h, data, npoly, m, scale_mode, s); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -187,7 +206,7 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
 static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int one_minus, cudaStream_t s) {
   const int N = h->N, logN = h->logn;
   ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
-  if (general) {
+  if (general) {  // SELECT: general product
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
     ProfScope ps(h, PK_TENSOR, s, 4.0 * b * NQB * N);
     k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->ext2, h->dprod, logN, b);
@@ -201,15 +220,13 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
     ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
     k_scale_round<<<ew_blocks((size_t)b * 3 * N), EW_THREADS, 0, s>>>(h->dprod, h->w3, h->status, logN, b);
   }
-  {
-    ProfScope ps(h, PK_KS_EXPAND, s, (double)b * L * NKS * N);
-    k_ks_expand<<<ew_blocks((size_t)b * L * NKS * N), EW_THREADS, 0, s>>>(h->w3, h->ksin, logN, b);
-  }
-  h->launches += 2;
-  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s);
+  h->launches += 1;
+  // key switching: digits [d2]_{q_i} mod p_j (reduction fused into the first
+  // transform pass), key multiply-accumulate, inverse transform, mod-down
+  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s, h->w3);
   {
     ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * L * NKS * N);
-    k_ks_mac<<<ew_blocks((size_t)b * NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
+    k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
   }
   h->launches += 1;
   ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
@@ -265,7 +282,7 @@ static int brv(int x, int bits) {
 
 static int build_tables(hp_handle* h) {
   const int N = h->N;
-  std::vector<uint64_t> tw((size_t)NPRIME * N), tws(tw.size()), itw(tw.size()), itws(tw.size());
+  std::vector<ulonglong2> tw((size_t)NPRIME * N), itw(tw.size());
   std::vector<uint64_t> sc((size_t)NSCALE * NPRIME * 2);
   std::vector<uint64_t> pw(N), ipw(N);
   for (int id = 0; id < NPRIME; ++id) {
@@ -279,10 +296,9 @@ static int build_tables(hp_handle* h) {
     }
     for (int j = 0; j < N; ++j) {
       size_t o = (size_t)id * N + j;
-      tw[o] = pw[brv(j, h->logn)];
-      tws[o] = h_shoup(tw[o], p);
-      itw[o] = ipw[brv(j, h->logn)];
-      itws[o] = h_shoup(itw[o], p);
+      const uint64_t w = pw[brv(j, h->logn)], iw = ipw[brv(j, h->logn)];
+      tw[o] = make_ulonglong2(w, h_shoup(w, p));
+      itw[o] = make_ulonglong2(iw, h_shoup(iw, p));
     }
     const uint64_t ninv = h_invmod((uint64_t)N % p, p);
     const uint64_t r64 = (uint64_t)(((unsigned __int128)1 << 64) % p);
@@ -292,16 +308,12 @@ static int build_tables(hp_handle* h) {
       sc[((size_t)m * NPRIME + id) * 2 + 1] = h_shoup(vals[m], p);
     }
   }
-  size_t tb = tw.size() * sizeof(uint64_t);
+  size_t tb = tw.size() * sizeof(ulonglong2);
   CU(h, cudaMalloc(&h->tw, tb));
-  CU(h, cudaMalloc(&h->tws, tb));
   CU(h, cudaMalloc(&h->itw, tb));
-  CU(h, cudaMalloc(&h->itws, tb));
   CU(h, cudaMalloc(&h->scale, sc.size() * sizeof(uint64_t)));
   CU(h, cudaMemcpy(h->tw, tw.data(), tb, cudaMemcpyHostToDevice));
-  CU(h, cudaMemcpy(h->tws, tws.data(), tb, cudaMemcpyHostToDevice));
   CU(h, cudaMemcpy(h->itw, itw.data(), tb, cudaMemcpyHostToDevice));
-  CU(h, cudaMemcpy(h->itws, itws.data(), tb, cudaMemcpyHostToDevice));
   CU(h, cudaMemcpy(h->scale, sc.data(), sc.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
   return HP_OK;
 }
@@ -327,9 +339,9 @@ static int load_consts(hp_handle* h) {
 static void free_all(hp_handle* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
-  uint64_t* ptrs[] = {h->tw, h->tws, h->itw, h->itws, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
-                      h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto};
-  for (uint64_t* p : ptrs)
+  void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
+                  h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto};
+  for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
 }
@@ -392,6 +404,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
     return fail(HP_ERR_CUDA);
   }
   if ((rc = load_consts(h)) != HP_OK) return fail(rc);
+
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
   size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
   h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)4 << 30) / per);  // ~4 GB of workspace
