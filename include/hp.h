@@ -177,6 +177,28 @@ size_t hp_tile_size(const hp_handle* h);
  * parameters); HP_OK if clean.  The word is cleared afterwards. */
 int hp_check_status(hp_handle* h);
 
+/* ---- allocation-free squaring (no counterpart in the paper) ------------------
+ * For callers that cannot allocate device memory when they need the
+ * operation -- e.g. a process whose memory pool already holds the GPU's free
+ * memory, or a serving loop that must keep a fixed footprint and never call
+ * cudaMalloc/cudaFree in its steady state.  Computes exactly what
+ * hp_run(h, HP_SQUARE, ct_in, NULL, 0, ct_out, 1, stream) computes (one
+ * squaring + relinearisation of ONE ciphertext, bit-identical), but its
+ * working buffers live in a fixed array in the library's device memory image
+ * (472 words per coefficient for ring degree <= 4096: 15.5 MB, held by every
+ * GPU that loads the library until the process exits) instead of the
+ * handle's workspace.  It calls no allocation routine.
+ *   - ring degree above 4096: HP_ERR_UNSUPPORTED, nothing launched;
+ *   - ct_in / ct_out: device, [2][L][N], 16-byte aligned; ct_out may alias ct_in;
+ *   - the handle's device must be current (HP_ERR_ARG otherwise);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - all calls share the one array and it keeps the last call's contents;
+ *     nothing in it needs to start at zero.  Calls whose GPU work overlaps
+ *     (different streams, or several host threads) race on it: order them.
+ * Asynchronous on `stream` like hp_run. */
+int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, void* stream);
+
 /* ---- measurement -----------------------------------------------------------
  * Per-kernel-class timing with CUDA events recorded on the launching stream
  * around every launch of the classes in `class_mask` (bit c = class c):

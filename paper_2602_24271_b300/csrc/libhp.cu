@@ -686,6 +686,70 @@ int hp_probe_peak(int kind, double* per_second) {
   return HP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free squaring.  Some callers cannot allocate device memory at the
+// point where they need a squaring: a process whose memory pool already owns
+// the GPU's free memory, or code that must not call cudaMalloc/cudaFree in its
+// steady state (a serving loop with a fixed memory footprint).  For them,
+// hp_square_noalloc runs the same squaring + relinearisation as
+// hp_run(HP_SQUARE) on one ciphertext, with its working buffers in a
+// fixed-size array that lives in the library's own device memory image.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_MAX_LOGN = 12;  // ring degree up to 4096
+constexpr size_t NOALLOC_WORDS_PER_COEFF = 2 * NQB + 3 * NQB + 3 * L + L * NKS + 2 * NKS;  // 472
+constexpr size_t NOALLOC_WORDS = NOALLOC_WORDS_PER_COEFF << NOALLOC_MAX_LOGN;            // 15.5 MB
+static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
+static uint64_t* g_noalloc_addr[64];  // device address of the array, per device (set up on first use)
+
+static int noalloc_scratch(hp_handle* h, uint64_t** out) {
+  if (!g_noalloc_addr[h->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) HP_FAIL(h, HP_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr[h->device] = (uint64_t*)p;
+  }
+  *out = g_noalloc_addr[h->device];
+  return HP_OK;
+}
+
+int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (!ct_in || !ct_out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (h->logn > NOALLOC_MAX_LOGN)
+    HP_FAIL(h, HP_ERR_UNSUPPORTED,
+            "hp_square_noalloc: ring degree %d exceeds the static scratch limit of %d (%zu words)", h->N,
+            1 << NOALLOC_MAX_LOGN, NOALLOC_WORDS);
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  if (((uintptr_t)ct_in | (uintptr_t)ct_out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  int cur = -1;
+  CU(h, cudaGetDevice(&cur));
+  if (cur != h->device) HP_FAIL(h, HP_ERR_ARG, "the handle's device must be current");
+  uint64_t* ws = nullptr;
+  int rc = noalloc_scratch(h, &ws);
+  if (rc != HP_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N, logN = h->logn;
+  uint64_t* ext = ws;
+  uint64_t* dprod = ext + (size_t)2 * NQB * N;
+  uint64_t* w3 = dprod + (size_t)3 * NQB * N;
+  uint64_t* ksin = w3 + (size_t)3 * L * N;
+  uint64_t* ksout = ksin + (size_t)L * NKS * N;
+  // every scratch word read below is written earlier in this call: nothing needs clearing
+  k_lift<<<ew_blocks((size_t)2 * N), EW_THREADS, 0, s>>>(ct_in, nullptr, 0, LIFT_COPY, ext, logN, 1);
+  ntt_fwd(h, ext, 2 * NQB, MAP_QB, s);
+  k_tensor_sq<<<ew_blocks((size_t)NQB * N), EW_THREADS, 0, s>>>(ext, dprod, logN, 1);
+  ntt_inv(h, dprod, 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
+  k_scale_round<<<ew_blocks((size_t)3 * N), EW_THREADS, 0, s>>>(dprod, w3, h->status, logN, 1);
+  ntt_fwd(h, ksin, (size_t)L * NKS, MAP_KS, s, w3);
+  k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(ksin, h->rkm, ksout, logN, 1);
+  ntt_inv(h, ksout, 2 * NKS, MAP_KS, SCALE_NINV, s);
+  k_moddown<<<ew_blocks((size_t)2 * L * N), EW_THREADS, 0, s>>>(ksout, w3, ct_out, 0, logN, 1);
+  h->launches += 6;
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
 // Synchronise and report the device status word (exactness checks), then clear it.
 int hp_check_status(hp_handle* h) {
   if (!h) return HP_ERR_ARG;

@@ -40,6 +40,7 @@ EXPORTED = [
     "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
+    "hp_square_noalloc",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -109,6 +110,7 @@ def load():
                                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
         "hp_probe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "hp_tile_size": (ctypes.c_size_t, [H]),
+        "hp_square_noalloc": (ctypes.c_int, [H, P64, P64, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
