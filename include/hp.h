@@ -1,13 +1,13 @@
 /* libhp — the NSHEDB equality predicate over BFV-packed columns on one GPU.
  *
  * Paper: "NSHEDB: Noise-Sensitive Homomorphic Encrypted Database Query Engine"
- * (arXiv 2602.24271).  The operation is the equality predicate of Sec. 2.1.6,
- * Eq. (equality):  EQ(x, y) = 1 - (x - y)^(p-1), evaluated slot-wise on BFV
- * ciphertexts that pack N column values each (Sec. 3.1), with p = 65537 so that
- * exponentiation by squaring (Sec. 3.3.1, Table 3: ceil(log(p-1)) = 16
+ * (arXiv 2602.24271).  The operation is the equality predicate of Sec. 2.1.7,
+ * Eq. 3:  EQ(x, y) = 1 - (x - y)^(p-1), evaluated slot-wise on BFV
+ * ciphertexts that pack N column values each (Sec. 4.1), with p = 65537 so that
+ * exponentiation by squaring (Sec. 4.3.1, Table 3: ceil(log(p-1)) = 16
  * multiplications) is 16 ciphertext squarings, each relinearised.
  *
- * Scheme and parameters (paper Sec. 4.1: N = 32768, log QP = 881, p = 65537):
+ * Scheme and parameters (paper Sec. 5.1: N = 32768, log QP = 881, p = 65537):
  *   ring            Z_Q[X] / (X^N + 1), N = 2^log_n, 12 <= log_n <= 15
  *   data modulus    Q = q_0 ... q_{L-1}, L = 15, q_i prime < 2^55, q_i = 1 mod 2^16
  *   special prime   P < 2^56, P = 1 mod 2^16 (relinearisation only)
@@ -74,9 +74,9 @@ typedef struct {
 
 /* Operations of hp_run / hp_run_batched. */
 typedef enum {
-  HP_EQ_CT_CT = 0,    /* EQ(x, y) = 1 - (x - y)^(p-1), Eq. (equality) */
+  HP_EQ_CT_CT = 0,    /* EQ(x, y) = 1 - (x - y)^(p-1), Eq. 3 */
   HP_EQ_CT_CONST = 1, /* EQ(x, c) with c broadcast to every slot */
-  HP_SELECT = 2,      /* y * EQ(x, c): the SELECT tail of Eq. (select); ct_y is the column */
+  HP_SELECT = 2,      /* y * EQ(x, c): the SELECT tail of Eq. 5; ct_y is the column */
   HP_SQUARE = 3       /* one squaring + relinearisation (building block, for tests) */
 } hp_op;
 

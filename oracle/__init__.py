@@ -5,9 +5,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 module.  The CUDA library never calls it, and it never calls the CUDA library.
 
 The C++ source (``bfv_oracle.cpp``) restates the paper's equality predicate
-(Sec. 2.1.6, Eq. (equality): EQ(x, y) = 1 - (x - y)^(p-1)), computed by
-exponentiation by squaring (Sec. 3.3.1: ceil(log2(p-1)) = 16 multiplications for
-p = 65537), over textbook BFV with the parameters of Sec. 4.1 (N = 32768,
+(Sec. 2.1.7, Eq. 3: EQ(x, y) = 1 - (x - y)^(p-1)), computed by
+exponentiation by squaring (Sec. 4.3.1: ceil(log2(p-1)) = 16 multiplications for
+p = 65537), over textbook BFV with the parameters of Sec. 5.1 (N = 32768,
 log QP = 881, p = 65537).  Every function below states which operation it
 exposes; the arithmetic lives in the C++ file.
 
@@ -104,7 +104,7 @@ L_DEFAULT = 15
 def default_primes(L: int = L_DEFAULT):
     """Data primes q_0 > ... > q_{L-1} (largest below 2^55, = 1 mod 2^16) and the
     special prime P (largest below 2^56, = 1 mod 2^16).  log2(Q P) ~ 881 for
-    L = 15 (paper Sec. 4.1)."""
+    L = 15 (paper Sec. 5.1)."""
     lib = _load()
     q = np.zeros(L, dtype=np.uint64)
     P = np.zeros(1, dtype=np.uint64)

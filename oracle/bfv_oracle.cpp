@@ -5,8 +5,8 @@
 // benchmark do.  It shares no code, header, table or constant generator with
 // the CUDA library.
 //
-// What it computes (paper: Sec. 2.1.6 "Basic logical comparisons", Eq. (equality);
-// Sec. 3.3.1 "Equality checks" for exponentiation by squaring; Sec. 4.1 for the
+// What it computes (paper: Sec. 2.1.7 "Basic logical comparisons", Eq. 3;
+// Sec. 4.3.1 "Equality checks" for exponentiation by squaring; Sec. 5.1 for the
 // parameters N = 32768, log QP = 881, p = 65537):
 //
 //   EQ(ct_x, ct_y) = 1 - (ct_x - ct_y)^(p-1),  p - 1 = 2^16  =>  16 squarings.

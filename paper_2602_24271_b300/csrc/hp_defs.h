@@ -11,7 +11,7 @@
 
 namespace hp {
 
-constexpr int L = 15;              // data primes (paper Sec. 4.1: log QP = 881 with P)
+constexpr int L = 15;              // data primes (paper Sec. 5.1: log QP = 881 with P)
 constexpr int K = 16;              // auxiliary base: B > t N Q covers |round(t d / Q)| < B / 2
 constexpr int NQB = L + K;         // primes of the extended base Q u B
 constexpr int ID_P = L + K;        // 31

@@ -1,8 +1,8 @@
 """Seeded synthetic plaintext columns for the equality predicate.
 
 This module holds no arithmetic of the method: it only draws integer columns
-shaped like the paper's workloads (16-bit integer columns, Sec. 4.3 "Memory and
-Storage Efficiency"; dictionary IDs 1..|D|, Sec. 3.2 GROUP BY) with numpy's
+shaped like the paper's workloads (16-bit integer columns, Sec. 5.4 "Memory and
+Storage Efficiency"; dictionary IDs 1..|D|, Sec. 4.2.2 GROUP BY) with numpy's
 seeded generator.  Both the CUDA path and the oracle-based tests consume its
 output; neither side's randomness for keys and encryption comes from here.
 """

@@ -65,7 +65,7 @@ def test_philox_draw_uses_seed_as_key_and_counter_fields():
 
 
 # --------------------------------------------------------------------------
-# parameters (Sec. 4.1)
+# parameters (Sec. 5.1)
 # --------------------------------------------------------------------------
 def test_default_primes_match_their_definition_and_the_paper():
     q, P = oracle.default_primes(15)
@@ -336,7 +336,7 @@ def test_eq_depth_is_sixteen(orc16):
 
 def test_depth_overflow_decrypts_wrongly():
     """With a 3-prime modulus the noise budget runs out after a few squarings and
-    decryption stops matching the plaintext closed form (leveled HE, Sec. 2.1.2)."""
+    decryption stops matching the plaintext closed form (leveled HE, Sec. 2.1.1-2.1.2)."""
     q, P = oracle.default_primes(15)
     o = oracle.Oracle(4, q=q[:3], P=P)
     o.keygen(3)
