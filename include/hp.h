@@ -126,14 +126,26 @@ typedef struct {
 } hp_instance;
 
 /* Evaluate `op` (HP_EQ_CT_CT or HP_EQ_CT_CONST) for n_inst instances of
- * uneven size in one pipelined, CUDA-graph-replayed pass over the union of
- * their ciphertexts.  `inst` is host memory; ct_x / ct_y / ct_out are device
- * arrays of n_ct_total ciphertexts.  For HP_EQ_CT_CONST with slot-packed
- * instances each instance's constant applies to its own slot range only.
- * Every ciphertext index must be covered by exactly one instance (or by
- * several slot-packed ones whose ranges do not overlap). */
+ * uneven size in one pass over the union of their ciphertexts: tiles of
+ * ciphertexts, each replayed from a CUDA graph of the whole 16-squaring launch
+ * sequence (captured once per tile shape and kept in the handle).  `inst` is
+ * host memory; ct_x / ct_y / ct_out are device arrays of n_ct_total
+ * ciphertexts.  Instance i covers global slots [ct_offset N + slot_offset,
+ * + n_slots) inside its ciphertexts ct_offset .. ct_offset + n_ct - 1.  For
+ * HP_EQ_CT_CONST each instance's constant applies to its own slot range (slots
+ * outside every instance compare against 0).  Every ciphertext must belong to
+ * at least one instance and slot ranges must not overlap (HP_ERR_ARG).
+ * Stream-ordered; the first call per tile shape also captures its graph. */
 int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst, const uint64_t* ct_x,
                    const uint64_t* ct_y, uint64_t* ct_out, size_t n_ct_total, void* stream);
+
+/* Time the EQ launch sequence for candidate tile sizes (up to the handle's
+ * workspace tile) and make the fastest per ciphertext the tile used by hp_run
+ * and hp_run_batched; *best_tile (optional) receives it.  Runs on the
+ * handle's own staging buffers (the computation is data-oblivious, so the
+ * timing does not depend on the data); cached per (ring degree, device, max
+ * tile) for the process.  Synchronous. */
+int hp_autotune(hp_handle* h, size_t* best_tile);
 
 /* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
  * derivative, so this always returns HP_ERR_UNSUPPORTED. */
@@ -168,8 +180,9 @@ int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, 
  * h (for launch accounting). */
 uint64_t hp_launch_count(const hp_handle* h);
 
-/* Ciphertexts per pipeline tile chosen by hp_create (max_tile_ct or the
- * default that fits about 4 GB of workspace). */
+/* Ciphertexts per pipeline tile used by hp_run / hp_run_batched: the
+ * autotuned size if hp_autotune ran, else the workspace tile chosen by
+ * hp_create (max_tile_ct or the default that fits about 4 GB of workspace). */
 size_t hp_tile_size(const hp_handle* h);
 
 /* Synchronise the device and report the exactness status word of h (a

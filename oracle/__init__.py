@@ -78,6 +78,7 @@ def _load():
         "orc_mul_relin": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_eq": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_uint64, ctypes.c_int, _u64p]),
         "orc_square_chain": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p]),
+        "orc_eq_plain": (ctypes.c_int, [V, _u64p, _u32p, ctypes.c_int, _u64p]),
         "orc_tensor_round": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_relin": (ctypes.c_int, [V, _u64p, _u64p]),
     }
@@ -269,6 +270,15 @@ class Oracle:
             Y = _c(y, np.uint64)
             yp = _p(Y, ctypes.c_uint64)
         if self.lib.orc_eq(self.h, _p(X, ctypes.c_uint64), yp, const_val, squarings, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("relinearisation key not set")
+        return out
+
+    def eq_plain(self, x, cslots, squarings: int = 16):
+        """EQ(x, c) with one plaintext constant per slot: x - (Delta encode(c), 0),
+        the squarings, then "1 -"."""
+        X, C, out = _c(x, np.uint64), _c(cslots, np.uint32), self._ct_out()
+        if self.lib.orc_eq_plain(self.h, _p(X, ctypes.c_uint64), _p(C, ctypes.c_uint32), squarings,
+                                 _p(out, ctypes.c_uint64)) != 0:
             raise RuntimeError("relinearisation key not set")
         return out
 

@@ -1041,6 +1041,21 @@ int orc_eq(void* h, const uint64_t* x, const uint64_t* y, uint64_t const_val, in
   return 0;
 }
 
+// EQ against a plaintext with one constant per slot: d = x - (Delta m, 0) with
+// m = encode(cslots) (textbook plaintext subtraction), then the squarings and
+// "1 -".  With every slot equal to c this is the broadcast form x - c.
+int orc_eq_plain(void* h, const uint64_t* x, const uint32_t* cslots, int squarings, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk) return -2;
+  std::vector<uint64_t> m(c.N);
+  encode_slots(c, cslots, m.data());
+  Ct d = ct_from_rns(c, x);
+  for (int k = 0; k < c.N; ++k) d.c0[k] = mod_Q(c, big_sub(d.c0[k], big_mul_u64(c.Delta, m[k])));
+  for (int r = 0; r < squarings; ++r) d = ct_mul_relin(c, d, d);
+  ct_to_rns(c, ct_one_minus(c, d), out);
+  return 0;
+}
+
 // Squarings only (no difference, no "1 -"): for noise-depth tests.
 int orc_square_chain(void* h, const uint64_t* x, int squarings, uint64_t* out) {
   Ctx& c = *(Ctx*)h;

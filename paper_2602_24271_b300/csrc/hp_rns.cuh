@@ -16,8 +16,10 @@ constexpr int EW_THREADS = 256;
 // status bits written by kernels (never expected; checked by the host)
 enum { ST_BQ_WINDOW = 1 };
 
-// Difference modes of the first lift (row a1).
-enum { LIFT_COPY = 0, LIFT_SUB_CT = 1, LIFT_SUB_CONST = 2 };
+// Difference modes of the first lift (row a1).  LIFT_SUB_PT subtracts
+// (Delta m, 0) for a plaintext polynomial m per ciphertext (sub: [nct][N],
+// coefficients < t): the packed form of x = c with per-slot constants.
+enum { LIFT_COPY = 0, LIFT_SUB_CT = 1, LIFT_SUB_CONST = 2, LIFT_SUB_PT = 3 };
 
 // One thread per (ciphertext b, component c, coefficient n).
 // src, sub: [nct][2][L][N]; ext: [nct][2][NQB][N].
@@ -42,6 +44,8 @@ __global__ void __launch_bounds__(EW_THREADS) k_lift(const uint64_t* __restrict_
       v = sub_mod(v, sub[bc * L * N + (size_t)i * N + n], p);
     } else if (mode == LIFT_SUB_CONST && comp == 0 && n == 0) {
       v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
+    } else if (mode == LIFT_SUB_PT && comp == 0) {
+      v = sub_mod(v, mul_shoup(sub[(bc >> 1) * N + n], cK.delta[i], cK.delta_s[i], p), p);
     }
     o[(size_t)i * N] = v;
     y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
@@ -257,6 +261,30 @@ __global__ void __launch_bounds__(EW_THREADS) k_moddown(const uint64_t* __restri
     if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], q);
   }
   out[gid] = r;
+}
+
+// Plaintext slots of a tile of slot-packed instances: slot j of ciphertext
+// ct0 + c gets the constant of the instance whose global slot range
+// [start, start + len) contains (ct0 + c) N + j, or 0.  Instances sorted by
+// start, non-overlapping.  M: [nct][N] (input of the encoding transform).
+__global__ void k_pack_slots(const uint64_t* __restrict__ start, const uint32_t* __restrict__ len,
+                             const uint64_t* __restrict__ cval, int n_inst, uint64_t ct0, uint64_t* __restrict__ M,
+                             int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * N) return;
+  const uint64_t g = (ct0 << logN) + gid;
+  int lo = 0, hi = n_inst - 1, f = -1;  // last instance with start <= g
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= g) {
+      f = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
+  M[gid] = (f >= 0 && g < start[f] + len[f]) ? cval[f] : 0;
 }
 
 // "1 -" alone: out = (Delta - c0, -c1).  One thread per word of [nct][2][L][N].

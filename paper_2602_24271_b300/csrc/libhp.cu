@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -37,8 +38,18 @@ struct hp_handle {
   size_t tile = 0;
   uint64_t *ext = nullptr, *ext2 = nullptr, *dprod = nullptr, *w3 = nullptr, *ksin = nullptr, *ksout = nullptr,
            *ctbuf = nullptr, *maskbuf = nullptr;
-  // staging for host-memory calls: x, y, out for one tile
-  uint64_t *stx = nullptr, *sty = nullptr, *sto = nullptr;
+  // staging for host-memory calls and graph-replayed tiles: x, y, out, and the
+  // plaintext polynomials of packed per-instance constants ([tile][N])
+  uint64_t *stx = nullptr, *sty = nullptr, *sto = nullptr, *stm = nullptr;
+  size_t run_tile = 0;  // tile used by hp_run / hp_run_batched (autotuned, <= tile; 0 = tile)
+  // CUDA graphs of the whole per-tile launch sequence, keyed by (first-lift mode, tile size)
+  struct GraphEntry {
+    int mode, b;
+    cudaGraphExec_t exec;
+    uint64_t kernels;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap = nullptr;
   int* status = nullptr;  // device status word (ST_* bits)
   uint64_t launches = 0;
   std::string err;
@@ -99,6 +110,7 @@ struct ProfScope {
 };
 
 static std::string g_create_err;
+extern "C" int hp_check_status(hp_handle* h);
 
 #define HP_FAIL(h, code, ...)                                  \
   do {                                                         \
@@ -127,6 +139,7 @@ static size_t ws_words_per_ct(int N) {
                       + 2 * L      // ctbuf
                       + 2 * L      // maskbuf
                       + 3 * 2 * L  // staging x, y, out
+                      + 1          // staging plaintext polynomials
                      );
 }
 
@@ -244,19 +257,18 @@ static void lift(hp_handle* h, const uint64_t* src, const uint64_t* sub, uint64_
   h->launches += 1;
 }
 
-// The whole hot path for one tile of b device-resident ciphertexts.
-static void run_tile(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t cval, uint64_t* out, int b,
-                     cudaStream_t s) {
+// The whole hot path for one tile of b device-resident ciphertexts; the first
+// lift applies row a1 in mode `lmode` (sub = y for LIFT_SUB_CT, the plaintext
+// polynomials for LIFT_SUB_PT).
+static void run_tile_mode(hp_handle* h, int op, int lmode, const uint64_t* x, const uint64_t* sub, const uint64_t* y,
+                          uint64_t cval, uint64_t* out, int b, cudaStream_t s) {
   if (op == HP_SQUARE) {
     lift(h, x, nullptr, 0, LIFT_COPY, h->ext, b, s);
     mul_relin_tail(h, b, false, out, 0, s);
     return;
   }
   // a1: difference, fused into the first lift
-  if (op == HP_EQ_CT_CT)
-    lift(h, x, y, 0, LIFT_SUB_CT, h->ext, b, s);
-  else
-    lift(h, x, nullptr, cval, LIFT_SUB_CONST, h->ext, b, s);
+  lift(h, x, sub, cval, lmode, h->ext, b, s);
   // a2: 16 squarings; a3: "1 -" fused into the last mod-down
   for (int it = 0; it < 16; ++it) {
     if (it > 0) lift(h, h->ctbuf, nullptr, 0, LIFT_COPY, h->ext, b, s);
@@ -269,6 +281,12 @@ static void run_tile(hp_handle* h, int op, const uint64_t* x, const uint64_t* y,
     lift(h, y, nullptr, 0, LIFT_COPY, h->ext2, b, s);
     mul_relin_tail(h, b, true, out, 0, s);
   }
+}
+
+static void run_tile(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t cval, uint64_t* out, int b,
+                     cudaStream_t s) {
+  const int lmode = op == HP_EQ_CT_CT ? LIFT_SUB_CT : LIFT_SUB_CONST;
+  run_tile_mode(h, op, lmode, x, op == HP_EQ_CT_CT ? y : nullptr, y, cval, out, b, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,8 +357,11 @@ static int load_consts(hp_handle* h) {
 static void free_all(hp_handle* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  if (h->cap) cudaStreamDestroy(h->cap);
   void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
-                  h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto};
+                  h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
@@ -417,12 +438,18 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   } allocs[] = {{&h->ext, T * 2 * NQB * N},  {&h->ext2, T * 2 * NQB * N}, {&h->dprod, T * 3 * NQB * N},
                 {&h->w3, T * 3 * L * N},     {&h->ksin, T * L * NKS * N}, {&h->ksout, T * 2 * NKS * N},
                 {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
-                {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->rkm, (size_t)L * 2 * NKS * N}};
+                {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
+                {&h->rkm, (size_t)L * 2 * NKS * N}};
   for (auto& a : allocs) {
     if (cudaMalloc(a.p, a.words * sizeof(uint64_t)) != cudaSuccess) {
       h->err = "device allocation failed for the workspace";
       return fail(HP_ERR_OOM);
     }
+  }
+  // staging starts zeroed (the autotuner times tiles on it)
+  if (cudaMemset(h->stx, 0, T * 2 * L * N * 8) != cudaSuccess || cudaMemset(h->sty, 0, T * 2 * L * N * 8) != cudaSuccess) {
+    h->err = "workspace initialisation failed";
+    return fail(HP_ERR_CUDA);
   }
   if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess || cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
     h->err = "status word allocation failed";
@@ -476,8 +503,9 @@ int hp_run(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t 
   const bool dev = is_device_ptr(x);
   if (dev != is_device_ptr(out) || ((op == HP_EQ_CT_CT || op == HP_SELECT) && dev != is_device_ptr(y)))
     HP_FAIL(h, HP_ERR_ARG, "ciphertext arguments must all be device memory or all host memory");
-  for (size_t c0 = 0; c0 < n_ct; c0 += h->tile) {
-    const int b = (int)((n_ct - c0 < h->tile) ? n_ct - c0 : h->tile);
+  const size_t TT = h->run_tile ? h->run_tile : h->tile;
+  for (size_t c0 = 0; c0 < n_ct; c0 += TT) {
+    const int b = (int)((n_ct - c0 < TT) ? n_ct - c0 : TT);
     const size_t off = c0 * W, bytes = (size_t)b * W * sizeof(uint64_t);
     if (dev) {
       run_tile(h, op, x + off, y ? y + off : nullptr, cval, out + off, b, s);
@@ -493,18 +521,179 @@ int hp_run(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t 
   return HP_OK;
 }
 
+// Graph of one tile's launch sequence on the staging buffers (captured once per
+// (mode, tile size) on an internal stream, replayed on the caller's stream).
+enum { GM_CTCT = 0, GM_PT = 1 };
+static int tile_graph(hp_handle* h, int mode, int b, cudaGraphExec_t* exec, uint64_t* kernels) {
+  for (auto& g : h->graphs)
+    if (g.mode == mode && g.b == b) {
+      *exec = g.exec;
+      *kernels = g.kernels;
+      return HP_OK;
+    }
+  if (!h->cap) CU(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  const uint32_t saved_mask = h->prof_mask;
+  const uint64_t saved_launches = h->launches;
+  h->prof_mask = 0;  // no timing events inside graphs
+  h->launches = 0;
+  CU(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  if (mode == GM_CTCT)
+    run_tile_mode(h, HP_EQ_CT_CT, LIFT_SUB_CT, h->stx, h->sty, nullptr, 0, h->sto, b, h->cap);
+  else
+    run_tile_mode(h, HP_EQ_CT_CONST, LIFT_SUB_PT, h->stx, h->stm, nullptr, 0, h->sto, b, h->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  h->prof_mask = saved_mask;
+  const uint64_t nk = h->launches;
+  h->launches = saved_launches;
+  if (e != cudaSuccess) HP_FAIL(h, HP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) HP_FAIL(h, HP_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  h->graphs.push_back({mode, b, ex, nk});
+  *exec = ex;
+  *kernels = nk;
+  return HP_OK;
+}
+
 int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst, const uint64_t* x, const uint64_t* y,
                    uint64_t* out, size_t n_ct_total, void* stream) {
   if (!h) return HP_ERR_ARG;
-  (void)inst;
-  (void)n_inst;
-  (void)x;
-  (void)y;
-  (void)out;
-  (void)n_ct_total;
-  (void)stream;
-  (void)op;
-  HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_run_batched: not built yet");
+  h->launches = 0;
+  if (op != HP_EQ_CT_CT && op != HP_EQ_CT_CONST) HP_FAIL(h, HP_ERR_ARG, "batched op must be EQ_CT_CT or EQ_CT_CONST");
+  if (n_ct_total == 0) return HP_OK;
+  if (!inst || n_inst == 0) HP_FAIL(h, HP_ERR_ARG, "no instances");
+  if (!x || !out || (op == HP_EQ_CT_CT && !y)) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  if (!is_device_ptr(x) || !is_device_ptr(out) || (op == HP_EQ_CT_CT && !is_device_ptr(y)))
+    HP_FAIL(h, HP_ERR_ARG, "batched ciphertext arrays must be device memory");
+  if (((uintptr_t)x | (uintptr_t)out | (uintptr_t)y) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  // validate the descriptors: ranges inside the batch, every ciphertext covered,
+  // slot ranges inside their ciphertexts and pairwise disjoint
+  const uint64_t N = (uint64_t)h->N;
+  std::vector<size_t> order(n_inst);
+  std::vector<uint64_t> start(n_inst);
+  std::vector<uint8_t> covered(n_ct_total, 0);
+  for (size_t i = 0; i < n_inst; ++i) {
+    const hp_instance& d = inst[i];
+    if (d.n_ct == 0 || d.ct_offset + d.n_ct > n_ct_total) HP_FAIL(h, HP_ERR_ARG, "instance %zu: ciphertext range outside the batch", i);
+    if (d.slot_offset >= N || d.slot_offset + (uint64_t)d.n_slots > (uint64_t)d.n_ct * N)
+      HP_FAIL(h, HP_ERR_ARG, "instance %zu: slot range outside its ciphertexts", i);
+    if (op == HP_EQ_CT_CONST && d.const_val >= h->t) HP_FAIL(h, HP_ERR_ARG, "instance %zu: const_val must be < t", i);
+    for (uint64_t c = d.ct_offset; c < d.ct_offset + d.n_ct; ++c) covered[c] = 1;
+    start[i] = d.ct_offset * N + d.slot_offset;
+    order[i] = i;
+  }
+  for (size_t c = 0; c < n_ct_total; ++c)
+    if (!covered[c]) HP_FAIL(h, HP_ERR_ARG, "ciphertext %zu is not covered by any instance", c);
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return start[a] < start[b]; });
+  std::vector<uint64_t> st(n_inst), cv(n_inst);
+  std::vector<uint32_t> ln(n_inst);
+  for (size_t k = 0; k < n_inst; ++k) {
+    st[k] = start[order[k]];
+    ln[k] = inst[order[k]].n_slots;
+    cv[k] = inst[order[k]].const_val;
+    if (k > 0 && st[k] < st[k - 1] + ln[k - 1]) HP_FAIL(h, HP_ERR_ARG, "instances overlap in slot space");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t *d_st = nullptr, *d_cv = nullptr;
+  uint32_t* d_ln = nullptr;
+  if (op == HP_EQ_CT_CONST) {
+    CU(h, cudaMallocAsync((void**)&d_st, n_inst * 8, s));
+    CU(h, cudaMallocAsync((void**)&d_cv, n_inst * 8, s));
+    CU(h, cudaMallocAsync((void**)&d_ln, n_inst * 4, s));
+    CU(h, cudaMemcpyAsync(d_st, st.data(), n_inst * 8, cudaMemcpyHostToDevice, s));
+    CU(h, cudaMemcpyAsync(d_cv, cv.data(), n_inst * 8, cudaMemcpyHostToDevice, s));
+    CU(h, cudaMemcpyAsync(d_ln, ln.data(), n_inst * 4, cudaMemcpyHostToDevice, s));
+  }
+  const size_t W = words_ct(h), TT = h->run_tile ? h->run_tile : h->tile;
+  uint64_t total = 0;
+  int rc = HP_OK;
+  for (size_t c0 = 0; c0 < n_ct_total && rc == HP_OK; c0 += TT) {
+    const int b = (int)((n_ct_total - c0 < TT) ? n_ct_total - c0 : TT);
+    const size_t off = c0 * W, bytes = (size_t)b * W * sizeof(uint64_t);
+    cudaGraphExec_t ex = nullptr;
+    uint64_t nk = 0;
+    rc = tile_graph(h, op == HP_EQ_CT_CT ? GM_CTCT : GM_PT, b, &ex, &nk);
+    if (rc != HP_OK) break;
+    CU(h, cudaMemcpyAsync(h->stx, x + off, bytes, cudaMemcpyDeviceToDevice, s));
+    if (op == HP_EQ_CT_CT) {
+      CU(h, cudaMemcpyAsync(h->sty, y + off, bytes, cudaMemcpyDeviceToDevice, s));
+    } else {  // per-slot constants of this tile, encoded (slots -> plaintext polynomial)
+      k_pack_slots<<<ew_blocks((size_t)b * N), EW_THREADS, 0, s>>>(d_st, d_ln, d_cv, (int)n_inst, c0, h->stm, h->logn,
+                                                                    b);
+      ntt_inv(h, h->stm, b, MAP_T, SCALE_NINV, s);
+      total += 3;
+    }
+    CU(h, cudaGraphLaunch(ex, s));
+    CU(h, cudaMemcpyAsync(out + off, h->sto, bytes, cudaMemcpyDeviceToDevice, s));
+    total += nk;
+  }
+  if (d_st) {
+    cudaFreeAsync(d_st, s);
+    cudaFreeAsync(d_cv, s);
+    cudaFreeAsync(d_ln, s);
+  }
+  h->launches = total;
+  if (rc != HP_OK) return rc;
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
+// Tile-size autotuner: times the EQ launch sequence for candidate tile sizes on
+// the handle's own staging buffers (the path is data-oblivious, so timings do
+// not depend on the data) and keeps the fastest per ciphertext.  Results are
+// cached per (ring degree, device) for the process.
+struct TuneKey {
+  int logn, device;
+  size_t maxtile, best;
+};
+static std::vector<TuneKey> g_tune;
+
+int hp_autotune(hp_handle* h, size_t* best_tile) {
+  if (!h) return HP_ERR_ARG;
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  for (auto& k : g_tune)
+    if (k.logn == h->logn && k.device == h->device && k.maxtile == h->tile) {
+      h->run_tile = k.best;
+      if (best_tile) *best_tile = k.best;
+      return HP_OK;
+    }
+  const size_t cand[] = {1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  cudaEvent_t e0, e1;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  const uint32_t saved_mask = h->prof_mask;
+  h->prof_mask = 0;
+  double best = 1e30;
+  size_t bt = h->tile;
+  std::vector<size_t> cs;
+  for (size_t c : cand)
+    if (c < h->tile) cs.push_back(c);
+  cs.push_back(h->tile);
+  for (size_t T : cs) {
+    run_tile(h, HP_EQ_CT_CT, h->stx, h->sty, 0, h->sto, (int)T, 0);  // warm-up
+    CU(h, cudaEventRecord(e0, 0));
+    for (int r = 0; r < 2; ++r) run_tile(h, HP_EQ_CT_CT, h->stx, h->sty, 0, h->sto, (int)T, 0);
+    CU(h, cudaEventRecord(e1, 0));
+    CU(h, cudaEventSynchronize(e1));
+    float ms = 0;
+    CU(h, cudaEventElapsedTime(&ms, e0, e1));
+    const double per = ms / (2.0 * T);
+    if (per < best * 0.98) {  // prefer smaller tiles unless a larger one is clearly faster
+      best = per;
+      bt = T;
+    }
+  }
+  h->prof_mask = saved_mask;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(h, hp_check_status(h) == HP_OK ? cudaSuccess : cudaErrorUnknown);
+  h->run_tile = bt;
+  g_tune.push_back({h->logn, h->device, h->tile, bt});
+  if (best_tile) *best_tile = bt;
+  return HP_OK;
 }
 
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream) {
@@ -528,7 +717,7 @@ const char* hp_last_error(const hp_handle* h) { return h ? h->err.c_str() : g_cr
 
 uint64_t hp_launch_count(const hp_handle* h) { return h ? h->launches : 0; }
 
-size_t hp_tile_size(const hp_handle* h) { return h ? h->tile : 0; }
+size_t hp_tile_size(const hp_handle* h) { return h ? (h->run_tile ? h->run_tile : h->tile) : 0; }
 
 // ---- client helpers ---------------------------------------------------------
 int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* stream) {

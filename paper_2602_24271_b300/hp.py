@@ -40,7 +40,7 @@ EXPORTED = [
     "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
-    "hp_square_noalloc",
+    "hp_square_noalloc", "hp_autotune",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -111,6 +111,7 @@ def load():
         "hp_probe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "hp_tile_size": (ctypes.c_size_t, [H]),
         "hp_square_noalloc": (ctypes.c_int, [H, P64, P64, V]),
+        "hp_autotune": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_size_t)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,6 +243,11 @@ class Context:
 
     def backward(self, op: int, grad_out, grad_x, n: int):
         return self.lib.hp_backward(self.h, op, _ptr(grad_out), _ptr(grad_x), n, None)
+
+    def autotune(self) -> int:
+        t = ctypes.c_size_t()
+        _check(self.lib.hp_autotune(self.h, ctypes.byref(t)), self.h)
+        return int(t.value)
 
     def tile(self) -> int:
         return int(self.lib.hp_tile_size(self.h))

@@ -322,6 +322,20 @@ def test_eq_const_closed_form(orc16):
     assert np.array_equal(got, (x == 7).astype(np.uint32))
 
 
+def test_eq_plain_per_slot_constants(orc16):
+    """Per-slot constants: closed form [x_j == c_j]; a uniform constant gives
+    the same ciphertext as the broadcast form (encode(c, ..., c) = c)."""
+    o = orc16
+    rng = np.random.default_rng(9)
+    x = rng.integers(0, 6, o.N).astype(np.uint32)
+    c = rng.integers(0, 6, o.N).astype(np.uint32)
+    cx = o.encrypt(x, 12, 0)
+    got = o.decrypt(o.eq_plain(cx, c))
+    assert np.array_equal(got, (x == c).astype(np.uint32))
+    uni = np.full(o.N, 4, dtype=np.uint32)
+    assert np.array_equal(o.eq_plain(cx, uni), o.eq(cx, None, const_val=4))
+
+
 def test_eq_depth_is_sixteen(orc16):
     """Fewer squarings do not give the predicate: (x - y)^(2^k) for k < 16."""
     o = orc16
