@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -49,6 +49,9 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "batched":
+        return dict(n_ct=0, op="batched", desc="batched EQ(x, y): 4096 instances, sizes log-uniform in [2^8, 2^16] slots, "
+                    "dictionary IDs in [1, 2^15], N=32768, L=15, p=65537, bit-exact; slot-packed into shared ciphertexts")
     if cfg == "const28":
         return dict(n_ct=8192, op="const", desc="EQ(x, c): 2^28 slots = 8192 BFV ciphertexts vs a broadcast constant, "
                     "N=32768, L=15 (log QP=881), p=65537, bit-exact")
@@ -204,6 +207,8 @@ def run_libhp(args):
     n_ct = args.n_ct or wl["n_ct"]
     ctx = hp.Context(LOGN, max_tile_ct=args.tile)
     ctx.keygen(SEED_KEY)
+    if not args.ncu_region:
+        ctx.autotune()
     N = ctx.N
     # inputs: rank r encrypts its own share (weak scaling, no exchange)
     x, y = eq_pair_columns(n_ct * N, seed=SEED_DATA + 1000 * rank)
@@ -374,10 +379,129 @@ def e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist):
             "seconds_per_step": secs, "path": "hp_run with pinned host buffers (library stages tiles through HBM)"}
 
 
+def run_batched(args):
+    """Config 3: uneven instances through hp_run_batched (slot-packed and one
+    ciphertext group per instance) against plain hp_run calls per instance.
+    elements = slots of the instances (the real rows compared)."""
+    import numpy as np
+    import torch
+
+    from paper_2602_24271_b300 import hp
+    from paper_2602_24271_b300.inputs import dictionary_column, log_uniform_sizes
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = workload("batched")
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile)
+    ctx.keygen(SEED_KEY)
+    tile = ctx.autotune()
+    N = ctx.N
+    sizes = log_uniform_sizes(4096, seed=2, lo_log2=8, hi_log2=16)
+    total = int(sizes.sum())
+    rng = np.random.default_rng(2)
+
+    def columns(n):
+        x = dictionary_column(n, seed=2)
+        other = dictionary_column(n, seed=3)
+        y = np.where(rng.random(n) < 0.5, x, other).astype(np.uint32)
+        return x, y
+
+    def encrypt_all(slots, n_ct, idx0):
+        out = ctx.ct_empty(n_ct)
+        for c0 in range(0, n_ct, 128):
+            c1 = min(n_ct, c0 + 128)
+            out[c0:c1] = ctx.encrypt(slots[c0 * N:c1 * N].reshape(-1, N), seed=SEED_DATA, ct_index0=idx0 + c0)
+        return out
+
+    # (a) slot-packed: instances back to back in one global slot space
+    packed, off = [], 0
+    for n in sizes:
+        ct0, so = off // N, off % N
+        packed.append((ct0, (so + int(n) + N - 1) // N, so, int(n), 0, 0))
+        off += int(n)
+    n_pk = (off + N - 1) // N
+    xs, ys = columns(n_pk * N)
+    px, py = encrypt_all(xs, n_pk, 0), encrypt_all(ys, n_pk, n_pk)
+    pout = ctx.ct_empty(n_pk)
+    # (b) one group of ciphertexts per instance
+    per, c = [], 0
+    for n in sizes:
+        k = (int(n) + N - 1) // N
+        per.append((c, k, 0, int(n), 0, 0))
+        c += k
+    n_pi = c
+    xi, yi = columns(n_pi * N)
+    ix, iy = encrypt_all(xi, n_pi, 0), encrypt_all(yi, n_pi, n_pi)
+    iout = ctx.ct_empty(n_pi)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    launches = {}
+
+    def f_packed():
+        ctx.run_batched(hp.HP_EQ_CT_CT, packed, px, py, out=pout, stream=stream)
+        launches["packed"] = ctx.launch_count()
+
+    def f_per():
+        ctx.run_batched(hp.HP_EQ_CT_CT, per, ix, iy, out=iout, stream=stream)
+        launches["per"] = ctx.launch_count()
+
+    def f_plain():
+        n = 0
+        for (c0, k, _, _, _, _) in per:
+            ctx.run(hp.HP_EQ_CT_CT, ix[c0:c0 + k], iy[c0:c0 + k], 0, out=iout[c0:c0 + k], stream=stream)
+            n += ctx.launch_count()
+        launches["plain"] = n
+
+    ms_packed = timed(f_packed, args.steps, args.warmup)
+    ms_per = timed(f_per, 1, 1)
+    ms_plain = timed(f_plain, 1, 0)
+    clk = clocks.stop()
+    ctx.check_status()
+    # closed form on sampled instances of each form
+    dec_p = ctx.decrypt(pout[:4]).reshape(-1)
+    for (ct0, k, so, n, _, _) in packed[:8]:
+        g0 = ct0 * N + so
+        if g0 + n <= 4 * N:
+            assert np.array_equal(dec_p[g0:g0 + n], (xs[g0:g0 + n] == ys[g0:g0 + n]).astype(np.uint32))
+    dec_i = ctx.decrypt(iout[:2]).reshape(-1)
+    assert np.array_equal(dec_i[:N], (xi[:N] == yi[:N]).astype(np.uint32))
+    value = total / (ms_packed / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_packed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "instances": 4096, "instance_slots": total, "ciphertexts_packed": n_pk,
+                       "ciphertexts_per_instance": n_pi, "tile_ct": tile, "l2": "inputs larger than L2"},
+            "batched_vs_plain": {
+                "packed_batched_elements_per_s": value,
+                "per_instance_batched_elements_per_s": total / (ms_per / 1e3),
+                "plain_per_instance_calls_elements_per_s": total / (ms_plain / 1e3),
+                "packed_over_plain": ms_plain / ms_packed,
+                "per_instance_batched_over_plain": ms_plain / ms_per,
+                "error": "bit-exact (integer arithmetic; parity tests vs the oracle)"},
+            "clocks": clk, "gpu_launches": launches.get("packed", 0) * args.steps,
+            "gpu_launches_by_form": launches}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_libhp(args)
 

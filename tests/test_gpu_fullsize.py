@@ -1,0 +1,89 @@
+"""Full-size parity at N = 32768 in the benchmark's launch configuration
+(autotuned tiles): the plain workload (2^26 slots = 2048 ciphertext pairs) and
+the constant form at 2^28 slots (8192 ciphertexts).  Every slot of every
+result is checked against the closed form [x == y] after GPU decryption (whose
+own parity with the oracle is tested at N = 4096 and again here on samples),
+and sampled ciphertexts are compared with the oracle bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_24271_b300 import build, hp
+from paper_2602_24271_b300.inputs import eq_pair_columns
+
+pytestmark = pytest.mark.gpu
+LOGN = 15
+SEED_KEY = 1
+
+
+@pytest.fixture(scope="module")
+def big():
+    import torch
+
+    build.build()
+    ctx = hp.Context(LOGN)
+    ctx.keygen(SEED_KEY)
+    ctx.autotune()
+    o = oracle.Oracle(LOGN)
+    o.keygen(SEED_KEY)
+    yield ctx, o
+    ctx.close()
+    torch.cuda.empty_cache()
+
+
+def encrypt_chunked(ctx, slots, n_ct, seed, idx0):
+    out = ctx.ct_empty(n_ct)
+    for c0 in range(0, n_ct, 128):
+        c1 = min(n_ct, c0 + 128)
+        out[c0:c1] = ctx.encrypt(slots[c0 * ctx.N:c1 * ctx.N].reshape(-1, ctx.N), seed=seed, ct_index0=idx0 + c0)
+    return out
+
+
+def decrypt_chunked(ctx, ct):
+    return np.concatenate([ctx.decrypt(ct[c0:c0 + 256]) for c0 in range(0, ct.shape[0], 256)])
+
+
+def test_keygen_parity_n32768(big):
+    ctx, o = big
+    sk, rk = ctx.keygen(SEED_KEY)
+    assert np.array_equal(sk.cpu().numpy(), o.s)
+    assert np.array_equal(hp.to_u64(rk), o.rk)
+
+
+def test_plain_workload_2048_pairs(big):
+    ctx, o = big
+    n_ct, N = 2048, ctx.N
+    x, y = eq_pair_columns(n_ct * N, seed=1)
+    cx = encrypt_chunked(ctx, x, n_ct, 1, 0)
+    cy = encrypt_chunked(ctx, y, n_ct, 1, n_ct)
+    out = ctx.eq(cx, cy)
+    dec = decrypt_chunked(ctx, out)
+    assert np.array_equal(dec.reshape(-1), (x == y).astype(np.uint32))
+    ctx.check_status()
+    for c in (0, 1537):  # sampled ciphertexts, bit for bit
+        assert np.array_equal(hp.to_u64(out[c]), o.eq(hp.to_u64(cx[c]), hp.to_u64(cy[c])))
+    import torch
+
+    del cx, cy, out
+    torch.cuda.empty_cache()
+
+
+def test_const_workload_2_28_slots(big):
+    import torch
+
+    ctx, o = big
+    n_ct, N, cval = 8192, ctx.N, 4242
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 1 << 16, n_ct * N, dtype=np.uint32)
+    x[rng.random(n_ct * N) < 0.25] = cval
+    cx = encrypt_chunked(ctx, x, n_ct, 3, 0)
+    out = ctx.eq(cx, None, const_val=cval)
+    ctx.check_status()
+    for c0 in range(0, n_ct, 512):
+        c1 = min(n_ct, c0 + 512)
+        dec = decrypt_chunked(ctx, out[c0:c1])
+        assert np.array_equal(dec.reshape(-1), (x[c0 * N:c1 * N] == cval).astype(np.uint32))
+    c = 8191
+    assert np.array_equal(hp.to_u64(out[c]), o.eq(hp.to_u64(cx[c]), None, const_val=cval))
+    del cx, out
+    torch.cuda.empty_cache()
