@@ -192,6 +192,7 @@ def run_libhp(args):
 
     from paper_2602_24271_b300 import hp
     from paper_2602_24271_b300.inputs import eq_pair_columns
+    from paper_2602_24271_b300.sharding import max_over_ranks, rank_seed
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -211,7 +212,7 @@ def run_libhp(args):
         ctx.autotune()
     N = ctx.N
     # inputs: rank r encrypts its own share (weak scaling, no exchange)
-    x, y = eq_pair_columns(n_ct * N, seed=SEED_DATA + 1000 * rank)
+    x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank))
     cx = ctx.ct_empty(n_ct)
     cy = ctx.ct_empty(n_ct) if wl["op"] == "ctct" else None
     chunk = 128
@@ -274,10 +275,7 @@ def run_libhp(args):
     dom_ms, dom_n, dom_work = ctx.profile_read(dom)
     ctx.profile(0)
     ctx.check_status()
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_total, dist, device="cuda")
     ms_per_step = ms_max / args.steps
     slots_all = n_ct * N * world
     value = slots_all / (ms_per_step / 1e3)
@@ -367,11 +365,7 @@ def e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.run(op, hx, hy, const_val, out=ho)
-    secs = (time.perf_counter() - t0) / args.steps
-    t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    secs = float(t.item())
+    secs = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, device="cuda")
     word = 8
     h2d = n_ct * 2 * 15 * N * word * (2 if cy is not None else 1)
     d2h = n_ct * 2 * 15 * N * word
