@@ -26,6 +26,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2602_24271_b300.sharding import max_over_ranks, rank_seed  # noqa: E402
+
 METRIC = "hot-path elements/s and % roofline, batched vs plain at stated error, 1 B300"
 UNIT = "elements/s"
 LOGN = 15
@@ -192,8 +194,6 @@ def run_libhp(args):
 
     from paper_2602_24271_b300 import hp
     from paper_2602_24271_b300.inputs import eq_pair_columns
-    from paper_2602_24271_b300.sharding import max_over_ranks, rank_seed
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

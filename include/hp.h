@@ -28,8 +28,9 @@
  *
  * Pointers: "device" arguments must be CUDA device (or managed) memory.  The
  * ciphertext arguments of hp_run may instead be host memory (pageable or
- * pinned); the library then streams them through device staging buffers and
- * returns after the last result is back in host memory.
+ * pinned); the library then streams them through two device staging sets
+ * (copy-in, compute and copy-out of consecutive tiles overlap when the host
+ * buffers are pinned) and returns after the last result is back in host memory.
  *
  * Streams: every call is ordered on the caller's `stream` (a cudaStream_t
  * passed as void*, NULL = legacy default stream).  Device-pointer calls are
@@ -89,8 +90,9 @@ int hp_default_params(uint32_t L, uint64_t* q_out, uint64_t* P_out, uint64_t* t_
  * parameters (primality, congruences, sizes) and the static depth estimate
  * (HP_ERR_DEPTH if max_depth exceeds what the modulus supports).
  * `max_tile_ct` bounds how many ciphertexts are processed per pipeline tile
- * (0 = library default); device workspace grows linearly with it (about
- * 130 MB per ciphertext at N = 32768).  `relin_key` may be NULL (set it later
+ * (0 = library default, about 5 GB of workspace); device workspace grows
+ * linearly with it (about 200 MB per ciphertext at N = 32768, including two
+ * staging sets for overlapped host-memory calls).  `relin_key` may be NULL (set it later
  * with hp_set_relin_key); otherwise it is a device pointer with the layout
  * above.  On success *out owns all device memory it allocated. */
 int hp_create(const hp_params* params, const uint64_t* relin_key, size_t max_tile_ct, hp_handle** out);
@@ -182,7 +184,7 @@ uint64_t hp_launch_count(const hp_handle* h);
 
 /* Ciphertexts per pipeline tile used by hp_run / hp_run_batched: the
  * autotuned size if hp_autotune ran, else the workspace tile chosen by
- * hp_create (max_tile_ct or the default that fits about 4 GB of workspace). */
+ * hp_create (max_tile_ct or the default that fits about 5 GB of workspace). */
 size_t hp_tile_size(const hp_handle* h);
 
 /* Synchronise the device and report the exactness status word of h (a

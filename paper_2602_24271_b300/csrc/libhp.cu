@@ -41,6 +41,10 @@ struct hp_handle {
   // staging for host-memory calls and graph-replayed tiles: x, y, out, and the
   // plaintext polynomials of packed per-instance constants ([tile][N])
   uint64_t *stx = nullptr, *sty = nullptr, *sto = nullptr, *stm = nullptr;
+  // second staging set and copy streams for overlapped host-memory calls
+  uint64_t *stx2 = nullptr, *sty2 = nullptr, *sto2 = nullptr;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   size_t run_tile = 0;  // tile used by hp_run / hp_run_batched (autotuned, <= tile; 0 = tile)
   // CUDA graphs of the whole per-tile launch sequence, keyed by (first-lift mode, tile size)
   struct GraphEntry {
@@ -138,7 +142,7 @@ static size_t ws_words_per_ct(int N) {
                       + 2 * NKS    // ksout
                       + 2 * L      // ctbuf
                       + 2 * L      // maskbuf
-                      + 3 * 2 * L  // staging x, y, out
+                      + 6 * 2 * L  // two staging sets x, y, out
                       + 1          // staging plaintext polynomials
                      );
 }
@@ -360,8 +364,16 @@ static void free_all(hp_handle* h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->h2d) cudaStreamDestroy(h->h2d);
+  if (h->d2h) cudaStreamDestroy(h->d2h);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+    if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+    if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+  }
   void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
-                  h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm};
+                  h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
+                  h->stx2, h->sty2, h->sto2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
@@ -428,7 +440,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
 
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
   size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
-  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)4 << 30) / per);  // ~4 GB of workspace
+  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)5 << 30) / per);  // ~5 GB of workspace
   if (h->tile < 1) h->tile = 1;
   if (h->tile > 64) h->tile = 64;
   const size_t T = h->tile, N = h->N;
@@ -439,6 +451,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
                 {&h->w3, T * 3 * L * N},     {&h->ksin, T * L * NKS * N}, {&h->ksout, T * 2 * NKS * N},
                 {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
                 {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
+                {&h->stx2, T * 2 * L * N},   {&h->sty2, T * 2 * L * N},   {&h->sto2, T * 2 * L * N},
                 {&h->rkm, (size_t)L * 2 * NKS * N}};
   for (auto& a : allocs) {
     if (cudaMalloc(a.p, a.words * sizeof(uint64_t)) != cudaSuccess) {
@@ -504,20 +517,55 @@ int hp_run(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t 
   if (dev != is_device_ptr(out) || ((op == HP_EQ_CT_CT || op == HP_SELECT) && dev != is_device_ptr(y)))
     HP_FAIL(h, HP_ERR_ARG, "ciphertext arguments must all be device memory or all host memory");
   const size_t TT = h->run_tile ? h->run_tile : h->tile;
-  for (size_t c0 = 0; c0 < n_ct; c0 += TT) {
+  if (dev) {
+    for (size_t c0 = 0; c0 < n_ct; c0 += TT) {
+      const int b = (int)((n_ct - c0 < TT) ? n_ct - c0 : TT);
+      const size_t off = c0 * W;
+      run_tile(h, op, x + off, y ? y + off : nullptr, cval, out + off, b, s);
+      CU(h, cudaGetLastError());
+    }
+    return HP_OK;
+  }
+  // Host memory: two staging sets; tile k copies in on the h2d stream, computes
+  // on the caller's stream, copies out on the d2h stream, so that with pinned
+  // buffers the copies of tiles k-1 / k+1 overlap the compute of tile k.
+  if (!h->h2d) {
+    CU(h, cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+    CU(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CU(h, cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming));
+      CU(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
+      CU(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  uint64_t* SX[2] = {h->stx, h->stx2};
+  uint64_t* SY[2] = {h->sty, h->sty2};
+  uint64_t* SO[2] = {h->sto, h->sto2};
+  const bool two = op == HP_EQ_CT_CT || op == HP_SELECT;
+  CU(h, cudaEventRecord(h->ev_done[0], s));  // staging free (orders after earlier work on s)
+  CU(h, cudaEventRecord(h->ev_done[1], s));
+  CU(h, cudaEventRecord(h->ev_out[0], s));
+  CU(h, cudaEventRecord(h->ev_out[1], s));
+  size_t k = 0;
+  for (size_t c0 = 0; c0 < n_ct; c0 += TT, ++k) {
+    const int i = (int)(k & 1);
     const int b = (int)((n_ct - c0 < TT) ? n_ct - c0 : TT);
     const size_t off = c0 * W, bytes = (size_t)b * W * sizeof(uint64_t);
-    if (dev) {
-      run_tile(h, op, x + off, y ? y + off : nullptr, cval, out + off, b, s);
-    } else {
-      CU(h, cudaMemcpyAsync(h->stx, x + off, bytes, cudaMemcpyHostToDevice, s));
-      if (op == HP_EQ_CT_CT || op == HP_SELECT) CU(h, cudaMemcpyAsync(h->sty, y + off, bytes, cudaMemcpyHostToDevice, s));
-      run_tile(h, op, h->stx, h->sty, cval, h->sto, b, s);
-      CU(h, cudaMemcpyAsync(out + off, h->sto, bytes, cudaMemcpyDeviceToHost, s));
-    }
+    CU(h, cudaStreamWaitEvent(h->h2d, h->ev_done[i], 0));  // inputs of tile k-2 consumed
+    CU(h, cudaMemcpyAsync(SX[i], x + off, bytes, cudaMemcpyHostToDevice, h->h2d));
+    if (two) CU(h, cudaMemcpyAsync(SY[i], y + off, bytes, cudaMemcpyHostToDevice, h->h2d));
+    CU(h, cudaEventRecord(h->ev_in[i], h->h2d));
+    CU(h, cudaStreamWaitEvent(s, h->ev_in[i], 0));
+    CU(h, cudaStreamWaitEvent(s, h->ev_out[i], 0));  // outputs of tile k-2 copied out
+    run_tile(h, op, SX[i], SY[i], cval, SO[i], b, s);
+    CU(h, cudaEventRecord(h->ev_done[i], s));
+    CU(h, cudaStreamWaitEvent(h->d2h, h->ev_done[i], 0));
+    CU(h, cudaMemcpyAsync(out + off, SO[i], bytes, cudaMemcpyDeviceToHost, h->d2h));
+    CU(h, cudaEventRecord(h->ev_out[i], h->d2h));
     CU(h, cudaGetLastError());
   }
-  if (!dev) CU(h, cudaStreamSynchronize(s));
+  CU(h, cudaStreamSynchronize(h->d2h));
+  CU(h, cudaStreamSynchronize(s));
   return HP_OK;
 }
 
