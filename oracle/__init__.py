@@ -79,6 +79,9 @@ def _load():
         "orc_eq": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_uint64, ctypes.c_int, _u64p]),
         "orc_square_chain": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p]),
         "orc_eq_plain": (ctypes.c_int, [V, _u64p, _u32p, ctypes.c_int, _u64p]),
+        "orc_lt_coefficients": (ctypes.c_int, [V, _u32p]),
+        "orc_linear": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p, ctypes.c_uint64, _u64p]),
+        "orc_lt": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_tensor_round": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_relin": (ctypes.c_int, [V, _u64p, _u64p]),
     }
@@ -280,6 +283,28 @@ class Oracle:
         if self.lib.orc_eq_plain(self.h, _p(X, ctypes.c_uint64), _p(C, ctypes.c_uint32), squarings,
                                  _p(out, ctypes.c_uint64)) != 0:
             raise RuntimeError("relinearisation key not set")
+        return out
+
+    def lt_coefficients(self) -> np.ndarray:
+        """h_m = c_{2m+1} of the LT polynomial (Eq. 4), m < (t-1)/2."""
+        out = np.zeros((self.t - 1) // 2, dtype=np.uint32)
+        self.lib.orc_lt_coefficients(self.h, _p(out, ctypes.c_uint32))
+        return out
+
+    def linear(self, cts, coef, coef0: int = 0):
+        """sum_i coef[i] cts[i] + (Delta coef0, 0), coefficients < t."""
+        C = _c(cts, np.uint64)
+        k = _c(coef, np.uint64)
+        out = self._ct_out()
+        self.lib.orc_linear(self.h, _p(C, ctypes.c_uint64), len(k), _p(k, ctypes.c_uint64), coef0, _p(out, ctypes.c_uint64))
+        return out
+
+    def lt(self, x, y):
+        """LT(x, y) (Eq. 4) by the baby-step / giant-step schedule of the library."""
+        X, Y, out = _c(x, np.uint64), _c(y, np.uint64), self._ct_out()
+        rc = self.lib.orc_lt(self.h, _p(X, ctypes.c_uint64), _p(Y, ctypes.c_uint64), _p(out, ctypes.c_uint64))
+        if rc != 0:
+            raise RuntimeError("orc_lt failed (%d)" % rc)
         return out
 
     def square_chain(self, x, squarings: int):

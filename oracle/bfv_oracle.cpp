@@ -496,6 +496,7 @@ struct Ctx {
   std::vector<Poly> rk0, rk1;     // rk_i = (rk0[i], rk1[i]) mod QP, i < L
   int rk_nprimes = 0;
   std::vector<uint64_t> rk_ntt;   // [i][comp][prime][N]
+  std::vector<uint32_t> lt_h;     // LT polynomial's odd coefficients (computed on first use)
 };
 
 static int primes_needed(const Ctx& c, int bound_bits) {
@@ -1055,6 +1056,149 @@ int orc_eq_plain(void* h, const uint64_t* x, const uint32_t* cslots, int squarin
   ct_to_rns(c, ct_one_minus(c, d), out);
   return 0;
 }
+
+// ---------------------------------------------------------------------------
+// LT comparison (Eq. 4): LT(x, y) = sum_{a = -(p-1)/2}^{-1} (1 - (x - y - a)^(p-1)).
+// As a polynomial in z = x - y over F_p (binomial coefficients C(p-1, k) = (-1)^k):
+//   f(z) = sum_{k=1}^{p-1} c_k z^k,  c_k = -sum_{a in A} a^(p-1-k),  A = {-1, ..., -(p-1)/2},
+// so c_k = sum_{b=1}^{(p-1)/2} b^(p-1-k) for odd k, c_k = 0 for even k < p-1, and
+// c_{p-1} = -(p-1)/2.  With w = z^2:  f(z) = z h(w) - ((p-1)/2) w^((p-1)/2),
+// h(w) = sum_m c_{2m+1} w^m.
+// ---------------------------------------------------------------------------
+static std::vector<uint32_t> lt_odd_coefficients(uint64_t p) {
+  // h_m = c_{2m+1} = sum_{b=1}^{(p-1)/2} b^(p-2-2m) mod p, m < (p-1)/2 (plain power sums)
+  const uint64_t half = (p - 1) / 2;
+  std::vector<uint64_t> acc(half, 0);
+  for (uint64_t b = 1; b <= half; ++b) {
+    const uint64_t b2inv = invmod(b * b % p, p);  // b^(p-2-2m) = b^(p-2) * (b^-2)^m
+    uint64_t v = invmod(b, p);                    // b^(p-2)
+    for (uint64_t m = 0; m < half; ++m) {
+      acc[m] += v;
+      v = v * b2inv % p;
+    }
+    if ((b & 1023) == 0)
+      for (uint64_t m = 0; m < half; ++m) acc[m] %= p;
+  }
+  std::vector<uint32_t> h(half);
+  for (uint64_t m = 0; m < half; ++m) h[m] = (uint32_t)(acc[m] % p);
+  return h;
+}
+
+// c * ct for an integer c in [0, t), coefficient-wise mod Q
+static Ct ct_scale(const Ctx& c, const Ct& a, uint64_t k) {
+  Ct r;
+  r.c0.resize(c.N);
+  r.c1.resize(c.N);
+  for (int j = 0; j < c.N; ++j) {
+    r.c0[j] = mod_Q(c, big_mul_u64(a.c0[j], k));
+    r.c1[j] = mod_Q(c, big_mul_u64(a.c1[j], k));
+  }
+  return r;
+}
+static Ct ct_add(const Ctx& c, const Ct& a, const Ct& b) {
+  Ct r;
+  r.c0.resize(c.N);
+  r.c1.resize(c.N);
+  for (int j = 0; j < c.N; ++j) {
+    r.c0[j] = mod_Q(c, big_add(a.c0[j], b.c0[j]));
+    r.c1[j] = mod_Q(c, big_add(a.c1[j], b.c1[j]));
+  }
+  return r;
+}
+// (Delta k, 0): the encryption-free plaintext constant k
+static Ct ct_constant(const Ctx& c, uint64_t k) {
+  Ct r;
+  r.c0.assign(c.N, big_zero());
+  r.c1.assign(c.N, big_zero());
+  r.c0[0] = mod_Q(c, big_mul_u64(c.Delta, k % c.t));
+  return r;
+}
+
+// sum_i coef[i] * cts[i] + (Delta coef0, 0), evaluated on residues: Z_Q is
+// isomorphic to prod Z_{q_i}, so scalar multiply-accumulate is exact per prime.
+static Ct ct_linear(const Ctx& c, const std::vector<const Ct*>& cts, const std::vector<uint64_t>& coef, uint64_t coef0) {
+  const size_t W = (size_t)2 * c.L * c.N;
+  std::vector<unsigned __int128> acc(W, 0);
+  std::vector<uint64_t> buf(W);
+  for (size_t i = 0; i < cts.size(); ++i) {
+    if (coef[i] == 0) continue;
+    ct_to_rns(c, *cts[i], buf.data());
+    for (size_t w = 0; w < W; ++w) acc[w] += (unsigned __int128)buf[w] * coef[i];
+  }
+  for (int i = 0; i < c.L; ++i)
+    for (int comp = 0; comp < 2; ++comp)
+      for (int j = 0; j < c.N; ++j) {
+        size_t w = ((size_t)comp * c.L + i) * c.N + j;
+        buf[w] = (uint64_t)(acc[w] % c.q[i]);
+      }
+  Ct r = ct_from_rns(c, buf.data());
+  return ct_add(c, r, ct_constant(c, coef0));
+}
+
+// The evaluation schedule of f(z) (both the oracle and the CUDA library follow it):
+//   w = z z;  B_1 = w;  B_i = B_{i/2}^2 (i even) or B_{i-1} B_1 (i odd), i < 256;
+//   G_1 = B_128^2 (= w^256);  G_j = G_{j/2}^2 (j even) or G_{j-1} G_1 (j odd), j <= 128;
+//   H_j = Delta h_{256 j} + sum_{i=1}^{255} h_{256 j + i} B_i   (j < 128);
+//   h = H_0 + sum_{j=1}^{127} H_j G_j;   out = z h - ((p-1)/2) G_128.
+static Ct lt_eval(const Ctx& c, const Ct& z, const std::vector<uint32_t>& hc) {
+  const int BS = 256, GS = 128;
+  Ct w = ct_mul_relin(c, z, z);
+  std::vector<Ct> B(BS), G(GS + 1);
+  B[1] = w;
+  for (int i = 2; i < BS; ++i) B[i] = (i % 2 == 0) ? ct_mul_relin(c, B[i / 2], B[i / 2]) : ct_mul_relin(c, B[i - 1], B[1]);
+  G[1] = ct_mul_relin(c, B[128], B[128]);
+  for (int j = 2; j <= GS; ++j) G[j] = (j % 2 == 0) ? ct_mul_relin(c, G[j / 2], G[j / 2]) : ct_mul_relin(c, G[j - 1], G[1]);
+  std::vector<const Ct*> ptrs;
+  for (int i = 1; i < BS; ++i) ptrs.push_back(&B[i]);
+  Ct h;
+  for (int j = 0; j < GS; ++j) {
+    std::vector<uint64_t> coef(BS - 1);
+    for (int i = 1; i < BS; ++i) coef[i - 1] = hc[(size_t)BS * j + i];
+    Ct Hj = ct_linear(c, ptrs, coef, hc[(size_t)BS * j]);
+    h = (j == 0) ? Hj : ct_add(c, h, ct_mul_relin(c, Hj, G[j]));
+  }
+  Ct g = ct_mul_relin(c, z, h);
+  return ct_add(c, g, ct_scale(c, G[GS], c.t - (c.t - 1) / 2));  // - ((p-1)/2) w^((p-1)/2)
+}
+
+extern "C" {
+// h_m = c_{2m+1} of the LT polynomial, m < (t-1)/2 (t = 65537: 32768 words)
+static const std::vector<uint32_t>& lt_coeffs(Ctx& c) {
+  if (c.lt_h.empty()) c.lt_h = lt_odd_coefficients(c.t);
+  return c.lt_h;
+}
+int orc_lt_coefficients(void* h, uint32_t* out) {
+  Ctx& c = *(Ctx*)h;
+  const std::vector<uint32_t>& v = lt_coeffs(c);
+  std::copy(v.begin(), v.end(), out);
+  return 0;
+}
+// linear combination of n ciphertexts (residue layout [n][2][L][N]) with
+// coefficients coef[i] < t plus the constant (Delta coef0, 0)
+int orc_linear(void* h, const uint64_t* cts, int n, const uint64_t* coef, uint64_t coef0, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  const size_t W = (size_t)2 * c.L * c.N;
+  std::vector<Ct> v(n);
+  std::vector<const Ct*> p(n);
+  std::vector<uint64_t> k(coef, coef + n);
+  for (int i = 0; i < n; ++i) {
+    v[i] = ct_from_rns(c, cts + i * W);
+    p[i] = &v[i];
+  }
+  ct_to_rns(c, ct_linear(c, p, k, coef0), out);
+  return 0;
+}
+// LT(x, y) = [x - y in {-(t-1)/2 .. -1}] by the schedule above (t = 65537)
+int orc_lt(void* h, const uint64_t* x, const uint64_t* y, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk) return -2;
+  if (c.t != 65537) return -1;
+  const std::vector<uint32_t>& hc = lt_coeffs(c);
+  Ct z = ct_sub(c, ct_from_rns(c, x), ct_from_rns(c, y));
+  ct_to_rns(c, lt_eval(c, z, hc), out);
+  return 0;
+}
+}  // extern "C"
 
 // Squarings only (no difference, no "1 -"): for noise-depth tests.
 int orc_square_chain(void* h, const uint64_t* x, int squarings, uint64_t* out) {

@@ -362,3 +362,57 @@ def test_depth_overflow_decrypts_wrongly():
         ok_at[k] = np.array_equal(got, np.array([pow(int(v), 2**k, T) for v in x], dtype=np.uint32))
     assert ok_at[1] and ok_at[2]
     assert not ok_at[8]
+
+
+# --------------------------------------------------------------------------
+# LT comparison (Eq. 4) -- the first row beyond equality
+# --------------------------------------------------------------------------
+def _lt_poly(h, z, p=T):
+    """f(z) = z h(z^2) - ((p-1)/2) z^(p-1), by Horner over the odd coefficients."""
+    w = z * z % p
+    acc = 0
+    for m in range(len(h) - 1, -1, -1):
+        acc = (acc * w + int(h[m])) % p
+    return (z * acc - (p - 1) // 2 * pow(w, (p - 1) // 2, p)) % p
+
+
+def test_lt_polynomial_is_the_paper_sum(orc16):
+    """The coefficients reproduce Eq. 4 as a function on F_p: f(z) = [z in {-(p-1)/2..-1}]."""
+    h = orc16.lt_coefficients()
+    assert len(h) == (T - 1) // 2
+    rng = np.random.default_rng(11)
+    zs = [0, 1, 2, T - 1, T - 2, (T - 1) // 2, (T + 1) // 2, (T - 3) // 2, (T + 3) // 2]
+    zs += [int(v) for v in rng.integers(0, T, 12)]
+    for z in zs:
+        assert _lt_poly(h, z) == (1 if z >= (T + 1) // 2 else 0), z
+    # direct evaluation of Eq. 4 (sum over a of 1 - (z - a)^(p-1)) at a few points
+    for z in (0, 3, T - 3):
+        direct = sum(1 - pow((z - a) % T, T - 1, T) for a in range(-(T - 1) // 2, 0)) % T
+        assert _lt_poly(h, z) == direct
+
+
+def test_linear_combination_closed_form(orc16):
+    o = orc16
+    rng = np.random.default_rng(12)
+    xs = [rng.integers(0, T, o.N).astype(np.uint32) for _ in range(3)]
+    cts = np.stack([o.encrypt(x, 13, i) for i, x in enumerate(xs)])
+    coef = [5, T - 1, 40000]
+    got = o.decrypt(o.linear(cts, coef, coef0=7))
+    ref = (sum(int(k) * x.astype(object) for k, x in zip(coef, xs)) + 7) % T
+    assert np.array_equal(got, ref.astype(np.uint32))
+
+
+def test_lt_closed_form_n16(orc16):
+    """Oracle LT decrypts to [x < y] for x, y in [0, 2^15] (the valid domain:
+    the true difference must lie in [-(p-1)/2, (p-1)/2])."""
+    o = orc16
+    rng = np.random.default_rng(13)
+    x = rng.integers(0, (T - 1) // 2 + 1, o.N).astype(np.uint32)
+    y = rng.integers(0, (T - 1) // 2 + 1, o.N).astype(np.uint32)
+    pairs = [(5, 3), (3, 5), (0, 32768), (32768, 0), (7, 7), (100, 101), (101, 100), (0, 0)]
+    for i, (a, b) in enumerate(pairs):
+        x[i], y[i] = a, b
+    cx, cy = o.encrypt(x, 14, 0), o.encrypt(y, 14, 1)
+    got, nb = o.decrypt(o.lt(cx, cy), with_noise=True)
+    assert np.array_equal(got, (x < y).astype(np.uint32))
+    assert nb > 0
