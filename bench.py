@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +51,9 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "lt":
+        return dict(n_ct=64, op="lt", desc="LT(x, y) = [x < y] (Eq. 4): 2^21 slots = 64 BFV ciphertext pairs, "
+                    "x, y in [0, 2^15], N=32768, L=15, p=65537; 511 multiplications per ciphertext, bit-exact")
     if cfg == "batched":
         return dict(n_ct=0, op="batched", desc="batched EQ(x, y): 4096 instances, sizes log-uniform in [2^8, 2^16] slots, "
                     "dictionary IDs in [1, 2^15], N=32768, L=15, p=65537, bit-exact; slot-packed into shared ciphertexts")
@@ -212,9 +215,9 @@ def run_libhp(args):
         ctx.autotune()
     N = ctx.N
     # inputs: rank r encrypts its own share (weak scaling, no exchange)
-    x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank))
+    x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank), value_bits=15 if wl["op"] == "lt" else 16)
     cx = ctx.ct_empty(n_ct)
-    cy = ctx.ct_empty(n_ct) if wl["op"] == "ctct" else None
+    cy = ctx.ct_empty(n_ct) if wl["op"] in ("ctct", "lt") else None
     chunk = 128
     for c0 in range(0, n_ct, chunk):
         c1 = min(n_ct, c0 + chunk)
@@ -227,7 +230,9 @@ def run_libhp(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        if cy is not None:
+        if wl["op"] == "lt":
+            ctx.run(hp.HP_LT, cx, cy, 0, out=out, stream=stream)
+        elif cy is not None:
             ctx.run(hp.HP_EQ_CT_CT, cx, cy, 0, out=out, stream=stream)
         else:
             ctx.run(hp.HP_EQ_CT_CONST, cx, None, const_val, out=out, stream=stream)
@@ -285,7 +290,10 @@ def run_libhp(args):
     dec = ctx.decrypt(out[probe])
     for k, c in enumerate(probe):
         xs = x[c * N:(c + 1) * N]
-        ref = (xs == y[c * N:(c + 1) * N]) if cy is not None else (xs == const_val)
+        if wl["op"] == "lt":
+            ref = xs < y[c * N:(c + 1) * N]
+        else:
+            ref = (xs == y[c * N:(c + 1) * N]) if cy is not None else (xs == const_val)
         assert np.array_equal(dec[k], ref.astype(np.uint32)), "EQ result wrong in benchmark run"
 
     # ---- roofline of the dominant kernel ----
@@ -325,7 +333,7 @@ def run_libhp(args):
             "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
 
     # ---- end to end through the public API with pinned host buffers ----
-    if not args.no_e2e:
+    if not args.no_e2e and wl["op"] != "lt":
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:

@@ -78,7 +78,8 @@ typedef enum {
   HP_EQ_CT_CT = 0,    /* EQ(x, y) = 1 - (x - y)^(p-1), Eq. 3 */
   HP_EQ_CT_CONST = 1, /* EQ(x, c) with c broadcast to every slot */
   HP_SELECT = 2,      /* y * EQ(x, c): the SELECT tail of Eq. 5; ct_y is the column */
-  HP_SQUARE = 3       /* one squaring + relinearisation (building block, for tests) */
+  HP_SQUARE = 3,      /* one squaring + relinearisation (building block, for tests) */
+  HP_LT = 4           /* LT(x, y) = [x < y], Eq. 4, for x, y in [0, (p-1)/2] (depth 18) */
 } hp_op;
 
 /* Fill q_out[0..L) and *P_out with the default primes (largest primes below
@@ -107,6 +108,14 @@ int hp_set_relin_key(hp_handle* h, const uint64_t* relin_key_dev);
  *   HP_EQ_CT_CONST out[i] = EQ(x[i], const_val)           (y ignored, may be NULL)
  *   HP_SELECT      out[i] = y[i] * EQ(x[i], const_val)    (depth 17)
  *   HP_SQUARE      out[i] = relin(x[i]^2)                  (y ignored)
+ *   HP_LT          out[i] = LT(x[i], y[i]) = [x < y] slot-wise (Eq. 4), valid
+ *                  when x - y lies in [-(p-1)/2, (p-1)/2] (inputs below 2^15 + 1);
+ *                  the polynomial f(z) = z h(z^2) - ((p-1)/2) z^(p-1) of Eq. 4
+ *                  is evaluated by baby steps (255 powers of z^2) and giant
+ *                  steps (128 powers of z^512): 511 multiplications, depth 18.
+ *                  Device memory only; the first call allocates its workspace
+ *                  (about 3.1 GB per ciphertext of the LT tile, tile <= 8 at
+ *                  N = 32768).
  * ct_x, ct_y, ct_out: [n_ct][2][L][N]; all device memory, or all host memory
  * (then the call is synchronous).  ct_out may alias ct_x or ct_y.  n_ct = 0
  * is a no-op.  const_val must be < t.  Requires the relinearisation key. */
@@ -181,6 +190,10 @@ int hp_decrypt(hp_handle* h, const int8_t* sk, const uint64_t* ct, size_t n_ct, 
 /* Number of kernel launches issued by the last hp_run / hp_run_batched call on
  * h (for launch accounting). */
 uint64_t hp_launch_count(const hp_handle* h);
+
+/* The 32768 odd coefficients h_m = c_{2m+1} of the LT polynomial of Eq. 4 over
+ * F_65537 (c_k = sum_{b=1}^{32768} b^(p-1-k)); host computation, no GPU. */
+int hp_lt_coefficients(uint32_t* out);
 
 /* Ciphertexts per pipeline tile used by hp_run / hp_run_batched: the
  * autotuned size if hp_autotune ran, else the workspace tile chosen by

@@ -49,6 +49,7 @@ struct Consts {
   uint64_t half_digit[L];                   // mixed-radix digits of (Q-1)/2
   // relinearisation mod-down
   uint64_t Pinv[L], Pinv_s[L];  // [P^{-1}]_{q_i}
+  uint64_t r32[L], r32_s[L];    // [2^32]_{q_i} (reduction of split 64-bit sums)
   // plaintext side
   uint64_t delta[L], delta_s[L];          // [floor(Q/t)]_{q_i}
   uint64_t tqhatinv[L], tqhatinv_s[L];    // [t (Q/q_i)^{-1}]_{q_i}   (decryption)
@@ -74,6 +75,9 @@ uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t m);
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);
 uint64_t h_invmod(uint64_t a, uint64_t m);
 uint64_t h_shoup(uint64_t w, uint64_t p);
+
+// LT polynomial's odd coefficients (32768 words), see hp_host.cpp.
+int lt_coefficients(uint32_t* out);
 
 // Static noise estimate: how many successive squarings (each relinearised)
 // the parameters support with a positive invariant-noise budget, from the

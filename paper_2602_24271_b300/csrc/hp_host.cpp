@@ -1,6 +1,8 @@
 // Host-side parameter logic of libhp: prime search, the constant block for the
 // exact RNS conversions, and the static depth estimate.
 #include <math.h>
+#include <algorithm>
+#include <vector>
 #include <stdio.h>
 #include <string.h>
 
@@ -201,6 +203,8 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
   for (int i = 0; i < L; ++i) {
     C->Pinv[i] = h_invmod(P % q[i], q[i]);
     C->Pinv_s[i] = h_shoup(C->Pinv[i], q[i]);
+    C->r32[i] = (uint64_t)(((unsigned __int128)1 << 32) % q[i]);
+    C->r32_s[i] = h_shoup(C->r32[i], q[i]);
     C->Pmodq[i] = P % q[i];
     tinvq = h_invmod(t, q[i]);
     C->delta[i] = h_mulmod((q[i] - rt % q[i]) % q[i], tinvq, q[i]);  // (Q - rt)/t mod q_i
@@ -228,6 +232,40 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->negBQ_h[i] = (uint32_t)(C->negBQ[i] >> 28);
   }
   C->Qinv_t = h_invmod(Qt, t);
+  return 0;
+}
+
+// Odd coefficients h_m = c_{2m+1} (m < 32768) of the LT polynomial over F_65537:
+// c_k = sum_{b=1}^{32768} b^(p-1-k) for odd k.  All power sums S(e) = sum_{b<=32768}
+// b^e come from one cyclic transform of length p - 1 = 2^16 with root g = 3 (a
+// generator of F_p^*): writing b = g^u, S(e) = sum_u [g^u <= 32768] (g^e)^u.
+int lt_coefficients(uint32_t* out) {
+  const uint64_t p = 65537, n = 65536, g = 3;
+  std::vector<uint64_t> a(n, 0);
+  uint64_t x = 1;
+  for (uint64_t u = 0; u < n; ++u) {
+    a[u] = x <= (p - 1) / 2 ? 1 : 0;
+    x = x * g % p;
+  }
+  for (uint64_t i = 1, j = 0; i < n; ++i) {  // bit-reversal permutation
+    uint64_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (uint64_t len = 2; len <= n; len <<= 1) {  // DIT butterflies, root of order len = g^(n/len)
+    const uint64_t wl = h_powmod(g, n / len, p);
+    for (uint64_t st = 0; st < n; st += len) {
+      uint64_t w = 1;
+      for (uint64_t k = 0; k < len / 2; ++k) {
+        const uint64_t u = a[st + k], v = a[st + k + len / 2] * w % p;
+        a[st + k] = (u + v) % p;
+        a[st + k + len / 2] = (u + p - v) % p;
+        w = w * wl % p;
+      }
+    }
+  }
+  for (uint64_t m = 0; m < (p - 1) / 2; ++m) out[m] = (uint32_t)a[(p - 2 - 2 * m) % n];
   return 0;
 }
 

@@ -287,6 +287,69 @@ __global__ void k_pack_slots(const uint64_t* __restrict__ start, const uint32_t*
   M[gid] = (f >= 0 && g < start[f] + len[f]) ? cval[f] : 0;
 }
 
+// ---- ciphertext-level linear operations (LT comparison) -----------------------
+// Word w of an array of ciphertexts [b][2][L][N] lives mod q_{(w >> logN) % L}.
+HPD int prime_of_word(size_t w, int logN) { return (int)((w >> logN) % L); }
+
+// out = a - b (or a + b)
+__global__ void k_ct_addsub(const uint64_t* __restrict__ a, const uint64_t* __restrict__ b, uint64_t* __restrict__ out,
+                            int subtract, int logN, size_t nwords) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwords) return;
+  const uint64_t q = cK.p[prime_of_word(w, logN)];
+  out[w] = subtract ? sub_mod(a[w], b[w], q) : add_mod(a[w], b[w], q);
+}
+
+// out = g + k G  for a small integer k (Shoup companions per prime passed by value)
+struct ScalarK {
+  uint64_t k[L], ks[L];
+};
+__global__ void k_ct_axpy(const uint64_t* __restrict__ g, const uint64_t* __restrict__ G, uint64_t* __restrict__ out,
+                          ScalarK sk, int logN, size_t nwords) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwords) return;
+  const int i = prime_of_word(w, logN);
+  const uint64_t q = cK.p[i];
+  out[w] = add_mod(g[w], mul_shoup(G[w], sk.k[i], sk.ks[i], q), q);
+}
+
+// Eight inner sums of the baby-step / giant-step evaluation at once:
+//   out_jj = (Delta coef[256 (j0+jj)], 0) + sum_{i=1}^{255} coef[256 (j0+jj) + i] B_i,  jj < 8.
+// B: [255][bw] (bw = words of one tile of ciphertexts), out: [8][bw].  Each
+// coefficient is < 2^17 and each word < 2^56, split in 32-bit halves: the two
+// 64-bit sums of 255 terms stay below 2^57.
+constexpr int LT_J = 8;
+__global__ void __launch_bounds__(EW_THREADS) k_lt_inner(const uint64_t* __restrict__ B, const uint32_t* __restrict__ coef,
+                                                         int j0, uint64_t* __restrict__ out, int logN, size_t bw) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= bw) return;
+  uint64_t lo[LT_J], hi[LT_J];
+#pragma unroll
+  for (int jj = 0; jj < LT_J; ++jj) lo[jj] = hi[jj] = 0;
+  const uint32_t* c = coef + (size_t)256 * j0;
+  for (int i = 1; i < 256; ++i) {
+    const uint64_t v = B[(size_t)(i - 1) * bw + w];
+    const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
+#pragma unroll
+    for (int jj = 0; jj < LT_J; ++jj) {
+      const uint32_t k = __ldg(c + 256 * jj + i);
+      lo[jj] += (uint64_t)vl * k;
+      hi[jj] += (uint64_t)vh * k;
+    }
+  }
+  const int ip = prime_of_word(w, logN);
+  const uint64_t q = cK.p[ip], pbar = cK.pbar[ip];
+  const bool const_slot = ((w >> logN) / L) % 2 == 0 && (w & ((1 << logN) - 1)) == 0;  // c0, coefficient 0
+#pragma unroll
+  for (int jj = 0; jj < LT_J; ++jj) {
+    uint64_t r = mul_shoup(hi[jj], cK.r32[ip], cK.r32_s[ip], q);  // hi 2^32 mod q
+    uint64_t t = lo[jj] - __umul64hi(lo[jj], pbar) * q;             // lo mod q, in [0, 2q)
+    r = csub(csub(r + t, q), q);
+    if (const_slot) r = add_mod(r, mul_shoup(c[256 * jj], cK.delta[ip], cK.delta_s[ip], q), q);
+    out[(size_t)jj * bw + w] = r;
+  }
+}
+
 // "1 -" alone: out = (Delta - c0, -c1).  One thread per word of [nct][2][L][N].
 __global__ void __launch_bounds__(EW_THREADS) k_one_minus(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                           int logN, int nct) {

@@ -54,6 +54,11 @@ struct hp_handle {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t cap = nullptr;
+  // LT comparison: baby-step (255), giant-step (128), inner-sum (8) and three
+  // temporary ciphertext arrays per tile, allocated on the first LT call
+  uint64_t* ltws = nullptr;
+  size_t lt_tile = 0;
+  uint32_t* lt_coef = nullptr;  // 32768 odd coefficients of the LT polynomial
   int* status = nullptr;  // device status word (ST_* bits)
   uint64_t launches = 0;
   std::string err;
@@ -294,6 +299,98 @@ static void run_tile(hp_handle* h, int op, const uint64_t* x, const uint64_t* y,
 }
 
 // ---------------------------------------------------------------------------
+// LT comparison (Eq. 4) on a tile of b ciphertext pairs: f(z) = z h(w) -
+// 32768 w^32768 with z = x - y, w = z^2, evaluated by the baby-step /
+// giant-step schedule documented with the oracle (511 multiplications,
+// depth 18):
+//   B_1 = w, B_i = B_{i/2}^2 (even i) or B_{i-1} B_1 (odd i), i < 256;
+//   G_1 = B_128^2, G_j = G_{j/2}^2 (even j) or G_{j-1} G_1 (odd j), j <= 128;
+//   H_j = (Delta h_{256j}, 0) + sum_i h_{256j+i} B_i;  h = H_0 + sum_{j>=1} H_j G_j.
+// ---------------------------------------------------------------------------
+static void hsquare(hp_handle* h, const uint64_t* a, uint64_t* out, int b, cudaStream_t s) {
+  lift(h, a, nullptr, 0, LIFT_COPY, h->ext, b, s);
+  mul_relin_tail(h, b, false, out, 0, s);
+}
+static void hmul(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64_t* out, int b, cudaStream_t s) {
+  lift(h, a, nullptr, 0, LIFT_COPY, h->ext, b, s);
+  lift(h, c, nullptr, 0, LIFT_COPY, h->ext2, b, s);
+  mul_relin_tail(h, b, true, out, 0, s);
+}
+static void ct_addsub(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64_t* out, int subtract, int b,
+                      cudaStream_t s) {
+  const size_t nw = (size_t)b * words_ct(h);
+  k_ct_addsub<<<ew_blocks(nw), EW_THREADS, 0, s>>>(a, c, out, subtract, h->logn, nw);
+  h->launches += 1;
+}
+
+static void run_lt_tile(hp_handle* h, const uint64_t* x, const uint64_t* y, uint64_t* out, int b, cudaStream_t s) {
+  const size_t W = words_ct(h), bw = (size_t)b * W, T = h->lt_tile * W;
+  uint64_t* Bp = h->ltws;              // B_1 .. B_255
+  uint64_t* Gp = Bp + 255 * T;         // G_1 .. G_128
+  uint64_t* Hp = Gp + 128 * T;         // 8 inner sums
+  uint64_t* z = Hp + LT_J * T;
+  uint64_t* acc = z + T;
+  uint64_t* tmp = acc + T;
+  auto B = [&](int i) { return Bp + (size_t)(i - 1) * T; };
+  auto G = [&](int j) { return Gp + (size_t)(j - 1) * T; };
+  ct_addsub(h, x, y, z, 1, b, s);
+  hsquare(h, z, B(1), b, s);
+  for (int i = 2; i < 256; ++i) {
+    if (i % 2 == 0)
+      hsquare(h, B(i / 2), B(i), b, s);
+    else
+      hmul(h, B(i - 1), B(1), B(i), b, s);
+  }
+  hsquare(h, B(128), G(1), b, s);
+  for (int j = 2; j <= 128; ++j) {
+    if (j % 2 == 0)
+      hsquare(h, G(j / 2), G(j), b, s);
+    else
+      hmul(h, G(j - 1), G(1), G(j), b, s);
+  }
+  // The inner-sum kernel reads B as [255][bw]; with a partial tile (b < lt_tile)
+  // the arrays keep their stride T, so compact them is unnecessary: pass bw = T
+  // and ignore the unused tail words.
+  for (int j0 = 0; j0 < 128; j0 += LT_J) {
+    k_lt_inner<<<ew_blocks(T), EW_THREADS, 0, s>>>(Bp, h->lt_coef, j0, Hp, h->logn, T);
+    h->launches += 1;
+    for (int jj = 0; jj < LT_J; ++jj) {
+      const int j = j0 + jj;
+      if (j == 0) {
+        cudaMemcpyAsync(acc, Hp, bw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+      } else {
+        hmul(h, Hp + (size_t)jj * T, G(j), tmp, b, s);
+        ct_addsub(h, acc, tmp, acc, 0, b, s);
+      }
+    }
+  }
+  hmul(h, z, acc, tmp, b, s);
+  ScalarK sk;  // out = tmp - 32768 G_128 = tmp + (t - 32768) G_128
+  for (int i = 0; i < L; ++i) {
+    sk.k[i] = (h->t - (h->t - 1) / 2) % h->q[i];
+    sk.ks[i] = h_shoup(sk.k[i], h->q[i]);
+  }
+  k_ct_axpy<<<ew_blocks(bw), EW_THREADS, 0, s>>>(tmp, G(128), out, sk, h->logn, bw);
+  h->launches += 1;
+}
+
+static int lt_prepare(hp_handle* h) {
+  if (h->ltws) return HP_OK;
+  h->lt_tile = h->tile < 8 ? h->tile : 8;
+  const size_t words = (size_t)(255 + 128 + LT_J + 3) * h->lt_tile * words_ct(h);
+  if (cudaMalloc(&h->ltws, words * sizeof(uint64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    h->ltws = nullptr;
+    HP_FAIL(h, HP_ERR_OOM, "LT workspace (%zu MB) allocation failed", (words * 8) >> 20);
+  }
+  std::vector<uint32_t> coef(32768);
+  lt_coefficients(coef.data());
+  CU(h, cudaMalloc(&h->lt_coef, coef.size() * sizeof(uint32_t)));
+  CU(h, cudaMemcpy(h->lt_coef, coef.data(), coef.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  return HP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // tables
 // ---------------------------------------------------------------------------
 static int brv(int x, int bits) {
@@ -373,7 +470,7 @@ static void free_all(hp_handle* h) {
   }
   void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
                   h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
-                  h->stx2, h->sty2, h->sto2};
+                  h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
@@ -501,21 +598,33 @@ int hp_run(hp_handle* h, int op, const uint64_t* x, const uint64_t* y, uint64_t 
            void* stream) {
   if (!h) return HP_ERR_ARG;
   h->launches = 0;
-  if (op < HP_EQ_CT_CT || op > HP_SQUARE) HP_FAIL(h, HP_ERR_ARG, "unknown op %d", op);
+  if (op < HP_EQ_CT_CT || op > HP_LT) HP_FAIL(h, HP_ERR_ARG, "unknown op %d", op);
   if (n_ct == 0) return HP_OK;
   if (!x || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
-  if ((op == HP_EQ_CT_CT || op == HP_SELECT) && !y) HP_FAIL(h, HP_ERR_ARG, "op needs ct_y");
+  if ((op == HP_EQ_CT_CT || op == HP_SELECT || op == HP_LT) && !y) HP_FAIL(h, HP_ERR_ARG, "op needs ct_y");
   if ((op == HP_EQ_CT_CONST || op == HP_SELECT) && cval >= h->t) HP_FAIL(h, HP_ERR_ARG, "const_val must be < t");
   if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
-  int need = op == HP_SQUARE ? 1 : (op == HP_SELECT ? 17 : 16);
+  int need = op == HP_SQUARE ? 1 : (op == HP_SELECT ? 17 : (op == HP_LT ? 18 : 16));
   if (need > supported_depth(h->logn, h->q, L, h->P, h->t))
     HP_FAIL(h, HP_ERR_DEPTH, "operation depth %d exceeds the parameters' budget", need);
   if (((uintptr_t)x | (uintptr_t)out | (uintptr_t)y) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t W = words_ct(h);
   const bool dev = is_device_ptr(x);
-  if (dev != is_device_ptr(out) || ((op == HP_EQ_CT_CT || op == HP_SELECT) && dev != is_device_ptr(y)))
+  if (dev != is_device_ptr(out) || ((op == HP_EQ_CT_CT || op == HP_SELECT || op == HP_LT) && dev != is_device_ptr(y)))
     HP_FAIL(h, HP_ERR_ARG, "ciphertext arguments must all be device memory or all host memory");
+  if (op == HP_LT) {
+    if (!dev) HP_FAIL(h, HP_ERR_UNSUPPORTED, "HP_LT takes device memory");
+    int rc = lt_prepare(h);
+    if (rc != HP_OK) return rc;
+    for (size_t c0 = 0; c0 < n_ct; c0 += h->lt_tile) {
+      const int b = (int)((n_ct - c0 < h->lt_tile) ? n_ct - c0 : h->lt_tile);
+      const size_t off = c0 * W;
+      run_lt_tile(h, x + off, y + off, out + off, b, s);
+      CU(h, cudaGetLastError());
+    }
+    return HP_OK;
+  }
   const size_t TT = h->run_tile ? h->run_tile : h->tile;
   if (dev) {
     for (size_t c0 = 0; c0 < n_ct; c0 += TT) {
@@ -764,6 +873,11 @@ void hp_destroy(hp_handle* h) {
 const char* hp_last_error(const hp_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 uint64_t hp_launch_count(const hp_handle* h) { return h ? h->launches : 0; }
+
+int hp_lt_coefficients(uint32_t* out) {
+  if (!out) return HP_ERR_ARG;
+  return lt_coefficients(out) == 0 ? HP_OK : HP_ERR_ARG;
+}
 
 size_t hp_tile_size(const hp_handle* h) { return h ? (h->run_tile ? h->run_tile : h->tile) : 0; }
 

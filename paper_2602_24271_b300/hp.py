@@ -32,6 +32,7 @@ HP_EQ_CT_CT = 0
 HP_EQ_CT_CONST = 1
 HP_SELECT = 2
 HP_SQUARE = 3
+HP_LT = 4
 
 L = 15
 T = 65537
@@ -40,7 +41,7 @@ EXPORTED = [
     "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
-    "hp_square_noalloc", "hp_autotune",
+    "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -112,6 +113,7 @@ def load():
         "hp_tile_size": (ctypes.c_size_t, [H]),
         "hp_square_noalloc": (ctypes.c_int, [H, P64, P64, V]),
         "hp_autotune": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_size_t)]),
+        "hp_lt_coefficients": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -265,6 +267,13 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
         _check(self.lib.hp_profile_read(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)), self.h)
         return ms.value, int(n.value), w.value
+
+
+def lt_coefficients() -> np.ndarray:
+    """Odd coefficients of the LT polynomial (Eq. 4), computed by the library."""
+    out = np.zeros(32768, dtype=np.uint32)
+    _check(load().hp_lt_coefficients(out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return out
 
 
 def probe_peak(kind: int) -> float:

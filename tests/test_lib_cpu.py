@@ -102,3 +102,11 @@ def lib_depth(logn, q, P):
     lt = math.log2(65537)
     fresh = lq - lt - logn - 8
     return int((fresh - 1) // (lt + logn + 2)) if fresh > 0 else 0
+
+
+def test_lt_coefficients_match_oracle(lib):
+    """The library's LT coefficients (one length-2^16 transform over F_65537)
+    equal the oracle's (plain power sums); computed independently."""
+    got = hp.lt_coefficients()
+    o = oracle.Oracle(4)
+    assert np.array_equal(got, o.lt_coefficients())
