@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +51,11 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "in":
+        return dict(n_ct=256, op="in", n_const=8,
+                    desc="IN(x, S) (Eq. 6) with |S| = 8 constants, GROUP BY fan-out of 8 EQ chains per ciphertext: "
+                    "2^23 slots = 256 BFV ciphertexts, N=32768, L=15, p=65537, bit-exact; value = slot-constant "
+                    "comparisons/s")
     if cfg == "lt":
         return dict(n_ct=64, op="lt", desc="LT(x, y) = [x < y] (Eq. 4): 2^21 slots = 64 BFV ciphertext pairs, "
                     "x, y in [0, 2^15], N=32768, L=15, p=65537; 511 multiplications per ciphertext, bit-exact")
@@ -226,12 +231,15 @@ def run_libhp(args):
             cy[c0:c1] = ctx.encrypt(y[c0 * N:c1 * N].reshape(-1, N), seed=SEED_DATA, ct_index0=n_ct + c0)
     out = ctx.ct_empty(n_ct)
     const_val = 4242
+    in_consts = [int(v) for v in x[:wl.get("n_const", 0)]]  # members drawn from the column itself
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
     def step():
         if wl["op"] == "lt":
             ctx.run(hp.HP_LT, cx, cy, 0, out=out, stream=stream)
+        elif wl["op"] == "in":
+            ctx.eq_fanout(cx, in_consts, masks=False, in_set=out, stream=stream)
         elif cy is not None:
             ctx.run(hp.HP_EQ_CT_CT, cx, cy, 0, out=out, stream=stream)
         else:
@@ -282,7 +290,7 @@ def run_libhp(args):
     ctx.check_status()
     ms_max = max_over_ranks(ms_total, dist, device="cuda")
     ms_per_step = ms_max / args.steps
-    slots_all = n_ct * N * world
+    slots_all = n_ct * N * world * wl.get("n_const", 1)
     value = slots_all / (ms_per_step / 1e3)
 
     # correctness of this run (decrypt a few ciphertexts, closed form)
@@ -292,6 +300,8 @@ def run_libhp(args):
         xs = x[c * N:(c + 1) * N]
         if wl["op"] == "lt":
             ref = xs < y[c * N:(c + 1) * N]
+        elif wl["op"] == "in":
+            ref = np.isin(xs, in_consts)
         else:
             ref = (xs == y[c * N:(c + 1) * N]) if cy is not None else (xs == const_val)
         assert np.array_equal(dec[k], ref.astype(np.uint32)), "EQ result wrong in benchmark run"
@@ -333,7 +343,7 @@ def run_libhp(args):
             "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
 
     # ---- end to end through the public API with pinned host buffers ----
-    if not args.no_e2e and wl["op"] != "lt":
+    if not args.no_e2e and wl["op"] not in ("lt", "in"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:

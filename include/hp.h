@@ -158,6 +158,19 @@ int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst,
  * tile) for the process.  Synchronous. */
 int hp_autotune(hp_handle* h, size_t* best_tile);
 
+/* One column against many constants (device memory, n_ct ciphertexts of x,
+ * n_const constants in host memory, each < t):
+ *   GROUP BY (Sec. 4.2.2): masks[k][c] = EQ(x[c], consts[k])   (masks: [n_const][n_ct] ciphertexts)
+ *   IN (Eq. 6):            in_out[c] = sum_k EQ(x[c], consts[k]) = [x in S]
+ * Either output may be NULL (not both); with masks == NULL the masks live in
+ * stream-ordered temporary memory.  The sum is a balanced addition tree
+ * (Sec. 4.3.1); ciphertext addition is exact mod Q, so the result does not
+ * depend on the tree shape.  The n_const * n_ct chains run in tiles of the
+ * handle's tile size.  IN is the set-membership mask only when the constants
+ * are distinct (else it counts multiplicities). */
+int hp_eq_fanout(hp_handle* h, const uint64_t* ct_x, size_t n_ct, const uint64_t* consts, size_t n_const,
+                 uint64_t* masks, uint64_t* in_out, void* stream);
+
 /* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
  * derivative, so this always returns HP_ERR_UNSUPPORTED. */
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream);

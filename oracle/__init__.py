@@ -299,6 +299,15 @@ class Oracle:
         self.lib.orc_linear(self.h, _p(C, ctypes.c_uint64), len(k), _p(k, ctypes.c_uint64), coef0, _p(out, ctypes.c_uint64))
         return out
 
+    def group_by_masks(self, x, consts):
+        """GROUP BY masks (Sec. 4.2.2): EQ(x, c_k) for each constant c_k."""
+        return np.stack([self.eq(x, None, const_val=int(c)) for c in consts])
+
+    def in_set(self, x, consts, masks=None):
+        """IN (Eq. 6): the sum of the EQ masks of x against every constant."""
+        m = self.group_by_masks(x, consts) if masks is None else masks
+        return self.linear(m, [1] * len(m))
+
     def lt(self, x, y):
         """LT(x, y) (Eq. 4) by the baby-step / giant-step schedule of the library."""
         X, Y, out = _c(x, np.uint64), _c(y, np.uint64), self._ct_out()

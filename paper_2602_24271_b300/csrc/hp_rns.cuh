@@ -19,7 +19,10 @@ enum { ST_BQ_WINDOW = 1 };
 // Difference modes of the first lift (row a1).  LIFT_SUB_PT subtracts
 // (Delta m, 0) for a plaintext polynomial m per ciphertext (sub: [nct][N],
 // coefficients < t): the packed form of x = c with per-slot constants.
-enum { LIFT_COPY = 0, LIFT_SUB_CT = 1, LIFT_SUB_CONST = 2, LIFT_SUB_PT = 3 };
+// LIFT_SUB_CONSTS subtracts (Delta c_b, 0) with one constant per ciphertext
+// (sub: uint64 [nct], values < t): the fan-out of one column against many
+// constants (GROUP BY, IN).
+enum { LIFT_COPY = 0, LIFT_SUB_CT = 1, LIFT_SUB_CONST = 2, LIFT_SUB_PT = 3, LIFT_SUB_CONSTS = 4 };
 
 // One thread per (ciphertext b, component c, coefficient n).
 // src, sub: [nct][2][L][N]; ext: [nct][2][NQB][N].
@@ -46,6 +49,8 @@ __global__ void __launch_bounds__(EW_THREADS) k_lift(const uint64_t* __restrict_
       v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
     } else if (mode == LIFT_SUB_PT && comp == 0) {
       v = sub_mod(v, mul_shoup(sub[(bc >> 1) * N + n], cK.delta[i], cK.delta_s[i], p), p);
+    } else if (mode == LIFT_SUB_CONSTS && comp == 0 && n == 0) {
+      v = sub_mod(v, mul_shoup(sub[bc >> 1], cK.delta[i], cK.delta_s[i], p), p);
     }
     o[(size_t)i * N] = v;
     y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
@@ -298,6 +303,27 @@ __global__ void k_ct_addsub(const uint64_t* __restrict__ a, const uint64_t* __re
   if (w >= nwords) return;
   const uint64_t q = cK.p[prime_of_word(w, logN)];
   out[w] = subtract ? sub_mod(a[w], b[w], q) : add_mod(a[w], b[w], q);
+}
+
+// out += a (IN accumulation of one tile of masks into the running sum; out
+// and a are distinct buffers, out is read and written in place)
+__global__ void k_ct_acc(uint64_t* out, const uint64_t* __restrict__ a, int logN, size_t nwords) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwords) return;
+  const uint64_t q = cK.p[prime_of_word(w, logN)];
+  out[w] = add_mod(out[w], a[w], q);
+}
+
+// out = sum_k M[k] over n_const arrays of nwords words each (Eq. 6 sum of the
+// GROUP BY masks in one pass: every mask is read once)
+__global__ void k_ct_sum(const uint64_t* __restrict__ M, int n_const, uint64_t* __restrict__ out, int logN,
+                         size_t nwords) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwords) return;
+  const uint64_t q = cK.p[prime_of_word(w, logN)];
+  uint64_t acc = 0;
+  for (int k = 0; k < n_const; ++k) acc = add_mod(acc, M[(size_t)k * nwords + w], q);
+  out[w] = acc;
 }
 
 // out = g + k G  for a small integer k (Shoup companions per prime passed by value)

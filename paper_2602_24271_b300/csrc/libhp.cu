@@ -853,6 +853,67 @@ int hp_autotune(hp_handle* h, size_t* best_tile) {
   return HP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fan-out of one column against many constants: GROUP BY masks EQ(x, c_k)
+// (Sec. 4.2.2) and IN(x, S) = sum_k EQ(x, c_k) (Eq. 6).  The n_const * n_ct
+// chains (item = k * n_ct + c) are independent and run in tiles; each tile
+// gathers its x ciphertexts into staging and its first lift subtracts one
+// constant per ciphertext.  Ciphertext addition is exact mod Q, so the sum
+// equals the paper's divide-and-conquer addition for any order: with masks
+// kept it is one pass over all masks, otherwise each tile's masks are added
+// into the running sum and only one tile of masks is ever stored.
+// ---------------------------------------------------------------------------
+int hp_eq_fanout(hp_handle* h, const uint64_t* x, size_t n_ct, const uint64_t* consts, size_t n_const,
+                 uint64_t* masks, uint64_t* in_out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (n_ct == 0 || n_const == 0) return HP_OK;
+  if (!x || !consts || (!masks && !in_out)) HP_FAIL(h, HP_ERR_ARG, "null argument");
+  if (n_const > (1u << 20)) HP_FAIL(h, HP_ERR_ARG, "at most 2^20 constants");
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  if (16 > supported_depth(h->logn, h->q, L, h->P, h->t)) HP_FAIL(h, HP_ERR_DEPTH, "depth 16 exceeds the budget");
+  for (size_t k = 0; k < n_const; ++k)
+    if (consts[k] >= h->t) HP_FAIL(h, HP_ERR_ARG, "constant %zu must be < t", k);
+  if (!is_device_ptr(x) || (masks && !is_device_ptr(masks)) || (in_out && !is_device_ptr(in_out)))
+    HP_FAIL(h, HP_ERR_ARG, "fan-out arrays must be device memory");
+  if (((uintptr_t)x | (uintptr_t)masks | (uintptr_t)in_out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t W = words_ct(h), TT = h->run_tile ? h->run_tile : h->tile, items = n_const * n_ct;
+  std::vector<uint64_t> hc(items);
+  for (size_t it = 0; it < items; ++it) hc[it] = consts[it / n_ct];
+  uint64_t* dconst = nullptr;
+  CU(h, cudaMallocAsync((void**)&dconst, items * sizeof(uint64_t), s));
+  CU(h, cudaMemcpyAsync(dconst, hc.data(), items * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  if (in_out && !masks) CU(h, cudaMemsetAsync(in_out, 0, n_ct * W * sizeof(uint64_t), s));
+  for (size_t i0 = 0; i0 < items; i0 += TT) {
+    const int b = (int)((items - i0 < TT) ? items - i0 : TT);
+    for (int u = 0; u < b; ++u)
+      CU(h, cudaMemcpyAsync(h->stx + (size_t)u * W, x + ((i0 + u) % n_ct) * W, W * sizeof(uint64_t),
+                            cudaMemcpyDeviceToDevice, s));
+    uint64_t* dst = masks ? masks + i0 * W : h->sto;
+    run_tile_mode(h, HP_EQ_CT_CONST, LIFT_SUB_CONSTS, h->stx, dconst + i0, nullptr, 0, dst, b, s);
+    if (!masks) {  // add each run of consecutive c into the running sum
+      for (int u = 0; u < b;) {
+        const size_t c = (i0 + u) % n_ct;
+        const int run = (int)std::min<size_t>(b - u, n_ct - c);
+        const size_t nw = (size_t)run * W;
+        k_ct_acc<<<ew_blocks(nw), EW_THREADS, 0, s>>>(in_out + c * W, h->sto + (size_t)u * W, h->logn, nw);
+        h->launches += 1;
+        u += run;
+      }
+    }
+    CU(h, cudaGetLastError());
+  }
+  if (masks && in_out) {
+    const size_t nw = n_ct * W;
+    k_ct_sum<<<ew_blocks(nw), EW_THREADS, 0, s>>>(masks, (int)n_const, in_out, h->logn, nw);
+    h->launches += 1;
+  }
+  cudaFreeAsync(dconst, s);
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream) {
   (void)op;
   (void)grad_out;

@@ -41,7 +41,7 @@ EXPORTED = [
     "hp_default_params", "hp_create", "hp_set_relin_key", "hp_run", "hp_run_batched", "hp_backward",
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
-    "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients",
+    "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -114,6 +114,7 @@ def load():
         "hp_square_noalloc": (ctypes.c_int, [H, P64, P64, V]),
         "hp_autotune": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_size_t)]),
         "hp_lt_coefficients": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+        "hp_eq_fanout": (ctypes.c_int, [H, P64, SZ, ctypes.POINTER(ctypes.c_uint64), SZ, P64, P64, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,6 +243,22 @@ class Context:
         _check(self.lib.hp_run_batched(self.h, op, arr, len(instances), _ptr(x), _ptr(y), _ptr(out), n,
                                        _stream(stream)), self.h)
         return out
+
+    def eq_fanout(self, x, consts, masks=True, in_set=True, stream=None):
+        """GROUP BY masks EQ(x, c_k) ([n_const, n_ct, 2, L, N]) and/or IN(x, consts)
+        ([n_ct, 2, L, N]).  `masks` / `in_set`: True (allocate), False/None (skip)
+        or a preallocated device tensor to write."""
+        n = x.shape[0]
+        k = len(consts)
+        c = (ctypes.c_uint64 * max(1, k))(*[int(v) for v in consts])
+        if masks is True:
+            masks = self.torch.empty((k, n, 2, self.L, self.N), dtype=self.torch.int64, device="cuda")
+        if in_set is True:
+            in_set = self.ct_empty(n)
+        m = masks if masks is not False else None
+        io = in_set if in_set is not False else None
+        _check(self.lib.hp_eq_fanout(self.h, _ptr(x), n, c, k, _ptr(m), _ptr(io), _stream(stream)), self.h)
+        return m, io
 
     def backward(self, op: int, grad_out, grad_x, n: int):
         return self.lib.hp_backward(self.h, op, _ptr(grad_out), _ptr(grad_x), n, None)

@@ -416,3 +416,21 @@ def test_lt_closed_form_n16(orc16):
     got, nb = o.decrypt(o.lt(cx, cy), with_noise=True)
     assert np.array_equal(got, (x < y).astype(np.uint32))
     assert nb > 0
+
+
+def test_group_by_and_in_closed_form_n16(orc16):
+    """GROUP BY masks decrypt to [x == c_k] per constant and IN (Eq. 6) to
+    [x in S] for a set of distinct constants, including one absent value, the
+    value 0 and p - 1; a repeated constant counts twice (the sum is a count)."""
+    o = orc16
+    rng = np.random.default_rng(15)
+    consts = [0, 9, T - 1, 12345]
+    x = rng.choice([0, 9, T - 1, 1, 2], o.N).astype(np.uint32)
+    cx = o.encrypt(x, 16, 0)
+    masks = o.group_by_masks(cx, consts)
+    for k, c in enumerate(consts):
+        assert np.array_equal(o.decrypt(masks[k]), (x == c).astype(np.uint32))
+    got = o.decrypt(o.in_set(cx, consts, masks=masks))
+    assert np.array_equal(got, np.isin(x, consts).astype(np.uint32))
+    twice = o.decrypt(o.in_set(cx, [9, 9], masks=masks[[1, 1]]))
+    assert np.array_equal(twice, 2 * (x == 9).astype(np.uint32))
