@@ -84,6 +84,10 @@ def _load():
         "orc_lt": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_tensor_round": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_relin": (ctypes.c_int, [V, _u64p, _u64p]),
+        "orc_galois_keygen": (ctypes.c_int, [V, ctypes.c_uint64, _i8p, ctypes.c_uint64, _u64p]),
+        "orc_automorphism": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
+        "orc_rotate": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
+        "orc_rotate_sum": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -307,6 +311,43 @@ class Oracle:
         """IN (Eq. 6): the sum of the EQ masks of x against every constant."""
         m = self.group_by_masks(x, consts) if masks is None else masks
         return self.linear(m, [1] * len(m))
+
+    # -- rotations, COUNT / SUM (Sec. 4.2.2) -----------------------------------------
+    def galois_elements(self):
+        """Elements of the rotate-and-add reduction, in order: 3^(2^i) mod 2N for
+        i = logN-2 .. 0 (row rotations by N/4 .. 1), then 2N - 1 (row exchange)."""
+        twoN = 2 * self.N
+        return [pow(3, 1 << i, twoN) for i in range(self.logn - 2, -1, -1)] + [twoN - 1]
+
+    def galois_keygen(self, seed: int, g: int, s=None):
+        """Galois key for element g (uint64 [L][2][L+1][N]); kept for rotations."""
+        s = self.s if s is None else _c(s, np.int8)
+        gk = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
+        if self.lib.orc_galois_keygen(self.h, seed, _p(s, ctypes.c_int8), g, _p(gk, ctypes.c_uint64)) != 0:
+            raise ValueError("Galois element must be odd and < 2N")
+        return gk
+
+    def automorphism(self, x, g: int):
+        """tau_g(ct) without key switching (decrypts under tau_g(s))."""
+        X, out = _c(x, np.uint64), self._ct_out()
+        if self.lib.orc_automorphism(self.h, _p(X, ctypes.c_uint64), g, _p(out, ctypes.c_uint64)) != 0:
+            raise ValueError("Galois element must be odd and < 2N")
+        return out
+
+    def rotate(self, x, g: int):
+        X, out = _c(x, np.uint64), self._ct_out()
+        if self.lib.orc_rotate(self.h, _p(X, ctypes.c_uint64), g, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("Galois key for %d not generated" % g)
+        return out
+
+    def rotate_sum(self, x, row_steps=None, swap: bool = True):
+        """Rotate-and-add reduction: every slot ends with the sum of all slots."""
+        rs = self.logn - 1 if row_steps is None else row_steps
+        X, out = _c(x, np.uint64), self._ct_out()
+        rc = self.lib.orc_rotate_sum(self.h, _p(X, ctypes.c_uint64), rs, int(swap), _p(out, ctypes.c_uint64))
+        if rc != 0:
+            raise RuntimeError("orc_rotate_sum failed (%d)" % rc)
+        return out
 
     def lt(self, x, y):
         """LT(x, y) (Eq. 4) by the baby-step / giant-step schedule of the library."""

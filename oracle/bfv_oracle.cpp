@@ -32,6 +32,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cmath>
+#include <map>
 #include <vector>
 #include <algorithm>
 
@@ -170,7 +171,9 @@ static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 
 // Sampling domains: every random draw of the scheme is philox(seed; counter =
 // (coefficient k, prime index j, object index, domain)).
-enum { DOM_S = 1, DOM_E_ENC = 2, DOM_A_ENC = 3, DOM_E_RK = 4, DOM_A_RK = 5 };
+// Galois keys (domains 6, 7) use object index (g << 5) | digit for Galois
+// element g, so a key does not depend on which other elements are generated.
+enum { DOM_S = 1, DOM_E_ENC = 2, DOM_A_ENC = 3, DOM_E_RK = 4, DOM_A_RK = 5, DOM_E_GK = 6, DOM_A_GK = 7 };
 
 static void draw(uint64_t seed, uint32_t k, uint32_t j, uint32_t obj, uint32_t dom, uint32_t w[4]) {
   uint32_t ctr[4] = {k, j, obj, dom};
@@ -480,6 +483,15 @@ static int brv(int x, int bits) {
 // ---------------------------------------------------------------------------
 typedef std::vector<Big> Poly;  // N big-integer coefficients
 
+// A key-switching key from a secret s' to s: k_i = (-(a_i s + e_i) + P g_i s',
+// a_i) mod QP, i < L (per-prime digits, one special prime), kept in big-integer
+// form and transformed over the oracle primes used for the exact products.
+struct KsKey {
+  std::vector<Poly> k0, k1;
+  int nprimes = 0;
+  std::vector<uint64_t> ntt;      // [i][comp][prime][N]
+};
+
 struct Ctx {
   int logn, N, L;
   uint64_t t, P;
@@ -491,11 +503,10 @@ struct Ctx {
   std::vector<NttPlan> plans;     // one per oracle prime
   NttPlan tplan;                  // plaintext-modulus transform (batch encoding)
   std::vector<Crt> crt_prefix;    // crt over the first k oracle primes, k = 1..
-  // relinearisation key (big-integer form) and its transforms over oracle primes
+  // relinearisation key and Galois keys (switching from s^2, resp. tau_g(s), to s)
   bool have_rk = false;
-  std::vector<Poly> rk0, rk1;     // rk_i = (rk0[i], rk1[i]) mod QP, i < L
-  int rk_nprimes = 0;
-  std::vector<uint64_t> rk_ntt;   // [i][comp][prime][N]
+  KsKey rk;
+  std::map<uint64_t, KsKey> gk;   // by Galois element g
   std::vector<uint32_t> lt_h;     // LT polynomial's odd coefficients (computed on first use)
 };
 
@@ -681,10 +692,12 @@ static Ct ct_one_minus(const Ctx& c, const Ct& x) {
   return r;
 }
 
-// relinearisation of (d0, d1, d2) (coefficients in [0, Q))
-static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& d2) {
-  if (!c.have_rk) fail("relinearisation key not set");
-  int N = c.N, L = c.L, k = c.rk_nprimes;
+// Key switching of (d0, d1, d2), coefficients in [0, Q), where d2 is to be
+// multiplied by the key's source secret: (d0, d1) + round(sum_i [d2]_{q_i} k_i / P)
+// mod Q.  With the relinearisation key this is relinearisation (source s^2);
+// with a Galois key it completes an automorphism (source tau_g(s)).
+static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d1, const Poly& d2) {
+  int N = c.N, L = c.L, k = K.nprimes;
   // u = sum_i digit_i * rk_i  (exact integer negacyclic products, then mod QP)
   std::vector<uint64_t> res0((size_t)k * N), res1((size_t)k * N);
   std::vector<uint64_t> digit((size_t)L * N);  // digit_i = [d2]_{q_i}
@@ -698,8 +711,8 @@ static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& 
     for (int i = 0; i < L; ++i) {
       for (int j = 0; j < N; ++j) D[j] = digit[(size_t)i * N + j] % m;
       c.plans[pi].forward(D.data());
-      const uint64_t* K0 = &c.rk_ntt[(((size_t)i * 2 + 0) * k + pi) * N];
-      const uint64_t* K1 = &c.rk_ntt[(((size_t)i * 2 + 1) * k + pi) * N];
+      const uint64_t* K0 = &K.ntt[(((size_t)i * 2 + 0) * k + pi) * N];
+      const uint64_t* K1 = &K.ntt[(((size_t)i * 2 + 1) * k + pi) * N];
       for (int j = 0; j < N; ++j) {
         acc0[j] = addmod(acc0[j], mulmod(D[j], K0[j], m), m);
         acc1[j] = addmod(acc1[j], mulmod(D[j], K1[j], m), m);
@@ -734,6 +747,11 @@ static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& 
     }
   }
   return out;
+}
+
+static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& d2) {
+  if (!c.have_rk) fail("relinearisation key not set");
+  return key_switch(c, c.rk, d0, d1, d2);
 }
 
 // textbook multiplication + relinearisation
@@ -779,6 +797,101 @@ static Poly phase(const Ctx& c, const Ct& ct, const int8_t* s) {
 // ---------------------------------------------------------------------------
 // extern "C" interface (consumed by oracle/__init__.py through ctypes)
 // ---------------------------------------------------------------------------
+// Key-switching key from source secret `src` (an integer polynomial: s^2 or
+// tau_g(s)) to s: k_i = (-(a_i s + e_i) + P g_i src, a_i) mod QP with
+// g_i = (Q/q_i) [(Q/q_i)^{-1}]_{q_i}; a_i uniform mod QP (residue j drawn with
+// counter (k, j, obj_base | i, dom_a)), e_i centred binomial (counter
+// (k, 0, obj_base | i, dom_e)).  `out` (may be null): uint64 [L][2][L+1][N].
+static void make_ks_key(const Ctx& c, uint64_t seed, const Poly& s, const Poly& src, uint32_t dom_a, uint32_t dom_e,
+                        uint32_t obj_base, KsKey& K, uint64_t* out) {
+  int N = c.N, L = c.L;
+  uint32_t w[4];
+  K.k0.assign(L, Poly(N));
+  K.k1.assign(L, Poly(N));
+  std::vector<uint64_t> res(L + 1);
+  for (int i = 0; i < L; ++i) {
+    uint64_t rr;
+    Big qhat = mag_divmod_u64(c.Q, c.q[i], &rr);
+    uint64_t qhat_inv = invmod(big_mod_u64(qhat, c.q[i]), c.q[i]);
+    Big Pg = big_mul_u64(big_mul_u64(qhat, qhat_inv), c.P);
+    Poly a(N), e(N);
+    for (int k = 0; k < N; ++k) {
+      for (int j = 0; j <= L; ++j) {
+        draw(seed, k, j, obj_base | (uint32_t)i, dom_a, w);
+        res[j] = sample_uniform(w, c.qp[j]);
+      }
+      a[k] = c.crtQP.reconstruct(res.data());
+      draw(seed, k, 0, obj_base | (uint32_t)i, dom_e, w);
+      int ev = sample_cbd21(w);
+      e[k] = big_u64((uint64_t)std::abs(ev));
+      if (ev < 0) e[k] = big_neg(e[k]);
+    }
+    Poly as = poly_mul_exact(c, a, s);
+    for (int k = 0; k < N; ++k) {
+      Big v = big_neg(big_add(as[k], e[k]));
+      v = big_add(v, big_mul(Pg, src[k]));
+      K.k0[i][k] = mod_QP(c, v);
+      K.k1[i][k] = a[k];
+    }
+    if (out)
+      for (int comp = 0; comp < 2; ++comp)
+        for (int j = 0; j <= L; ++j)
+          for (int k = 0; k < N; ++k) {
+            const Big& v = comp ? K.k1[i][k] : K.k0[i][k];
+            out[((((size_t)i * 2 + comp) * (L + 1)) + j) * N + k] = big_mod_u64(v, c.qp[j]);
+          }
+  }
+  // transforms over the oracle primes: |u| < L N max(q) QP
+  int bound = 56 + big_bits(c.QP) + c.logn + (int)std::ceil(std::log2((double)L + 1)) + 1;
+  int k = primes_needed(c, bound);
+  K.nprimes = k;
+  K.ntt.assign((size_t)L * 2 * k * N, 0);
+  for (int i = 0; i < L; ++i)
+    for (int comp = 0; comp < 2; ++comp)
+      for (int pi = 0; pi < k; ++pi) {
+        uint64_t* dst = &K.ntt[(((size_t)i * 2 + comp) * k + pi) * N];
+        const Poly& srcp = comp ? K.k1[i] : K.k0[i];
+        for (int j = 0; j < N; ++j) dst[j] = big_mod_u64(srcp[j], c.om[pi]);
+        c.plans[pi].forward(dst);
+      }
+}
+
+// Galois automorphism tau_g: a(X) -> a(X^g) mod X^N + 1 (g odd).  Coefficient j
+// moves to j g mod 2N; landing at N + r means -X^r.  `M` null: signed
+// integer coefficients (negation), else residues in [0, M) (negation mod M).
+static Poly automorph(const Ctx& c, const Poly& a, uint64_t g, const Big* M) {
+  const uint64_t twoN = 2 * (uint64_t)c.N;
+  Poly out(c.N);
+  for (int j = 0; j < c.N; ++j) {
+    uint64_t e = ((uint64_t)j * g) % twoN;
+    if (e < (uint64_t)c.N) {
+      out[e] = a[j];
+    } else {
+      const Big& v = a[j];
+      out[e - c.N] = M ? (big_is_zero(v) ? v : big_sub(*M, v)) : big_neg(v);
+    }
+  }
+  return out;
+}
+
+// ct -> tau_g(ct), which decrypts under tau_g(s) to tau_g(m)
+static Ct ct_automorph(const Ctx& c, const Ct& x, uint64_t g) {
+  Ct r;
+  r.c0 = automorph(c, x.c0, g, &c.Q);
+  r.c1 = automorph(c, x.c1, g, &c.Q);
+  return r;
+}
+
+// Rotation (slot permutation) by g: tau_g(ct) switched back to s with the
+// Galois key of g: (tau_g(c0), 0) + round(sum_i [tau_g(c1)]_{q_i} gk_i / P).
+static Ct ct_rotate(const Ctx& c, const Ct& x, uint64_t g) {
+  auto it = c.gk.find(g);
+  if (it == c.gk.end()) fail("Galois key not generated");
+  Ct t = ct_automorph(c, x, g);
+  Poly zero(c.N, big_zero());
+  return key_switch(c, it->second, t.c0, zero, t.c1);
+}
+
 extern "C" {
 
 // Largest `L` primes below 2^55 and the largest prime below 2^56, all = 1 mod 2^16.
@@ -891,63 +1004,13 @@ int orc_decode(void* h, const uint64_t* m, uint32_t* slots) {
 // the context for later multiplications.
 int orc_keygen(void* h, uint64_t seed, int8_t* s_out, uint64_t* rk_out) {
   Ctx& c = *(Ctx*)h;
-  int N = c.N, L = c.L;
   uint32_t w[4];
-  for (int k = 0; k < N; ++k) {
+  for (int k = 0; k < c.N; ++k) {
     draw(seed, k, 0, 0, DOM_S, w);
     s_out[k] = (int8_t)sample_ternary(w);
   }
   Poly s = secret_poly(c, s_out);
-  Poly s2 = poly_mul_exact(c, s, s);
-  c.rk0.assign(L, Poly(N));
-  c.rk1.assign(L, Poly(N));
-  std::vector<uint64_t> res(L + 1);
-  for (int i = 0; i < L; ++i) {
-    // g_i = (Q/q_i) [(Q/q_i)^{-1}]_{q_i}
-    uint64_t rr;
-    Big qhat = mag_divmod_u64(c.Q, c.q[i], &rr);
-    uint64_t qhat_inv = invmod(big_mod_u64(qhat, c.q[i]), c.q[i]);
-    Big Pg = big_mul_u64(big_mul_u64(qhat, qhat_inv), c.P);
-    Poly a(N), e(N);
-    for (int k = 0; k < N; ++k) {
-      for (int j = 0; j <= L; ++j) {
-        draw(seed, k, j, i, DOM_A_RK, w);
-        res[j] = sample_uniform(w, c.qp[j]);
-      }
-      a[k] = c.crtQP.reconstruct(res.data());
-      draw(seed, k, 0, i, DOM_E_RK, w);
-      int ev = sample_cbd21(w);
-      e[k] = big_u64((uint64_t)std::abs(ev));
-      if (ev < 0) e[k] = big_neg(e[k]);
-    }
-    Poly as = poly_mul_exact(c, a, s);
-    for (int k = 0; k < N; ++k) {
-      Big v = big_neg(big_add(as[k], e[k]));
-      v = big_add(v, big_mul(Pg, s2[k]));
-      c.rk0[i][k] = mod_QP(c, v);
-      c.rk1[i][k] = a[k];
-    }
-    for (int comp = 0; comp < 2; ++comp)
-      for (int j = 0; j <= L; ++j)
-        for (int k = 0; k < N; ++k) {
-          const Big& v = comp ? c.rk1[i][k] : c.rk0[i][k];
-          rk_out[((((size_t)i * 2 + comp) * (L + 1)) + j) * N + k] = big_mod_u64(v, c.qp[j]);
-        }
-  }
-  // transforms of the key over the oracle primes used by relinearisation:
-  // u < L * N * max(q) * QP
-  int bound = 56 + big_bits(c.QP) + c.logn + (int)std::ceil(std::log2((double)L + 1)) + 1;
-  int k = primes_needed(c, bound);
-  c.rk_nprimes = k;
-  c.rk_ntt.assign((size_t)L * 2 * k * N, 0);
-  for (int i = 0; i < L; ++i)
-    for (int comp = 0; comp < 2; ++comp)
-      for (int pi = 0; pi < k; ++pi) {
-        uint64_t* dst = &c.rk_ntt[(((size_t)i * 2 + comp) * k + pi) * N];
-        const Poly& src = comp ? c.rk1[i] : c.rk0[i];
-        for (int j = 0; j < N; ++j) dst[j] = big_mod_u64(src[j], c.om[pi]);
-        c.plans[pi].forward(dst);
-      }
+  make_ks_key(c, seed, s, poly_mul_exact(c, s, s), DOM_A_RK, DOM_E_RK, 0, c.rk, rk_out);
   c.have_rk = true;
   return 0;
 }
@@ -1239,6 +1302,62 @@ int orc_relin(void* h, const uint64_t* d3, uint64_t* out) {
   size_t s = (size_t)c.L * c.N;
   Poly d0 = poly_from_rns(c, d3), d1 = poly_from_rns(c, d3 + s), d2 = poly_from_rns(c, d3 + 2 * s);
   ct_to_rns(c, relinearize(c, d0, d1, d2), out);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Rotations and the rotate-and-add reduction behind COUNT and SUM (Sec. 4.2.2:
+// rotate, add, and double the rotation amount until every slot holds the sum).
+// The N slots form two rows of N/2 under the Galois group {+-3^k} mod 2N: g =
+// 3^(2^i) rotates each row by 2^i, g = 2N - 1 exchanges the rows.  The
+// reduction applies the row rotations by N/4, N/8, ..., 1 (largest first, as in
+// the paper's worked example), then the row exchange: log2 N steps in all.
+// ---------------------------------------------------------------------------
+
+// Galois key for element g (odd, < 2N) from the secret s: source tau_g(s).
+// gk_out (may be null): uint64 [L][2][L+1][N] residues mod q_0..q_{L-1}, P.
+int orc_galois_keygen(void* h, uint64_t seed, const int8_t* s_in, uint64_t g, uint64_t* gk_out) {
+  Ctx& c = *(Ctx*)h;
+  if (g % 2 == 0 || g >= 2 * (uint64_t)c.N) return -1;
+  Poly s = secret_poly(c, s_in);
+  Poly sg = automorph(c, s, g, nullptr);
+  make_ks_key(c, seed, s, sg, DOM_A_GK, DOM_E_GK, (uint32_t)(g << 5), c.gk[g], gk_out);
+  return 0;
+}
+
+// tau_g applied to both components (no key switching).
+int orc_automorphism(void* h, const uint64_t* x, uint64_t g, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (g % 2 == 0 || g >= 2 * (uint64_t)c.N) return -1;
+  ct_to_rns(c, ct_automorph(c, ct_from_rns(c, x), g), out);
+  return 0;
+}
+
+int orc_rotate(void* h, const uint64_t* x, uint64_t g, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.gk.count(g)) return -2;
+  ct_to_rns(c, ct_rotate(c, ct_from_rns(c, x), g), out);
+  return 0;
+}
+
+// ct <- ct + rotate(ct, g) for the first `row_steps` row rotations (by N/4, ...,
+// of the full logN - 1), then, if `swap`, the row exchange.
+int orc_rotate_sum(void* h, const uint64_t* x, int row_steps, int swap, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  const uint64_t twoN = 2 * (uint64_t)c.N;
+  if (row_steps < 0 || row_steps > c.logn - 1) return -1;
+  Ct a = ct_from_rns(c, x);
+  for (int st = 0; st < row_steps; ++st) {
+    const int i = c.logn - 2 - st;
+    const uint64_t g = powmod(3, (uint64_t)1 << i, twoN);
+    if (!c.gk.count(g)) return -2;
+    a = ct_add(c, a, ct_rotate(c, a, g));
+  }
+  if (swap) {
+    if (!c.gk.count(twoN - 1)) return -2;
+    a = ct_add(c, a, ct_rotate(c, a, twoN - 1));
+  }
+  ct_to_rns(c, a, out);
   return 0;
 }
 

@@ -434,3 +434,114 @@ def test_group_by_and_in_closed_form_n16(orc16):
     assert np.array_equal(got, np.isin(x, consts).astype(np.uint32))
     twice = o.decrypt(o.in_set(cx, [9, 9], masks=masks[[1, 1]]))
     assert np.array_equal(twice, 2 * (x == 9).astype(np.uint32))
+
+
+# ---- rotations and the rotate-and-add reduction (COUNT / SUM, Sec. 4.2.2) ----
+def _slot_exponents(logn):
+    """Slot j is the evaluation at psi^(2 brv(j) + 1) (the batch-encoding order)."""
+    N = 1 << logn
+    return np.array([2 * int(format(j, "0%db" % logn)[::-1], 2) + 1 for j in range(N)])
+
+
+def _slot_permutation(logn, g):
+    """tau_g(m)(psi^e) = m(psi^(e g)): new slot j takes old slot of exponent e_j g mod 2N."""
+    e = _slot_exponents(logn)
+    where = {int(v): j for j, v in enumerate(e)}
+    return np.array([where[int(v) * g % (2 << logn)] for v in e])
+
+
+def _secret_automorph(s, g):
+    N = len(s)
+    out = np.zeros(N, dtype=np.int64)
+    for j in range(N):
+        e = j * g % (2 * N)
+        if e < N:
+            out[e] += s[j]
+        else:
+            out[e - N] -= s[j]
+    return out.astype(np.int8)
+
+
+@pytest.mark.parametrize("g", [3, 9, 5, 31])
+def test_automorphism_permutes_slots(orc16, g):
+    """tau_g(ct) decrypts under tau_g(s) to the slots permuted by e -> e g (mod 2N);
+    tau_g(s) and the permutation are computed here from their definitions."""
+    o = orc16
+    rng = np.random.default_rng(20 + g)
+    x = rng.integers(0, T, o.N).astype(np.uint32)
+    ct = o.encrypt(x, 21, 0)
+    got = o.decrypt(o.automorphism(ct, g), s=_secret_automorph(o.s, g))
+    assert np.array_equal(got, x[_slot_permutation(o.logn, g)])
+
+
+def test_rotation_with_galois_key(orc16):
+    """Key switching with a Galois key brings tau_g(ct) back under s; the slots
+    are the same permutation and the noise budget stays positive."""
+    o = orc16
+    rng = np.random.default_rng(22)
+    x = rng.integers(0, T, o.N).astype(np.uint32)
+    ct = o.encrypt(x, 23, 0)
+    for g in o.galois_elements():
+        o.galois_keygen(5, g)
+        got, nb = o.decrypt(o.rotate(ct, g), with_noise=True)
+        assert np.array_equal(got, x[_slot_permutation(o.logn, g)]), g
+        assert nb > 0
+    with pytest.raises(RuntimeError):
+        o.rotate(ct, 7)  # no key for 7
+
+
+def test_galois_elements_generate_the_rows():
+    """3 has order N/2 mod 2N (one row), -1 is outside <3> (the other row)."""
+    for logn in (4, 12, 15):
+        twoN = 2 << logn
+        powers, v = set(), 1
+        for _ in range(twoN):
+            powers.add(v)
+            v = v * 3 % twoN
+        assert len(powers) == (1 << logn) // 2 and twoN - 1 not in powers
+
+
+def test_rotate_sum_paper_worked_example_n16(orc16):
+    """Sec. 4.2.2's 8-slot example on one row of N = 16 (a row holds 8 slots,
+    position r at exponent 3^r): rotate by 4 and add gives v_r + v_(r+4); by 2,
+    v_r + v_(r+2) + v_(r+4) + v_(r+6); by 1, the row sum.  The row exchange then
+    puts the sum of all 16 slots in every slot."""
+    o = orc16
+    N, twoN = o.N, 2 * o.N
+    for g in o.galois_elements():
+        o.galois_keygen(5, g)
+    e = _slot_exponents(o.logn)
+    where = {int(v): j for j, v in enumerate(e)}
+    row0 = [where[pow(3, r, twoN)] for r in range(8)]
+    row1 = [where[twoN - pow(3, r, twoN)] for r in range(8)]
+    v = np.array([1, 10, 100, 1000, 7, 70, 700, 7000])
+    w = np.array([3, 5, 11, 13, 17, 19, 23, 29])
+    x = np.zeros(N, dtype=np.uint32)
+    x[row0], x[row1] = v, w
+    ct = o.encrypt(x, 24, 0)
+    r = np.arange(8)
+    step1 = o.decrypt(o.rotate_sum(ct, row_steps=1, swap=False))
+    assert np.array_equal(step1[row0], v + v[(r + 4) % 8])
+    step2 = o.decrypt(o.rotate_sum(ct, row_steps=2, swap=False))
+    assert np.array_equal(step2[row0], v + v[(r + 2) % 8] + v[(r + 4) % 8] + v[(r + 6) % 8])
+    step3 = o.decrypt(o.rotate_sum(ct, row_steps=3, swap=False))
+    assert np.all(step3[row0] == v.sum()) and np.all(step3[row1] == w.sum())
+    full = o.decrypt(o.rotate_sum(ct))
+    assert np.all(full == (v.sum() + w.sum()) % T)
+
+
+def test_count_and_sum_closed_form_n16(orc16):
+    """COUNT = rotate-sum of an EQ mask, SUM = rotate-sum of column x mask (Eq. 5),
+    both mod p in every slot."""
+    o = orc16
+    for g in o.galois_elements():
+        o.galois_keygen(5, g)
+    rng = np.random.default_rng(25)
+    key = rng.integers(0, 4, o.N).astype(np.uint32)
+    price = rng.integers(0, T, o.N).astype(np.uint32)
+    ck, cp = o.encrypt(key, 26, 0), o.encrypt(price, 26, 1)
+    mask = o.eq(ck, None, const_val=2)
+    count, nb = o.decrypt(o.rotate_sum(mask), with_noise=True)
+    assert np.all(count == int((key == 2).sum())) and nb > 0
+    total = o.decrypt(o.rotate_sum(o.mul_relin(cp, mask)))
+    assert np.all(total == int(price[key == 2].astype(np.int64).sum() % T))
