@@ -171,6 +171,38 @@ int hp_autotune(hp_handle* h, size_t* best_tile);
 int hp_eq_fanout(hp_handle* h, const uint64_t* ct_x, size_t n_ct, const uint64_t* consts, size_t n_const,
                  uint64_t* masks, uint64_t* in_out, void* stream);
 
+/* ---- Rotations, COUNT and SUM (Sec. 4.2.2) ----------------------------------
+ * COUNT is the rotate-and-add reduction of an EQ mask, SUM that of
+ * column x mask (HP_SELECT, Eq. 5): rotate, add, double the rotation, until
+ * every slot holds the sum of all slots (mod t).  The slots form two rows of
+ * N/2 under the Galois group {+-3^k} mod 2N; the reduction applies the row
+ * rotations by N/4, N/8, ..., 1 (Galois elements 3^(2^i) mod 2N, i = logN-2..0)
+ * and then the row exchange (2N - 1): logN steps, one Galois key each.
+ *
+ * hp_galois_elements: the logN elements in that order (g_out: uint64 [logn]).
+ *
+ * hp_galois_keygen: Galois keys for those elements from the secret sk (device
+ * int8 [N], as made by hp_keygen with the same seed convention) and `seed`,
+ * installed in the handle.  Key st is the key-switching key from tau_g(s) to
+ * s: gk[st][i] = (-(a_i s + e_i) + P g_i tau_g(s), a_i) mod QP with a_i, e_i
+ * drawn by Philox with counter (k, j, (g << 5) | i, 7) resp. (k, 0, (g << 5) | i, 6).
+ * gk: NULL or device uint64 [logN][L][2][L+1][N] (residues mod q_0..q_{L-1}, P;
+ * the relinearisation-key layout per element).  Synchronous.
+ *
+ * hp_set_galois_keys: install keys made elsewhere (device, layout as above).
+ *
+ * hp_rotate_sum: out[o] = reduction of sum_{c in group o} x[c] for the groups of
+ * `group` consecutive ciphertexts (the last may be shorter): n_out =
+ * ceil(n_ct / group) ciphertexts, each holding in every slot the sum mod t of
+ * all slots of its group.  The result is exact (and a count or sum of the
+ * plain values) while that sum is below t.  out may equal x only when group ==
+ * 1 (in place); otherwise they must not overlap.  HP_ERR_STATE without Galois
+ * keys.  Device memory, stream-ordered. */
+int hp_galois_elements(int logn, uint64_t* g_out);
+int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk, void* stream);
+int hp_set_galois_keys(hp_handle* h, const uint64_t* gk);
+int hp_rotate_sum(hp_handle* h, const uint64_t* ct_x, size_t n_ct, size_t group, uint64_t* ct_out, void* stream);
+
 /* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
  * derivative, so this always returns HP_ERR_UNSUPPORTED. */
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream);

@@ -51,6 +51,14 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def galois_elements(logn: int):
+    """Elements of the rotate-and-add reduction (Sec. 4.2.2), in order: 3^(2^i)
+    mod 2N for i = logN-2 .. 0 (row rotations by N/4 .. 1), then 2N - 1 (row
+    exchange)."""
+    twoN = 2 << logn
+    return [pow(3, 1 << i, twoN) for i in range(logn - 2, -1, -1)] + [twoN - 1]
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -314,10 +322,7 @@ class Oracle:
 
     # -- rotations, COUNT / SUM (Sec. 4.2.2) -----------------------------------------
     def galois_elements(self):
-        """Elements of the rotate-and-add reduction, in order: 3^(2^i) mod 2N for
-        i = logN-2 .. 0 (row rotations by N/4 .. 1), then 2N - 1 (row exchange)."""
-        twoN = 2 * self.N
-        return [pow(3, 1 << i, twoN) for i in range(self.logn - 2, -1, -1)] + [twoN - 1]
+        return galois_elements(self.logn)
 
     def galois_keygen(self, seed: int, g: int, s=None):
         """Galois key for element g (uint64 [L][2][L+1][N]); kept for rotations."""

@@ -38,9 +38,25 @@ __global__ void k_pointwise_mont(const uint64_t* a, const uint64_t* b, uint64_t*
   c[gid] = mont_mul_lazy(a[gid], bb, cK.p[id], cK.pinv[id]);
 }
 
-// Relinearisation key, part 1: a_{i,j,k} (uniform mod p_j) into both the
-// output rk[i][1][j][k] and a work copy A[i][j][k].
-__global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN) {
+// tau_g(s) for the ternary secret: coefficient k moves to k g mod 2N, and to
+// -X^(e - N) when k g mod 2N = e >= N.
+__global__ void k_secret_automorph(const int8_t* s, int8_t* out, uint32_t g, int logN) {
+  const int N = 1 << logN;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const uint32_t e = (uint32_t)(((uint64_t)k * g) & (2 * (uint64_t)N - 1));
+  if (e < (uint32_t)N) {
+    out[e] = s[k];
+  } else {
+    out[e - N] = (int8_t)(-s[k]);
+  }
+}
+
+// Key-switching key (relinearisation: source s^2, domains A_RK / E_RK, object
+// i; Galois element g: source tau_g(s), domains A_GK / E_GK, object (g << 5) | i),
+// part 1: a_{i,j,k} (uniform mod p_j) into both the output rk[i][1][j][k] and a
+// work copy A[i][j][k].
+__global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN, uint32_t dom, uint32_t obj_base) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (size_t)L * NKS * N) return;
@@ -48,14 +64,15 @@ __global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN
   size_t ij = gid >> logN;
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
   int id = j < L ? j : ID_P;
-  uint64_t a = draw_uniform(philox((uint32_t)k, (uint32_t)j, (uint32_t)i, DOM_A_RK, seed), cK.p[id]);
+  uint64_t a = draw_uniform(philox((uint32_t)k, (uint32_t)j, obj_base | (uint32_t)i, dom, seed), cK.p[id]);
   A[gid] = a;
   rk[(((size_t)i * 2 + 1) * NKS + j) * N + k] = a;
 }
 
-// part 2: rk[i][0][j][k] = -(a s + e) + [i == j] [P]_{q_i} s^2  mod p_j, with
-// AS = a s and S2 = s^2 in coefficient domain (canonical).
-__global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2, uint64_t seed, int logN) {
+// part 2: rk[i][0][j][k] = -(a s + e) + [i == j] [P]_{q_i} src  mod p_j, with
+// AS = a s and S2 = the source secret in coefficient domain (canonical).
+__global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2, uint64_t seed, int logN,
+                            uint32_t dom, uint32_t obj_base) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (size_t)L * NKS * N) return;
@@ -64,7 +81,7 @@ __global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
   int id = j < L ? j : ID_P;
   uint64_t p = cK.p[id];
-  int e = draw_cbd21(philox((uint32_t)k, 0u, (uint32_t)i, DOM_E_RK, seed));
+  int e = draw_cbd21(philox((uint32_t)k, 0u, obj_base | (uint32_t)i, dom, seed));
   uint64_t em = e < 0 ? p - (uint64_t)(-e) : (uint64_t)e;
   uint64_t v = sub_mod(0, add_mod(AS[gid], em, p), p);
   if (j == i) {

@@ -103,7 +103,8 @@ HPD uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t se
   }
   return make_uint4(c0, c1, c2, c3);
 }
-enum { DOM_S = 1, DOM_E_ENC = 2, DOM_A_ENC = 3, DOM_E_RK = 4, DOM_A_RK = 5 };
+// Galois keys draw with object index (g << 5) | digit for Galois element g.
+enum { DOM_S = 1, DOM_E_ENC = 2, DOM_A_ENC = 3, DOM_E_RK = 4, DOM_A_RK = 5, DOM_E_GK = 6, DOM_A_GK = 7 };
 HPD int draw_ternary(uint4 w) { return (int)(((uint64_t)w.x * 3u) >> 32) - 1; }
 HPD int draw_cbd21(uint4 w) { return __popc(w.x & 0x1FFFFFu) - __popc(w.y & 0x1FFFFFu); }
 // floor(r m / 2^128) for the 128-bit r = w.w:w.z:w.y:w.x

@@ -3,7 +3,6 @@
 //   k_lift        (x - y) or x, centred-lifted exactly from Q to Q u B
 //   k_tensor      d0 = a0^2, d1 = 2 a0 a1, d2 = a1^2 (NTT domain, Montgomery)
 //   k_scale_round w = round(t d / Q) mod Q, exactly, via r = [t d]_Q lifted to B
-//   k_ks_expand   digits [d2]_{q_i} reduced mod every key-switching prime
 //   k_ks_mac      u_j = sum_i digit_i rk_{i,j} (NTT domain, 128-bit lazy sums)
 //   k_moddown     c += round(u / P) mod Q  (optionally fused with "1 -")
 #pragma once
@@ -179,22 +178,6 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
 
 HPD int ks_id(int j) { return j < L ? j : ID_P; }
 
-// One thread per (b, digit i, target j, n): ksin[b][i][j][n] = [w3[b][2][i][n]]_{p_j}.
-__global__ void __launch_bounds__(EW_THREADS) k_ks_expand(const uint64_t* __restrict__ w3, uint64_t* __restrict__ ksin,
-                                                          int logN, int nct) {
-  const int N = 1 << logN;
-  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)nct * L * NKS * N) return;
-  const int n = (int)(gid & (N - 1));
-  const size_t bij = gid >> logN;
-  const int j = (int)(bij % NKS);
-  const size_t bi = bij / NKS;
-  const int i = (int)(bi % L);
-  const size_t b = bi / L;
-  const uint64_t digit = w3[((b * 3 + 2) * L + i) * N + n];
-  ksin[gid] = csub(digit, cK.p[ks_id(j)]);  // digit < q_i < 2 p_j
-}
-
 // One thread per (target j, n), looping over the tile's ciphertexts so that
 // each key word is read once per launch.  rk: [L][2][NKS][N], NTT domain,
 // Montgomery form (canonical); digits in [0, 8p): sums < 15 8 p^2 < p 2^64.
@@ -324,6 +307,52 @@ __global__ void k_ct_sum(const uint64_t* __restrict__ M, int n_const, uint64_t* 
   uint64_t acc = 0;
   for (int k = 0; k < n_const; ++k) acc = add_mod(acc, M[(size_t)k * nwords + w], q);
   out[w] = acc;
+}
+
+// out[o] = sum of the ciphertexts x[o G .. min(n_ct, (o + 1) G)) (mod Q, word by
+// word; G = group).  out may alias x when G = 1 (each word is read, then written
+// by the same thread).
+__global__ void k_ct_group_sum(const uint64_t* x, size_t n_ct, size_t group, uint64_t* out, int logN, size_t W,
+                               size_t n_out) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= n_out * W) return;
+  const size_t o = gid / W, w = gid - o * W;
+  const uint64_t q = cK.p[prime_of_word(w, logN)];
+  const size_t c0 = o * group, c1 = c0 + group < n_ct ? c0 + group : n_ct;
+  uint64_t acc = 0;
+  for (size_t c = c0; c < c1; ++c) acc = add_mod(acc, x[c * W + w], q);
+  out[gid] = acc;
+}
+
+// Galois automorphism tau_g (rotation of the slots), gathered per output
+// coefficient: tau_g(a)_n = a_j with j = n g^{-1} mod 2N when j < N, else
+// -a_{j - N}.  One thread per (b, i, n); writes the key-switching input
+//   w3[b][0] = (acc ? c0 : 0) + tau_g(c0),  w3[b][1] = acc ? c1 : 0,
+//   w3[b][2] = tau_g(c1)   (switched from tau_g(s) to s by the Galois key),
+// so the mod-down that follows yields ct + rotate(ct) (acc) or rotate(ct).
+__global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict__ w3, uint32_t ginv, int acc,
+                            int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * L * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bi = gid >> logN;
+  const int i = (int)(bi % L);
+  const size_t b = bi / L;
+  const uint64_t q = cK.p[i];
+  const uint32_t j = (uint32_t)(((uint64_t)n * ginv) & (2 * (uint64_t)N - 1));
+  const uint32_t src = j < (uint32_t)N ? j : j - N;
+  const uint64_t* x0 = x + ((b * 2 + 0) * L + i) * N;
+  const uint64_t* x1 = x + ((b * 2 + 1) * L + i) * N;
+  uint64_t t0 = x0[src], t1 = x1[src];
+  if (j >= (uint32_t)N) {
+    t0 = sub_mod(0, t0, q);
+    t1 = sub_mod(0, t1, q);
+  }
+  uint64_t* o = w3 + (b * 3 * L + i) * N + n;
+  o[0] = acc ? add_mod(x0[n], t0, q) : t0;
+  o[(size_t)L * N] = acc ? x1[n] : 0;
+  o[(size_t)2 * L * N] = t1;
 }
 
 // out = g + k G  for a small integer k (Shoup companions per prime passed by value)

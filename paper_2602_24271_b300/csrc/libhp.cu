@@ -59,6 +59,10 @@ struct hp_handle {
   uint64_t* ltws = nullptr;
   size_t lt_tile = 0;
   uint32_t* lt_coef = nullptr;  // 32768 odd coefficients of the LT polynomial
+  // Galois keys of the rotate-and-add reduction (one per element of
+  // galois_elements, same layout and form as rkm), allocated on first use
+  uint64_t* gkm = nullptr;
+  bool have_gk = false;
   int* status = nullptr;  // device status word (ST_* bits)
   uint64_t launches = 0;
   std::string err;
@@ -83,7 +87,7 @@ enum {
   PK_LIFT = 4,          // [coefficients lifted]
   PK_TENSOR = 5,        // [residue products]
   PK_SCALE_ROUND = 6,   // [coefficients rounded]
-  PK_KS_EXPAND = 7,     // [words]
+  PK_AUTOMORPH = 7,     // [words written]
   PK_KS_MAC = 8,        // [multiply-accumulates]
   PK_MODDOWN = 9,       // [words]
   PK_COUNT = 10
@@ -470,7 +474,7 @@ static void free_all(hp_handle* h) {
   }
   void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
                   h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
-                  h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef};
+                  h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef, h->gkm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
@@ -914,6 +918,163 @@ int hp_eq_fanout(hp_handle* h, const uint64_t* x, size_t n_ct, const uint64_t* c
   return HP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Rotations and the rotate-and-add reduction of COUNT and SUM (Sec. 4.2.2).
+// The Galois group {+-3^k} mod 2N splits the slots into two rows of N/2:
+// g = 3^(2^i) rotates each row by 2^i, g = 2N - 1 exchanges the rows.  The
+// reduction rotates by N/4, N/8, ..., 1 (largest first, as in the paper's
+// doubling pattern) and then exchanges the rows: log2 N steps, one Galois key
+// each.
+// ---------------------------------------------------------------------------
+static void galois_elements(int logn, uint64_t* g) {
+  const uint64_t twoN = 2ull << logn;
+  int k = 0;
+  for (int i = logn - 2; i >= 0; --i) {
+    uint64_t v = 1, b = 3;
+    for (uint64_t e = 1ull << i; e; e >>= 1, b = b * b % twoN)
+      if (e & 1) v = v * b % twoN;
+    g[k++] = v;
+  }
+  g[k] = twoN - 1;
+}
+
+// g^{-1} mod 2N for odd g by Newton's iteration x <- x (2 - g x), which doubles
+// the number of correct low bits (g g = 1 mod 8 gives 3 to start).
+static uint32_t inverse_mod_2n(uint64_t g, int logn) {
+  uint64_t x = g;
+  for (int it = 0; it < 5; ++it) x = x * (2 - g * x);
+  return (uint32_t)(x & ((2ull << logn) - 1));
+}
+
+int hp_galois_elements(int logn, uint64_t* g_out) {
+  if (logn < 3 || logn > 16 || !g_out) return HP_ERR_ARG;
+  galois_elements(logn, g_out);
+  return HP_OK;
+}
+
+static size_t key_words(const hp_handle* h) { return (size_t)L * 2 * NKS * h->N; }
+
+static int install_galois_key(hp_handle* h, int st, const uint64_t* gk, cudaStream_t s) {
+  const size_t kw = key_words(h);
+  uint64_t* dst = h->gkm + (size_t)st * kw;
+  CU(h, cudaMemcpyAsync(dst, gk, kw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  ntt_fwd(h, dst, (size_t)L * 2 * NKS, MAP_KS, s);
+  k_to_mont<<<ew_blocks(kw), EW_THREADS, 0, s>>>(dst, NKS, 0, ID_P, (size_t)L * 2 * NKS, h->logn);
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
+static int alloc_gkm(hp_handle* h) {
+  if (!h->gkm) CU(h, cudaMalloc((void**)&h->gkm, (size_t)h->logn * key_words(h) * sizeof(uint64_t)));
+  return HP_OK;
+}
+
+int hp_set_galois_keys(hp_handle* h, const uint64_t* gk) {
+  if (!h) return HP_ERR_ARG;
+  if (!gk) HP_FAIL(h, HP_ERR_ARG, "null Galois keys");
+  if (!is_device_ptr(gk)) HP_FAIL(h, HP_ERR_ARG, "Galois keys must be device memory");
+  if (int rc = alloc_gkm(h)) return rc;
+  for (int st = 0; st < h->logn; ++st)
+    if (int rc = install_galois_key(h, st, gk + (size_t)st * key_words(h), 0)) return rc;
+  CU(h, cudaDeviceSynchronize());
+  h->have_gk = true;
+  return HP_OK;
+}
+
+int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  if (!sk) HP_FAIL(h, HP_ERR_ARG, "null secret key");
+  if (!is_device_ptr(sk) || (gk && !is_device_ptr(gk))) HP_FAIL(h, HP_ERR_ARG, "keys must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N, logN = h->logn;
+  const size_t kw = key_words(h);
+  if (int rc = alloc_gkm(h)) return rc;
+  uint64_t g[16];
+  galois_elements(logN, g);
+  uint64_t *S = nullptr, *S2 = nullptr, *A = nullptr, *K = nullptr;
+  int8_t* ts = nullptr;
+  CU(h, cudaMalloc(&S, (size_t)NKS * N * 8));
+  CU(h, cudaMalloc(&S2, (size_t)NKS * N * 8));
+  CU(h, cudaMalloc(&A, (size_t)L * NKS * N * 8));
+  CU(h, cudaMalloc(&ts, N));
+  if (!gk) CU(h, cudaMalloc(&K, kw * 8));
+  k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(sk, S, NKS, 0, ID_P, N);
+  ntt_fwd(h, S, NKS, MAP_KS, s);
+  for (int st = 0; st < logN; ++st) {
+    uint64_t* key = gk ? gk + (size_t)st * kw : K;
+    const uint32_t obj = (uint32_t)(g[st] << 5);
+    k_secret_automorph<<<ew_blocks(N), EW_THREADS, 0, s>>>(sk, ts, (uint32_t)g[st], logN);
+    k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(ts, S2, NKS, 0, ID_P, N);
+    k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(key, A, seed, logN, DOM_A_GK, obj);
+    ntt_fwd(h, A, (size_t)L * NKS, MAP_KS, s);
+    k_pointwise_mont<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P,
+                                                                          (size_t)L * NKS, logN);
+    ntt_inv(h, A, (size_t)L * NKS, MAP_KS, SCALE_NINV_R, s);
+    k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(key, A, S2, seed, logN, DOM_E_GK, obj);
+    if (int rc = install_galois_key(h, st, key, s)) return rc;
+  }
+  CU(h, cudaGetLastError());
+  CU(h, cudaStreamSynchronize(s));
+  cudaFree(S);
+  cudaFree(S2);
+  cudaFree(A);
+  cudaFree(ts);
+  if (K) cudaFree(K);
+  h->have_gk = true;
+  return HP_OK;
+}
+
+// ct <- ct + rotate(ct, g_st) in place on a tile of b ciphertexts.
+static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t ginv, cudaStream_t s) {
+  const int N = h->N, logN = h->logn;
+  {
+    ProfScope ps(h, PK_AUTOMORPH, s, 3.0 * b * L * N);
+    k_automorph<<<ew_blocks((size_t)b * L * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+  }
+  h->launches += 1;
+  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s, h->w3);
+  {
+    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * L * NKS * N);
+    k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->gkm + (size_t)st * key_words(h), h->ksout,
+                                                              logN, b);
+  }
+  h->launches += 1;
+  ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
+  {
+    ProfScope ps(h, PK_MODDOWN, s, 2.0 * b * L * N);
+    k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, ct, 0, logN, b);
+  }
+  h->launches += 1;
+}
+
+int hp_rotate_sum(hp_handle* h, const uint64_t* x, size_t n_ct, size_t group, uint64_t* out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (group == 0) HP_FAIL(h, HP_ERR_ARG, "group must be >= 1");
+  if (n_ct == 0) return HP_OK;
+  if (!x || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (!h->have_gk) HP_FAIL(h, HP_ERR_STATE, "Galois keys not set");
+  if (!is_device_ptr(x) || !is_device_ptr(out)) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be device memory");
+  if (((uintptr_t)x | (uintptr_t)out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  const size_t W = words_ct(h), n_out = (n_ct + group - 1) / group;
+  if (group > 1 && out < x + n_ct * W && x < out + n_out * W)
+    HP_FAIL(h, HP_ERR_ARG, "out overlaps x (allowed only in place with group = 1)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(group == 1 && out == x)) {
+    k_ct_group_sum<<<ew_blocks(n_out * W), EW_THREADS, 0, s>>>(x, n_ct, group, out, h->logn, W, n_out);
+    h->launches += 1;
+  }
+  uint64_t g[16];
+  galois_elements(h->logn, g);
+  const size_t TT = h->run_tile ? h->run_tile : h->tile;
+  for (size_t o0 = 0; o0 < n_out; o0 += TT) {
+    const int b = (int)((n_out - o0 < TT) ? n_out - o0 : TT);
+    for (int st = 0; st < h->logn; ++st) rotate_add_tile(h, out + o0 * W, b, st, inverse_mod_2n(g[st], h->logn), s);
+  }
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream) {
   (void)op;
   (void)grad_out;
@@ -957,12 +1118,12 @@ int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* strea
   ntt_fwd(h, S, NKS, MAP_KS, s);
   k_pointwise_mont<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(S, S, S2, NKS, NKS, 0, ID_P, NKS, logN);
   ntt_inv(h, S2, NKS, MAP_KS, SCALE_NINV_R, s);
-  k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, seed, logN);
+  k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, seed, logN, DOM_A_RK, 0);
   ntt_fwd(h, A, (size_t)L * NKS, MAP_KS, s);
   k_pointwise_mont<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P, (size_t)L * NKS,
                                                                         logN);
   ntt_inv(h, A, (size_t)L * NKS, MAP_KS, SCALE_NINV_R, s);
-  k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, S2, seed, logN);
+  k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, S2, seed, logN, DOM_E_RK, 0);
   CU(h, cudaGetLastError());
   CU(h, cudaStreamSynchronize(s));
   cudaFree(S);

@@ -42,12 +42,13 @@ EXPORTED = [
     "hp_destroy", "hp_last_error", "hp_keygen", "hp_encrypt", "hp_decrypt", "hp_launch_count",
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
+    "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
-                   "scale_round", "ks_expand", "ks_mac", "moddown"]
+                   "scale_round", "automorph", "ks_mac", "moddown"]
 KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows", "k_ntt_inv_rows", "k_ntt_inv_cols", "k_lift", "k_tensor_sq",
-                   "k_scale_round", "k_ks_expand", "k_ks_mac", "k_moddown"]
+                   "k_scale_round", "k_automorph", "k_ks_mac", "k_moddown"]
 
 
 class HpError(RuntimeError):
@@ -115,6 +116,10 @@ def load():
         "hp_autotune": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_size_t)]),
         "hp_lt_coefficients": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
         "hp_eq_fanout": (ctypes.c_int, [H, P64, SZ, ctypes.POINTER(ctypes.c_uint64), SZ, P64, P64, V]),
+        "hp_galois_elements": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+        "hp_galois_keygen": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
+        "hp_set_galois_keys": (ctypes.c_int, [H, P64]),
+        "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -260,6 +265,27 @@ class Context:
         _check(self.lib.hp_eq_fanout(self.h, _ptr(x), n, c, k, _ptr(m), _ptr(io), _stream(stream)), self.h)
         return m, io
 
+    def galois_keygen(self, seed: int, sk=None, keep: bool = False, stream=None):
+        """Galois keys of the rotate-and-add reduction (installed); returned as
+        [logN, L, 2, L+1, N] when `keep`."""
+        sk = self.sk if sk is None else sk
+        gk = self.torch.empty((self.log_n, self.L, 2, self.L + 1, self.N), dtype=self.torch.int64,
+                              device="cuda") if keep else None
+        _check(self.lib.hp_galois_keygen(self.h, seed, _ptr(sk), _ptr(gk), _stream(stream)), self.h)
+        return gk
+
+    def set_galois_keys(self, gk):
+        _check(self.lib.hp_set_galois_keys(self.h, _ptr(gk)), self.h)
+
+    def rotate_sum(self, x, group: int = 1, out=None, stream=None):
+        """COUNT / SUM reduction: ceil(n / group) ciphertexts whose every slot holds
+        the sum of all slots of a group of `group` consecutive ciphertexts."""
+        n = x.shape[0]
+        if out is None:
+            out = self.ct_empty((n + max(group, 1) - 1) // max(group, 1))
+        _check(self.lib.hp_rotate_sum(self.h, _ptr(x), n, group, _ptr(out), _stream(stream)), self.h)
+        return out
+
     def backward(self, op: int, grad_out, grad_x, n: int):
         return self.lib.hp_backward(self.h, op, _ptr(grad_out), _ptr(grad_x), n, None)
 
@@ -284,6 +310,14 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
         _check(self.lib.hp_profile_read(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)), self.h)
         return ms.value, int(n.value), w.value
+
+
+def galois_elements(log_n: int):
+    """Galois elements of the rotate-and-add reduction, in application order."""
+    lib = load()
+    g = (ctypes.c_uint64 * log_n)()
+    _check(lib.hp_galois_elements(log_n, g))
+    return [int(v) for v in g]
 
 
 def lt_coefficients() -> np.ndarray:

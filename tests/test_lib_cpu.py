@@ -110,3 +110,12 @@ def test_lt_coefficients_match_oracle(lib):
     got = hp.lt_coefficients()
     o = oracle.Oracle(4)
     assert np.array_equal(got, o.lt_coefficients())
+
+
+def test_galois_elements_match_oracle(lib):
+    """The library's rotate-and-add schedule equals the oracle's (elements and order)."""
+    for logn in (4, 12, 15):
+        assert hp.galois_elements(logn) == oracle.galois_elements(logn)
+    g = (ctypes.c_uint64 * 2)()
+    assert lib.hp_galois_elements(2, g) == hp.HP_ERR_ARG
+    assert lib.hp_galois_elements(12, None) == hp.HP_ERR_ARG
