@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in", "sum", "rotsum"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +51,14 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "sum":
+        return dict(n_ct=2048, op="sum", desc="SUM(y) WHERE x = c: SELECT (Eq. 5: EQ chain + column x mask) over 2^26 "
+                    "slots = 2048 BFV ciphertext pairs, then the whole column reduced by the rotate-and-add "
+                    "reduction (Sec. 4.2.2) into one ciphertext; N=32768, L=15, p=65537, bit-exact; value = slots/s")
+    if cfg == "rotsum":
+        return dict(n_ct=512, op="rotsum", desc="rotate-and-add reduction (COUNT/SUM, Sec. 4.2.2) of each of 512 BFV "
+                    "ciphertexts (2^24 slots): 15 rotations with key switching per ciphertext, N=32768, L=15, "
+                    "p=65537, bit-exact; value = slots reduced/s")
     if cfg == "in":
         return dict(n_ct=256, op="in", n_const=8,
                     desc="IN(x, S) (Eq. 6) with |S| = 8 constants, GROUP BY fan-out of 8 EQ chains per ciphertext: "
@@ -221,8 +229,13 @@ def run_libhp(args):
     N = ctx.N
     # inputs: rank r encrypts its own share (weak scaling, no exchange)
     x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank), value_bits=15 if wl["op"] == "lt" else 16)
+    const_val = 4242
+    if wl["op"] == "sum":  # WHERE x = c holds in about a quarter of the rows; y is the summed column
+        x[np.random.default_rng(rank_seed(SEED_DATA + 1, rank)).random(n_ct * N) < 0.25] = const_val
+    if wl["op"] in ("sum", "rotsum"):
+        ctx.galois_keygen(SEED_KEY)
     cx = ctx.ct_empty(n_ct)
-    cy = ctx.ct_empty(n_ct) if wl["op"] in ("ctct", "lt") else None
+    cy = ctx.ct_empty(n_ct) if wl["op"] in ("ctct", "lt", "sum") else None
     chunk = 128
     for c0 in range(0, n_ct, chunk):
         c1 = min(n_ct, c0 + chunk)
@@ -230,7 +243,7 @@ def run_libhp(args):
         if cy is not None:
             cy[c0:c1] = ctx.encrypt(y[c0 * N:c1 * N].reshape(-1, N), seed=SEED_DATA, ct_index0=n_ct + c0)
     out = ctx.ct_empty(n_ct)
-    const_val = 4242
+    agg = ctx.ct_empty(1)
     in_consts = [int(v) for v in x[:wl.get("n_const", 0)]]  # members drawn from the column itself
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -240,6 +253,13 @@ def run_libhp(args):
             ctx.run(hp.HP_LT, cx, cy, 0, out=out, stream=stream)
         elif wl["op"] == "in":
             ctx.eq_fanout(cx, in_consts, masks=False, in_set=out, stream=stream)
+        elif wl["op"] == "sum":
+            ctx.run(hp.HP_SELECT, cx, cy, const_val, out=out, stream=stream)
+            n = ctx.launch_count()
+            ctx.rotate_sum(out, group=n_ct, out=agg, stream=stream)
+            return n + ctx.launch_count()
+        elif wl["op"] == "rotsum":
+            ctx.rotate_sum(cx, out=out, stream=stream)
         elif cy is not None:
             ctx.run(hp.HP_EQ_CT_CT, cx, cy, 0, out=out, stream=stream)
         else:
@@ -296,9 +316,16 @@ def run_libhp(args):
     # correctness of this run (decrypt a few ciphertexts, closed form)
     probe = [0, n_ct // 2, n_ct - 1]
     dec = ctx.decrypt(out[probe])
+    if wl["op"] == "sum":
+        total = int(y[x == const_val].astype(np.int64).sum() % 65537)
+        assert np.all(ctx.decrypt(agg) == total), "SUM result wrong in benchmark run"
     for k, c in enumerate(probe):
         xs = x[c * N:(c + 1) * N]
-        if wl["op"] == "lt":
+        if wl["op"] == "sum":
+            ref = np.where(xs == const_val, y[c * N:(c + 1) * N], 0)
+        elif wl["op"] == "rotsum":
+            ref = np.full(N, int(xs.astype(np.int64).sum() % 65537))
+        elif wl["op"] == "lt":
             ref = xs < y[c * N:(c + 1) * N]
         elif wl["op"] == "in":
             ref = np.isin(xs, in_consts)
@@ -343,10 +370,10 @@ def run_libhp(args):
             "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
 
     # ---- end to end through the public API with pinned host buffers ----
-    if not args.no_e2e and wl["op"] not in ("lt", "in"):
+    if not args.no_e2e and wl["op"] not in ("lt", "in", "sum", "rotsum"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
-    if not args.no_cpu and rank == 0 and world == 1:
+    if not args.no_cpu and rank == 0 and world == 1 and wl["op"] != "rotsum":
         v, secs, desc = OracleSample().time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
