@@ -96,6 +96,7 @@ def _load():
         "orc_automorphism": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
         "orc_rotate": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
         "orc_rotate_sum": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, _u64p]),
+        "orc_mul_plain": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -353,6 +354,38 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("orc_rotate_sum failed (%d)" % rc)
         return out
+
+    # -- JOIN by Extract + Broadcast (Sec. 4.2.2) ------------------------------------
+    def mul_plain(self, x, m):
+        """ct * m for a plaintext polynomial m (uint64 [N], coefficients < t)."""
+        X, M, out = _c(x, np.uint64), _c(m, np.uint64), self._ct_out()
+        if self.lib.orc_mul_plain(self.h, _p(X, ctypes.c_uint64), _p(M, ctypes.c_uint64), _p(out, ctypes.c_uint64)) != 0:
+            raise ValueError("plaintext coefficients must be < t")
+        return out
+
+    def extract_broadcast(self, column, row: int):
+        """Extract row `row` of a column of ciphertexts (slot row % N of ciphertext
+        row // N: multiply by the plaintext unit vector of that slot) and broadcast
+        it to every slot by the rotate-and-add reduction."""
+        unit = np.zeros(self.N, dtype=np.uint32)
+        unit[row % self.N] = 1
+        return self.rotate_sum(self.mul_plain(column[row // self.N], self.encode(unit)))
+
+    def join(self, a_key, b_key, b_attrs, n_rows: int):
+        """Equi-join A.key = B.key over the first n_rows rows of B (Sec. 4.2.2):
+        mask_r = EQ(A.key, Broadcast(B.key[r])); with attributes, out[k] =
+        sum_r mask_r * Broadcast(B.attr_k[r]); without, out = sum_r mask_r."""
+        kb = [self.extract_broadcast(b_key, r) for r in range(n_rows)]
+        vb = [[self.extract_broadcast(col, r) for r in range(n_rows)] for col in b_attrs]
+        outs = []
+        for a in a_key:
+            masks = [self.eq(a, kb[r]) for r in range(n_rows)]
+            if not b_attrs:
+                outs.append(self.linear(np.stack(masks), [1] * n_rows)[None])
+            else:
+                outs.append(np.stack([self.linear(np.stack([self.mul_relin(masks[r], vb[k][r]) for r in range(n_rows)]),
+                                                  [1] * n_rows) for k in range(len(b_attrs))]))
+        return np.stack(outs, axis=1)  # [max(1, n_attr)][n_a][2][L][N]
 
     def lt(self, x, y):
         """LT(x, y) (Eq. 4) by the baby-step / giant-step schedule of the library."""

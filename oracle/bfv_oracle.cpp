@@ -1361,4 +1361,29 @@ int orc_rotate_sum(void* h, const uint64_t* x, int row_steps, int swap, uint64_t
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Plaintext multiplication and Extract + Broadcast (JOIN, Sec. 4.2.2).
+// ---------------------------------------------------------------------------
+
+// ct * m for a plaintext polynomial m (coefficients mod t, taken as centred
+// representatives in (-t/2, t/2]): (c0 m, c1 m) mod Q, exact negacyclic
+// products.  It decrypts to the slot-wise product of the two plaintexts.
+int orc_mul_plain(void* h, const uint64_t* x, const uint64_t* m, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  Poly mp(c.N);
+  for (int j = 0; j < c.N; ++j) {
+    if (m[j] >= c.t) return -1;
+    mp[j] = m[j] > c.t / 2 ? big_neg(big_u64(c.t - m[j])) : big_u64(m[j]);
+  }
+  Ct a = ct_from_rns(c, x), r;
+  r.c0 = poly_mul_exact(c, a.c0, mp);
+  r.c1 = poly_mul_exact(c, a.c1, mp);
+  for (int j = 0; j < c.N; ++j) {
+    r.c0[j] = mod_Q(c, r.c0[j]);
+    r.c1[j] = mod_Q(c, r.c1[j]);
+  }
+  ct_to_rns(c, r, out);
+  return 0;
+}
+
 }  // extern "C"

@@ -545,3 +545,56 @@ def test_count_and_sum_closed_form_n16(orc16):
     assert np.all(count == int((key == 2).sum())) and nb > 0
     total = o.decrypt(o.rotate_sum(o.mul_relin(cp, mask)))
     assert np.all(total == int(price[key == 2].astype(np.int64).sum() % T))
+
+
+# ---- JOIN by Extract + Broadcast (Sec. 4.2.2) ----
+def test_mul_plain_is_slotwise_product(orc16):
+    o = orc16
+    rng = np.random.default_rng(30)
+    x = rng.integers(0, T, o.N).astype(np.uint32)
+    v = rng.integers(0, T, o.N).astype(np.uint32)
+    v[:3] = [0, 1, T - 1]
+    got = o.decrypt(o.mul_plain(o.encrypt(x, 31, 0), o.encode(v)))
+    assert np.array_equal(got, (x.astype(np.int64) * v % T).astype(np.uint32))
+
+
+def test_extract_broadcast_n16(orc16):
+    o = orc16
+    for g in o.galois_elements():
+        o.galois_keygen(5, g)
+    rng = np.random.default_rng(32)
+    x = rng.integers(0, T, 2 * o.N).astype(np.uint32)
+    col = np.stack([o.encrypt(x[:o.N], 33, 0), o.encrypt(x[o.N:], 33, 1)])
+    for row in (0, 5, o.N - 1, o.N + 3):
+        got, nb = o.decrypt(o.extract_broadcast(col, row), with_noise=True)
+        assert np.all(got == x[row]) and nb > 0, row
+
+
+def test_join_closed_form_n16(orc16):
+    """SELECT size, brand FROM A, B WHERE A.key = B.key with unique B keys:
+    each A row gets the attributes of its matching B row, 0 without a match;
+    the attribute-free form (semi-join) gives the number of matches."""
+    o = orc16
+    for g in o.galois_elements():
+        o.galois_keygen(5, g)
+    N = o.N
+    rng = np.random.default_rng(34)
+    bkey = np.zeros(N, dtype=np.uint32)
+    bkey[:3] = [7, 42, 65000]
+    size = np.zeros(N, dtype=np.uint32)
+    size[:3] = [11, 22, 33]
+    brand = np.zeros(N, dtype=np.uint32)
+    brand[:3] = [100, 200, 300]
+    akey = rng.choice([7, 42, 65000, 5], N).astype(np.uint32)
+    ca = o.encrypt(akey, 35, 0)[None]
+    cb = o.encrypt(bkey, 35, 1)[None]
+    cs, cbr = o.encrypt(size, 35, 2)[None], o.encrypt(brand, 35, 3)[None]
+    out = o.join(ca, cb, [cs, cbr], 3)
+    for k, attr in enumerate((size, brand)):
+        ref = np.zeros(N, dtype=np.uint32)
+        for r in range(3):
+            ref[akey == bkey[r]] = attr[r]
+        got, nb = o.decrypt(out[k, 0], with_noise=True)
+        assert np.array_equal(got, ref) and nb > 0, k
+    semi = o.join(ca, cb, [], 3)
+    assert np.array_equal(o.decrypt(semi[0, 0]), np.isin(akey, bkey[:3]).astype(np.uint32))
