@@ -203,6 +203,31 @@ int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk
 int hp_set_galois_keys(hp_handle* h, const uint64_t* gk);
 int hp_rotate_sum(hp_handle* h, const uint64_t* ct_x, size_t n_ct, size_t group, uint64_t* ct_out, void* stream);
 
+/* ---- JOIN by Extract + Broadcast (Sec. 4.2.2) ---------------------------------
+ * Rows of a column: row r is slot r % N of ciphertext r / N (slot order of
+ * hp_encrypt).  Extract multiplies a ciphertext by the plaintext unit vector of
+ * one slot (plaintext coefficients taken centred in (-t/2, t/2]); Broadcast is
+ * the rotate-and-add reduction, so every slot ends holding the extracted value.
+ *
+ * hp_extract_broadcast: out[k] = Broadcast(Extract(column, row0 + k)),
+ * k < n_rows; column: n_ct ciphertexts; out must not overlap it.  Needs the
+ * Galois keys.
+ *
+ * hp_join: equi-join A.key = B.key over the first n_rows rows of table B:
+ *   kb_r = Broadcast(Extract(b_key, r)),  mask_r[c] = EQ(a_key[c], kb_r),
+ *   n_attr > 0:  out[k][c] = sum_r mask_r[c] * Broadcast(Extract(b_attr[k], r))
+ *   n_attr = 0:  out[0][c] = sum_r mask_r[c]   (semi-join: number of matches)
+ * a_key: n_a ciphertexts; b_key: ceil(n_rows / N) ciphertexts; b_attr:
+ * [n_attr][ceil(n_rows / N)] ciphertexts; out: [max(1, n_attr)][n_a]
+ * ciphertexts.  With unique B keys (a key-foreign key join) each A row gets
+ * the attributes of its matching B row, or 0.  Cost: n_rows * n_a EQ chains
+ * plus n_rows * n_a * n_attr products and (1 + n_attr) n_rows broadcasts.
+ * Needs the relinearisation and Galois keys; stream-ordered, device memory. */
+int hp_extract_broadcast(hp_handle* h, const uint64_t* column, size_t n_ct, size_t row0, size_t n_rows, uint64_t* out,
+                         void* stream);
+int hp_join(hp_handle* h, const uint64_t* a_key, size_t n_a, const uint64_t* b_key, const uint64_t* b_attr,
+            size_t n_attr, size_t n_rows, uint64_t* out, void* stream);
+
 /* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
  * derivative, so this always returns HP_ERR_UNSUPPORTED. */
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream);

@@ -355,6 +355,45 @@ __global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict
   o[(size_t)2 * L * N] = t1;
 }
 
+// ---- Extract (JOIN, Sec. 4.2.2): product with a plaintext unit vector --------------
+// Slot-domain unit vectors of rows r0 .. r0 + nct - 1: M[c][j] = [j == (r0 + c) mod N]
+// (input of the encoding transform).
+__global__ void k_unit_slots(uint64_t* __restrict__ M, uint64_t r0, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * N) return;
+  const size_t c = gid >> logN;
+  const uint64_t j = gid & (N - 1);
+  M[gid] = j == ((r0 + c) & (N - 1)) ? 1 : 0;
+}
+
+// Plaintext polynomials (coefficients < t) to the data primes with centred
+// representatives in (-t/2, t/2]: Mq[c][i][n].
+__global__ void k_plain_to_q(const uint64_t* __restrict__ M, uint64_t* __restrict__ Mq, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * L * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t ci = gid >> logN;
+  const int i = (int)(ci % L);
+  const size_t c = ci / L;
+  const uint64_t v = M[c * N + n], t = cK.p[ID_T];
+  Mq[gid] = v > t / 2 ? cK.p[i] - (t - v) : v;
+}
+
+// X[c][comp][i] <- X[c][comp][i] * Mq[c][i] 2^-64 (NTT domain, Montgomery; the
+// inverse transform's scaling restores the factor)
+__global__ void k_mul_plain_ntt(uint64_t* __restrict__ X, const uint64_t* __restrict__ Mq, int logN, int nct) {
+  const int N = 1 << logN;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)nct * 2 * L * N) return;
+  const int n = (int)(gid & (N - 1));
+  const size_t bci = gid >> logN;
+  const int i = (int)(bci % L);
+  const size_t c = bci / (2 * L);
+  X[gid] = mont_mul_lazy(X[gid], Mq[(c * L + i) * N + n], cK.p[i], cK.pinv[i]);
+}
+
 // out = g + k G  for a small integer k (Shoup companions per prime passed by value)
 struct ScalarK {
   uint64_t k[L], ks[L];

@@ -1047,6 +1047,17 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
   h->launches += 1;
 }
 
+// The reduction on n ciphertexts in place, in tiles.
+static void rotate_sum_inplace(hp_handle* h, uint64_t* ct, size_t n, cudaStream_t s) {
+  uint64_t g[16];
+  galois_elements(h->logn, g);
+  const size_t W = words_ct(h), TT = h->run_tile ? h->run_tile : h->tile;
+  for (size_t o0 = 0; o0 < n; o0 += TT) {
+    const int b = (int)((n - o0 < TT) ? n - o0 : TT);
+    for (int st = 0; st < h->logn; ++st) rotate_add_tile(h, ct + o0 * W, b, st, inverse_mod_2n(g[st], h->logn), s);
+  }
+}
+
 int hp_rotate_sum(hp_handle* h, const uint64_t* x, size_t n_ct, size_t group, uint64_t* out, void* stream) {
   if (!h) return HP_ERR_ARG;
   h->launches = 0;
@@ -1064,13 +1075,140 @@ int hp_rotate_sum(hp_handle* h, const uint64_t* x, size_t n_ct, size_t group, ui
     k_ct_group_sum<<<ew_blocks(n_out * W), EW_THREADS, 0, s>>>(x, n_ct, group, out, h->logn, W, n_out);
     h->launches += 1;
   }
-  uint64_t g[16];
-  galois_elements(h->logn, g);
-  const size_t TT = h->run_tile ? h->run_tile : h->tile;
-  for (size_t o0 = 0; o0 < n_out; o0 += TT) {
-    const int b = (int)((n_out - o0 < TT) ? n_out - o0 : TT);
-    for (int st = 0; st < h->logn; ++st) rotate_add_tile(h, out + o0 * W, b, st, inverse_mod_2n(g[st], h->logn), s);
+  rotate_sum_inplace(h, out, n_out, s);
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// JOIN by Extract + Broadcast (Sec. 4.2.2).  Extract keeps one slot of a
+// ciphertext (product with the plaintext unit vector of that slot), Broadcast
+// spreads it to every slot (the rotate-and-add reduction).  The equi-join
+// masks the A table with EQ(A.key, Broadcast(B.key[r])) per B row r and sums
+// mask x Broadcast(B.attr[r]) over r.
+// ---------------------------------------------------------------------------
+// out[c] = Broadcast(Extract(column, r0 + c)) for c < b (b <= tile); Mt, Mq:
+// temporaries of b N and b L N words.
+static int extract_broadcast_tile(hp_handle* h, const uint64_t* column, size_t r0, int b, uint64_t* out, uint64_t* Mt,
+                                  uint64_t* Mq, cudaStream_t s) {
+  const size_t W = words_ct(h), N = h->N;
+  const int logN = h->logn;
+  for (int c = 0; c < b; ++c)
+    CU(h, cudaMemcpyAsync(out + c * W, column + ((r0 + c) / N) * W, W * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  k_unit_slots<<<ew_blocks((size_t)b * N), EW_THREADS, 0, s>>>(Mt, r0, logN, b);
+  ntt_inv(h, Mt, b, MAP_T, SCALE_NINV, s);  // encoding: slots are the transform of m
+  k_plain_to_q<<<ew_blocks((size_t)b * L * N), EW_THREADS, 0, s>>>(Mt, Mq, logN, b);
+  ntt_fwd(h, Mq, (size_t)b * L, MAP_Q, s);
+  ntt_fwd(h, out, (size_t)b * 2 * L, MAP_Q, s);
+  k_mul_plain_ntt<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(out, Mq, logN, b);
+  ntt_inv(h, out, (size_t)b * 2 * L, MAP_Q, SCALE_NINV_R, s);
+  h->launches += 3;
+  rotate_sum_inplace(h, out, b, s);
+  return HP_OK;
+}
+
+static int extract_broadcast(hp_handle* h, const uint64_t* column, size_t row0, size_t n_rows, uint64_t* out,
+                             cudaStream_t s) {
+  const size_t W = words_ct(h), TT = h->run_tile ? h->run_tile : h->tile;
+  uint64_t *Mt = nullptr, *Mq = nullptr;
+  CU(h, cudaMallocAsync((void**)&Mt, TT * h->N * sizeof(uint64_t), s));
+  CU(h, cudaMallocAsync((void**)&Mq, TT * L * h->N * sizeof(uint64_t), s));
+  for (size_t r = 0; r < n_rows; r += TT) {
+    const int b = (int)((n_rows - r < TT) ? n_rows - r : TT);
+    if (int rc = extract_broadcast_tile(h, column, row0 + r, b, out + r * W, Mt, Mq, s)) return rc;
   }
+  cudaFreeAsync(Mt, s);
+  cudaFreeAsync(Mq, s);
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
+int hp_extract_broadcast(hp_handle* h, const uint64_t* column, size_t n_ct, size_t row0, size_t n_rows, uint64_t* out,
+                         void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (n_rows == 0) return HP_OK;
+  if (!column || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (!h->have_gk) HP_FAIL(h, HP_ERR_STATE, "Galois keys not set");
+  if (row0 + n_rows > n_ct * (size_t)h->N) HP_FAIL(h, HP_ERR_ARG, "rows beyond the column");
+  if (!is_device_ptr(column) || !is_device_ptr(out)) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be device memory");
+  if (((uintptr_t)column | (uintptr_t)out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  const size_t W = words_ct(h);
+  if (out < column + n_ct * W && column < out + n_rows * W) HP_FAIL(h, HP_ERR_ARG, "out overlaps the column");
+  return extract_broadcast(h, column, row0, n_rows, out, (cudaStream_t)stream);
+}
+
+// out[run] += src[run] for the items i0 .. i0 + b - 1 of an (r, c) item space
+// (item = r * n_a + c), grouped into runs of consecutive c.
+static void accumulate_items(hp_handle* h, uint64_t* out, const uint64_t* src, size_t i0, int b, size_t n_a,
+                             cudaStream_t s) {
+  const size_t W = words_ct(h);
+  for (int u = 0; u < b;) {
+    const size_t c = (i0 + u) % n_a;
+    const int run = (int)std::min<size_t>(b - u, n_a - c);
+    const size_t nw = (size_t)run * W;
+    k_ct_acc<<<ew_blocks(nw), EW_THREADS, 0, s>>>(out + c * W, src + (size_t)u * W, h->logn, nw);
+    h->launches += 1;
+    u += run;
+  }
+}
+
+int hp_join(hp_handle* h, const uint64_t* a_key, size_t n_a, const uint64_t* b_key, const uint64_t* b_attr,
+            size_t n_attr, size_t n_rows, uint64_t* out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (n_a == 0) return HP_OK;
+  if (!a_key || !b_key || !out || (n_attr && !b_attr)) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (n_rows == 0) HP_FAIL(h, HP_ERR_ARG, "n_rows must be >= 1");
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  if (!h->have_gk) HP_FAIL(h, HP_ERR_STATE, "Galois keys not set");
+  if (17 > supported_depth(h->logn, h->q, L, h->P, h->t)) HP_FAIL(h, HP_ERR_DEPTH, "depth 17 exceeds the budget");
+  if (!is_device_ptr(a_key) || !is_device_ptr(b_key) || !is_device_ptr(out) || (n_attr && !is_device_ptr(b_attr)))
+    HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be device memory");
+  if (((uintptr_t)a_key | (uintptr_t)b_key | (uintptr_t)b_attr | (uintptr_t)out) & 15)
+    HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t W = words_ct(h), N = h->N, n_b = (n_rows + N - 1) / N, TT = h->run_tile ? h->run_tile : h->tile;
+  const size_t n_out = n_attr ? n_attr : 1;
+  // broadcasts of every joined B row: keys, then each attribute column
+  uint64_t* BC = nullptr;
+  CU(h, cudaMallocAsync((void**)&BC, (1 + n_attr) * n_rows * W * sizeof(uint64_t), s));
+  uint64_t launches = 0;
+  if (int rc = extract_broadcast(h, b_key, 0, n_rows, BC, s)) return rc;
+  launches += h->launches;
+  for (size_t k = 0; k < n_attr; ++k) {
+    h->launches = 0;
+    if (int rc = extract_broadcast(h, b_attr + k * n_b * W, 0, n_rows, BC + (1 + k) * n_rows * W, s)) return rc;
+    launches += h->launches;
+  }
+  h->launches = 0;
+  CU(h, cudaMemsetAsync(out, 0, n_out * n_a * W * sizeof(uint64_t), s));
+  const size_t items = n_rows * n_a;  // item = r * n_a + c
+  for (size_t i0 = 0; i0 < items; i0 += TT) {
+    const int b = (int)((items - i0 < TT) ? items - i0 : TT);
+    for (int u = 0; u < b; ++u) {
+      const size_t r = (i0 + u) / n_a, c = (i0 + u) % n_a;
+      CU(h, cudaMemcpyAsync(h->stx + u * W, a_key + c * W, W * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+      CU(h, cudaMemcpyAsync(h->sty + u * W, BC + r * W, W * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    }
+    run_tile_mode(h, HP_EQ_CT_CT, LIFT_SUB_CT, h->stx, h->sty, nullptr, 0, h->sto, b, s);  // masks
+    if (!n_attr) {
+      accumulate_items(h, out, h->sto, i0, b, n_a, s);
+      continue;
+    }
+    for (size_t k = 0; k < n_attr; ++k) {
+      for (int u = 0; u < b; ++u) {
+        const size_t r = (i0 + u) / n_a;
+        CU(h, cudaMemcpyAsync(h->sty + u * W, BC + ((1 + k) * n_rows + r) * W, W * sizeof(uint64_t),
+                              cudaMemcpyDeviceToDevice, s));
+      }
+      hmul(h, h->sto, h->sty, h->sto2, b, s);
+      accumulate_items(h, out + k * n_a * W, h->sto2, i0, b, n_a, s);
+    }
+    CU(h, cudaGetLastError());
+  }
+  cudaFreeAsync(BC, s);
+  h->launches += launches;
   CU(h, cudaGetLastError());
   return HP_OK;
 }

@@ -43,6 +43,7 @@ EXPORTED = [
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
+    "hp_extract_broadcast", "hp_join",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -120,6 +121,8 @@ def load():
         "hp_galois_keygen": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
         "hp_set_galois_keys": (ctypes.c_int, [H, P64]),
         "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
+        "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
+        "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -284,6 +287,25 @@ class Context:
         if out is None:
             out = self.ct_empty((n + max(group, 1) - 1) // max(group, 1))
         _check(self.lib.hp_rotate_sum(self.h, _ptr(x), n, group, _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def extract_broadcast(self, column, row0: int, n_rows: int = 1, out=None, stream=None):
+        """Ciphertexts whose every slot holds row row0 + k of the column (k < n_rows)."""
+        if out is None:
+            out = self.ct_empty(n_rows)
+        _check(self.lib.hp_extract_broadcast(self.h, _ptr(column), column.shape[0], row0, n_rows, _ptr(out),
+                                             _stream(stream)), self.h)
+        return out
+
+    def join(self, a_key, b_key, b_attrs, n_rows: int, out=None, stream=None):
+        """Equi-join A.key = B.key over the first n_rows rows of B: [max(1, n_attr), n_a] ciphertexts."""
+        n_a = a_key.shape[0]
+        attrs = self.torch.stack(list(b_attrs)).contiguous() if len(b_attrs) else None
+        k = 0 if attrs is None else attrs.shape[0]
+        if out is None:
+            out = self.torch.empty((max(1, k), n_a, 2, self.L, self.N), dtype=self.torch.int64, device="cuda")
+        _check(self.lib.hp_join(self.h, _ptr(a_key), n_a, _ptr(b_key), _ptr(attrs), k, n_rows, _ptr(out),
+                                _stream(stream)), self.h)
         return out
 
     def backward(self, op: int, grad_out, grad_x, n: int):
