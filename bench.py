@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in", "sum", "rotsum"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in", "sum", "rotsum", "join"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +51,10 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "join":
+        return dict(n_ct=64, op="join", n_rows=16, desc="equi-join A.key = B.key (Sec. 4.2.2, Extract + Broadcast): "
+                    "A = 2^21 rows (64 BFV ciphertexts), 16 B rows with 2 attributes; 1024 EQ chains, 2048 products, "
+                    "48 broadcasts per step; N=32768, L=15, p=65537, bit-exact; value = A-row x B-row comparisons/s")
     if cfg == "sum":
         return dict(n_ct=2048, op="sum", desc="SUM(y) WHERE x = c: SELECT (Eq. 5: EQ chain + column x mask) over 2^26 "
                     "slots = 2048 BFV ciphertext pairs, then the whole column reduced by the rotate-and-add "
@@ -232,8 +236,16 @@ def run_libhp(args):
     const_val = 4242
     if wl["op"] == "sum":  # WHERE x = c holds in about a quarter of the rows; y is the summed column
         x[np.random.default_rng(rank_seed(SEED_DATA + 1, rank)).random(n_ct * N) < 0.25] = const_val
-    if wl["op"] in ("sum", "rotsum"):
+    if wl["op"] in ("sum", "rotsum", "join"):
         ctx.galois_keygen(SEED_KEY)
+    if wl["op"] == "join":  # B: 16 rows with distinct keys drawn from A's column, two attribute columns
+        jr = wl["n_rows"]
+        bkey = np.zeros(N, dtype=np.uint32)
+        bkey[:jr] = np.unique(x[: 64 * jr])[:jr]
+        battr = np.random.default_rng(rank_seed(SEED_DATA + 2, rank)).integers(0, 65537, (2, N)).astype(np.uint32)
+        cbk = ctx.encrypt(bkey.reshape(1, N), seed=SEED_DATA + 5, ct_index0=0)
+        cba = [ctx.encrypt(battr[k].reshape(1, N), seed=SEED_DATA + 5, ct_index0=1 + k) for k in range(2)]
+        jout = torch.empty((2, n_ct, 2, 15, N), dtype=torch.int64, device="cuda")
     cx = ctx.ct_empty(n_ct)
     cy = ctx.ct_empty(n_ct) if wl["op"] in ("ctct", "lt", "sum") else None
     chunk = 128
@@ -260,6 +272,8 @@ def run_libhp(args):
             return n + ctx.launch_count()
         elif wl["op"] == "rotsum":
             ctx.rotate_sum(cx, out=out, stream=stream)
+        elif wl["op"] == "join":
+            ctx.join(cx, cbk, cba, wl["n_rows"], out=jout, stream=stream)
         elif cy is not None:
             ctx.run(hp.HP_EQ_CT_CT, cx, cy, 0, out=out, stream=stream)
         else:
@@ -310,12 +324,12 @@ def run_libhp(args):
     ctx.check_status()
     ms_max = max_over_ranks(ms_total, dist, device="cuda")
     ms_per_step = ms_max / args.steps
-    slots_all = n_ct * N * world * wl.get("n_const", 1)
+    slots_all = n_ct * N * world * wl.get("n_const", 1) * wl.get("n_rows", 1)
     value = slots_all / (ms_per_step / 1e3)
 
     # correctness of this run (decrypt a few ciphertexts, closed form)
     probe = [0, n_ct // 2, n_ct - 1]
-    dec = ctx.decrypt(out[probe])
+    dec = ctx.decrypt((jout[1] if wl["op"] == "join" else out)[probe])
     if wl["op"] == "sum":
         total = int(y[x == const_val].astype(np.int64).sum() % 65537)
         assert np.all(ctx.decrypt(agg) == total), "SUM result wrong in benchmark run"
@@ -325,6 +339,10 @@ def run_libhp(args):
             ref = np.where(xs == const_val, y[c * N:(c + 1) * N], 0)
         elif wl["op"] == "rotsum":
             ref = np.full(N, int(xs.astype(np.int64).sum() % 65537))
+        elif wl["op"] == "join":
+            ref = np.zeros(N, dtype=np.uint32)
+            for r in range(wl["n_rows"]):
+                ref[xs == bkey[r]] = battr[1][r]
         elif wl["op"] == "lt":
             ref = xs < y[c * N:(c + 1) * N]
         elif wl["op"] == "in":
@@ -370,10 +388,10 @@ def run_libhp(args):
             "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
 
     # ---- end to end through the public API with pinned host buffers ----
-    if not args.no_e2e and wl["op"] not in ("lt", "in", "sum", "rotsum"):
+    if not args.no_e2e and wl["op"] not in ("lt", "in", "sum", "rotsum", "join"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
-    if not args.no_cpu and rank == 0 and world == 1 and wl["op"] != "rotsum":
+    if not args.no_cpu and rank == 0 and world == 1 and wl["op"] not in ("rotsum", "join"):
         v, secs, desc = OracleSample().time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
