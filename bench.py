@@ -26,7 +26,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2602_24271_b300.sharding import max_over_ranks, rank_seed  # noqa: E402
+from paper_2602_24271_b300.sharding import allgather_partials, max_over_ranks, rank_seed  # noqa: E402
 
 METRIC = "hot-path elements/s and % roofline, batched vs plain at stated error, 1 B300"
 UNIT = "elements/s"
@@ -256,6 +256,7 @@ def run_libhp(args):
             cy[c0:c1] = ctx.encrypt(y[c0 * N:c1 * N].reshape(-1, N), seed=SEED_DATA, ct_index0=n_ct + c0)
     out = ctx.ct_empty(n_ct)
     agg = ctx.ct_empty(1)
+    total_ct = ctx.ct_empty(1)
     in_consts = [int(v) for v in x[:wl.get("n_const", 0)]]  # members drawn from the column itself
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -269,7 +270,11 @@ def run_libhp(args):
             ctx.run(hp.HP_SELECT, cx, cy, const_val, out=out, stream=stream)
             n = ctx.launch_count()
             ctx.rotate_sum(out, group=n_ct, out=agg, stream=stream)
-            return n + ctx.launch_count()
+            n += ctx.launch_count()
+            if dist:  # the one exchange: all-gather the partial aggregates, add them mod Q
+                ctx.ct_sum(allgather_partials(agg[0], dist), group=world, out=total_ct, stream=stream)
+                n += ctx.launch_count()
+            return n
         elif wl["op"] == "rotsum":
             ctx.rotate_sum(cx, out=out, stream=stream)
         elif wl["op"] == "join":
@@ -333,6 +338,10 @@ def run_libhp(args):
     if wl["op"] == "sum":
         total = int(y[x == const_val].astype(np.int64).sum() % 65537)
         assert np.all(ctx.decrypt(agg) == total), "SUM result wrong in benchmark run"
+        if dist:
+            t = torch.tensor([total], dtype=torch.int64, device="cuda")
+            dist.all_reduce(t)
+            assert np.all(ctx.decrypt(total_ct) == int(t.item()) % 65537), "combined SUM wrong in benchmark run"
     for k, c in enumerate(probe):
         xs = x[c * N:(c + 1) * N]
         if wl["op"] == "sum":

@@ -199,6 +199,13 @@ int hp_eq_fanout(hp_handle* h, const uint64_t* ct_x, size_t n_ct, const uint64_t
  * 1 (in place); otherwise they must not overlap.  HP_ERR_STATE without Galois
  * keys.  Device memory, stream-ordered. */
 int hp_galois_elements(int logn, uint64_t* g_out);
+
+/* hp_ct_sum: out[o] = sum of the ciphertexts x[o group .. min(n_ct, (o + 1) group))
+ * mod Q (n_out = ceil(n_ct / group)); ciphertext addition, which decrypts to the
+ * slot-wise sum mod t.  It combines partial aggregates, e.g. the per-GPU results
+ * of a SUM after they are gathered (NCCL has no sum mod q).  Aliasing as for
+ * hp_rotate_sum.  Device memory, stream-ordered. */
+int hp_ct_sum(hp_handle* h, const uint64_t* ct_x, size_t n_ct, size_t group, uint64_t* ct_out, void* stream);
 int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk, void* stream);
 int hp_set_galois_keys(hp_handle* h, const uint64_t* gk);
 int hp_rotate_sum(hp_handle* h, const uint64_t* ct_x, size_t n_ct, size_t group, uint64_t* ct_out, void* stream);

@@ -1047,6 +1047,22 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
   h->launches += 1;
 }
 
+int hp_ct_sum(hp_handle* h, const uint64_t* x, size_t n_ct, size_t group, uint64_t* out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (group == 0) HP_FAIL(h, HP_ERR_ARG, "group must be >= 1");
+  if (n_ct == 0) return HP_OK;
+  if (!x || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (!is_device_ptr(x) || !is_device_ptr(out)) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be device memory");
+  const size_t W = words_ct(h), n_out = (n_ct + group - 1) / group;
+  if (group > 1 && out < x + n_ct * W && x < out + n_out * W)
+    HP_FAIL(h, HP_ERR_ARG, "out overlaps x (allowed only in place with group = 1)");
+  k_ct_group_sum<<<ew_blocks(n_out * W), EW_THREADS, 0, (cudaStream_t)stream>>>(x, n_ct, group, out, h->logn, W, n_out);
+  h->launches = 1;
+  CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
 // The reduction on n ciphertexts in place, in tiles.
 static void rotate_sum_inplace(hp_handle* h, uint64_t* ct, size_t n, cudaStream_t s) {
   uint64_t g[16];

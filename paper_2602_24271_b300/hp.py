@@ -43,7 +43,7 @@ EXPORTED = [
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
-    "hp_extract_broadcast", "hp_join",
+    "hp_extract_broadcast", "hp_join", "hp_ct_sum",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -121,6 +121,7 @@ def load():
         "hp_galois_keygen": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
         "hp_set_galois_keys": (ctypes.c_int, [H, P64]),
         "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
+        "hp_ct_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }
@@ -287,6 +288,14 @@ class Context:
         if out is None:
             out = self.ct_empty((n + max(group, 1) - 1) // max(group, 1))
         _check(self.lib.hp_rotate_sum(self.h, _ptr(x), n, group, _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def ct_sum(self, x, group: int, out=None, stream=None):
+        """Sums of groups of `group` consecutive ciphertexts (mod Q)."""
+        n = x.shape[0]
+        if out is None:
+            out = self.ct_empty((n + max(group, 1) - 1) // max(group, 1))
+        _check(self.lib.hp_ct_sum(self.h, _ptr(x), n, group, _ptr(out), _stream(stream)), self.h)
         return out
 
     def extract_broadcast(self, column, row0: int, n_rows: int = 1, out=None, stream=None):

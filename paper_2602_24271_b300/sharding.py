@@ -1,7 +1,11 @@
 """Host-side multi-GPU logic (one process per GPU).
 
-The equality predicate has no exchange step: ciphertexts (and instances) are
-independent, so ranks share nothing on the data path.  Two layouts:
+The predicates have no exchange step: ciphertexts (and instances) are
+independent, so ranks share nothing on their data path.  The one exchange is
+an aggregate (COUNT / SUM) over a column split across ranks: each rank reduces
+its share to one partial aggregate ciphertext, the partials are all-gathered,
+and every rank adds them with the library's ciphertext sum (collectives have
+no sum mod q).  Two layouts:
   * weak scaling: every rank processes its own batch of the same size (the
     benchmark; inputs drawn from a per-rank seed);
   * strong scaling of one batch: ciphertext range [start, end) per rank.
@@ -34,3 +38,15 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def allgather_partials(part, dist):
+    """All ranks' partial aggregate ciphertexts in rank order, [world, *part.shape]
+    (the part itself without a process group).  The caller adds them mod Q."""
+    import torch
+
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return part.unsqueeze(0)
+    parts = [torch.empty_like(part) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, part.contiguous())
+    return torch.stack(parts)

@@ -72,6 +72,19 @@ def test_groups_over_ragged_tiles(env):
         assert np.array_equal(hp.to_u64(got[k]), ref), k
 
 
+def test_ct_sum_matches_oracle(env):
+    ctx, o, _, _ = env
+    N = ctx.N
+    rng = np.random.default_rng(103)
+    x = rng.integers(0, T, 3 * N).astype(np.uint32)
+    cx = ctx.encrypt(x.reshape(3, N), seed=104)
+    got = ctx.ct_sum(cx, group=2)
+    ox = hp.to_u64(cx)
+    assert np.array_equal(hp.to_u64(got[0]), o.linear(ox[:2], [1, 1]))
+    assert np.array_equal(hp.to_u64(got[1]), ox[2])
+    assert np.array_equal(ctx.decrypt(got[0:1])[0], ((x[:N].astype(np.int64) + x[N:2 * N]) % T).astype(np.uint32))
+
+
 def test_in_place_equals_out_of_place(env):
     ctx, _, _, _ = env
     N = ctx.N
