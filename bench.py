@@ -128,10 +128,17 @@ NTT_CLASSES = {0, 1, 2, 3}
 MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-switch MAC
 
 
-def source_hash() -> str:
+KERNEL_SOURCES = {  # files whose text determines a kernel's code
+    "ntt": ["hp_defs.h", "hp_device.cuh", "hp_ntt.cuh"],
+    "rns": ["hp_defs.h", "hp_device.cuh", "hp_rns.cuh"],
+}
+
+
+def source_hash(kernel: str) -> str:
+    files = KERNEL_SOURCES["ntt" if kernel.startswith("k_ntt") else "rns"]
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2602_24271_b300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2602_24271_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -143,10 +150,8 @@ def load_traffic(kernel: str):
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if d.get("source_hash") != source_hash():
-        return None
     k = d.get("kernels", {}).get(kernel)
-    if not k:
+    if not k or k.get("source_hash") != source_hash(kernel):
         return None
     return k.get("dram_bytes_per_launch_full")
 
