@@ -125,7 +125,11 @@ class ClockSampler:
 # roofline helpers
 # ---------------------------------------------------------------------------
 NTT_CLASSES = {0, 1, 2, 3}
-N_SM, MUL_LANES_PER_SM_CLK, MUL_PER_BUTTERFLY, MUL_PER_MAC = 148, 32, 9, 4
+# per unit, in multiplier lane-slots: a butterfly's Shoup product is 9 single-slot
+# multiplies (3 wide, 2 high, 4 low); a 64-bit multiply-accumulate is 4 wide
+# multiply-adds with a 64-bit addend, two slots each (the ratio of the two
+# register-only probes, 0.97 T butterflies/s and 1.06 T MAC/s, agrees)
+N_SM, MUL_LANES_PER_SM_CLK, MUL_PER_BUTTERFLY, MUL_PER_MAC = 148, 32, 9, 8
 MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-switch MAC
 
 
@@ -371,9 +375,8 @@ def run_libhp(args):
     work_per_launch = dom_work / max(1, dom_n)
     kernel = hp.KERNEL_OF_CLASS[dom]
     # ALU peak from unit counts and the clock seen in the timed region: 148 SMs x
-    # SM clock x 32 multiply-class lane-operations per SM per clock (the FMA-heavy
-    # pipe's rate for the 32x32 -> 64-bit integer multiplies), / 9 multiplies per
-    # butterfly or / 4 per 64-bit multiply-accumulate
+    # SM clock x 32 multiplier lane-slots per SM per clock (the FMA-heavy pipe),
+    # / 9 slots per butterfly or / 8 per 64-bit multiply-accumulate
     mhz = clk.get("sm_mhz") or 2032.0
     mul_rate = N_SM * mhz * 1e6 * MUL_LANES_PER_SM_CLK
     if dom in NTT_CLASSES:
@@ -395,7 +398,7 @@ def run_libhp(args):
     roof["avg_launch_ms"] = avg_ms
     roof["share_of_step"] = shares[dom] / tot if tot else None
     if probe is not None:
-        roof["peak_source"] = ("derived: 148 SMs x %.0f MHz x 32 multiply lane-ops per SM per clock / %d multiplies "
+        roof["peak_source"] = ("derived: 148 SMs x %.0f MHz x 32 multiplier lane-slots per SM per clock / %d slots "
                                "per unit" % (mhz, MUL_PER_BUTTERFLY if dom in NTT_CLASSES else MUL_PER_MAC))
         roof["probe_peak"] = probe / 1e9
         roof["frac_of_probe"] = roof["achieved"] / roof["probe_peak"]

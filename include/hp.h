@@ -13,16 +13,19 @@
  *   special prime   P < 2^56, P = 1 mod 2^16 (relinearisation only)
  *   plaintext       t = p = 65537
  *   multiplication  textbook Fan-Vercauteren: centred lift, exact tensor,
- *                   round(t d / Q) mod Q; relinearisation with per-prime digits
- *                   [d2]_{q_i} and the special prime P.  Results are bit-exact
- *                   against that integer definition.
+ *                   round(t d / Q) mod Q; key switching (relinearisation,
+ *                   rotations) with D = L / 3 digits [d2]_{q_3a q_3a+1 q_3a+2},
+ *                   each the residue modulo a group of three data primes, and
+ *                   the special prime P.  Results are bit-exact against that
+ *                   integer definition.
  *
  * Memory layouts (all words uint64, residues canonical in [0, prime)):
  *   ciphertext      [2][L][N]        (c0, c1) residues mod q_0..q_{L-1},
  *                                    coefficient domain; n ciphertexts are
  *                                    contiguous: [n][2][L][N]
- *   relin key       [L][2][L+1][N]   rk_i = (rk_i0, rk_i1), residues mod
- *                                    q_0..q_{L-1}, P; coefficient domain
+ *   relin key       [D][2][L+1][N]   rk_a = (rk_a0, rk_a1) for digit a < D = 5,
+ *                                    residues mod q_0..q_{L-1}, P; coefficient
+ *                                    domain
  *   secret key      int8 [N]         coefficients in {-1, 0, 1}
  *   slots           uint32 [N]       plaintext slot values mod t
  *
@@ -186,7 +189,7 @@ int hp_eq_fanout(hp_handle* h, const uint64_t* ct_x, size_t n_ct, const uint64_t
  * installed in the handle.  Key st is the key-switching key from tau_g(s) to
  * s: gk[st][i] = (-(a_i s + e_i) + P g_i tau_g(s), a_i) mod QP with a_i, e_i
  * drawn by Philox with counter (k, j, (g << 5) | i, 7) resp. (k, 0, (g << 5) | i, 6).
- * gk: NULL or device uint64 [logN][L][2][L+1][N] (residues mod q_0..q_{L-1}, P;
+ * gk: NULL or device uint64 [logN][D][2][L+1][N] (residues mod q_0..q_{L-1}, P;
  * the relinearisation-key layout per element).  Synchronous.
  *
  * hp_set_galois_keys: install keys made elsewhere (device, layout as above).
@@ -290,7 +293,7 @@ int hp_check_status(hp_handle* h);
  * hp_run(h, HP_SQUARE, ct_in, NULL, 0, ct_out, 1, stream) computes (one
  * squaring + relinearisation of ONE ciphertext, bit-identical), but its
  * working buffers live in a fixed array in the library's device memory image
- * (472 words per coefficient for ring degree <= 4096: 15.5 MB, held by every
+ * (312 words per coefficient for ring degree <= 4096: 10.2 MB, held by every
  * GPU that loads the library until the process exits) instead of the
  * handle's workspace.  It calls no allocation routine.
  *   - ring degree above 4096: HP_ERR_UNSUPPORTED, nothing launched;

@@ -13,7 +13,8 @@ exposes; the arithmetic lives in the C++ file.
 
 Array conventions (numpy):
   ciphertext  uint64 [2][L][N]  residues mod q_0..q_{L-1}, coefficient domain
-  relin key   uint64 [L][2][L+1][N]  residues mod q_0..q_{L-1}, P
+  relin key   uint64 [D][2][L+1][N]  residues mod q_0..q_{L-1}, P; D = ceil(L / 3)
+              key-switching digits, each the residue mod a group of 3 data primes
   secret key  int8 [N] in {-1, 0, 1}
   slots       uint32 [N] values mod t
 """
@@ -69,6 +70,7 @@ def _load():
         "orc_default_primes": (ctypes.c_int, [ctypes.c_int, _u64p, _u64p]),
         "orc_create": (V, [ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_uint64, ctypes.c_uint64]),
         "orc_destroy": (None, [V]),
+        "orc_num_digits": (ctypes.c_int, [V]),
         "orc_export_big": (ctypes.c_int, [V, ctypes.c_int, _u64p, ctypes.c_int]),
         "orc_philox": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u32p]),
         "orc_philox_raw": (None, [_u32p, _u32p, _u32p]),
@@ -174,6 +176,7 @@ class Oracle:
         self.t = int(t)
         qa = np.array(self.q, dtype=np.uint64)
         self.h = self.lib.orc_create(logn, self.L, _p(qa, ctypes.c_uint64), self.P, self.t)
+        self.D = self.lib.orc_num_digits(self.h)
         if not self.h:
             raise RuntimeError("orc_create failed")
         self.s = None
@@ -233,7 +236,7 @@ class Oracle:
     def keygen(self, seed: int):
         """Secret key and relinearisation key from `seed` (stored for later ops)."""
         s = np.zeros(self.N, dtype=np.int8)
-        rk = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
+        rk = np.zeros((self.D, 2, self.L + 1, self.N), dtype=np.uint64)
         self.lib.orc_keygen(self.h, seed, _p(s, ctypes.c_int8), _p(rk, ctypes.c_uint64))
         self.s, self.rk = s, rk
         return s, rk
@@ -326,9 +329,9 @@ class Oracle:
         return galois_elements(self.logn)
 
     def galois_keygen(self, seed: int, g: int, s=None):
-        """Galois key for element g (uint64 [L][2][L+1][N]); kept for rotations."""
+        """Galois key for element g (uint64 [D][2][L+1][N]); kept for rotations."""
         s = self.s if s is None else _c(s, np.int8)
-        gk = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
+        gk = np.zeros((self.D, 2, self.L + 1, self.N), dtype=np.uint64)
         if self.lib.orc_galois_keygen(self.h, seed, _p(s, ctypes.c_int8), g, _p(gk, ctypes.c_uint64)) != 0:
             raise ValueError("Galois element must be odd and < 2N")
         return gk

@@ -483,14 +483,17 @@ static int brv(int x, int bits) {
 // ---------------------------------------------------------------------------
 typedef std::vector<Big> Poly;  // N big-integer coefficients
 
-// A key-switching key from a secret s' to s: k_i = (-(a_i s + e_i) + P g_i s',
-// a_i) mod QP, i < L (per-prime digits, one special prime), kept in big-integer
-// form and transformed over the oracle primes used for the exact products.
+// A key-switching key from a secret s' to s: k_a = (-(a_a s + e_a) + P g_a s',
+// a_a) mod QP for the digits a < D (groups of DIGIT_PRIMES data primes, one
+// special prime), kept in big-integer form and transformed over the oracle
+// primes used for the exact products.
 struct KsKey {
   std::vector<Poly> k0, k1;
   int nprimes = 0;
   std::vector<uint64_t> ntt;      // [i][comp][prime][N]
 };
+
+enum { DIGIT_PRIMES = 3 };  // data primes per key-switching digit
 
 struct Ctx {
   int logn, N, L;
@@ -503,6 +506,11 @@ struct Ctx {
   std::vector<NttPlan> plans;     // one per oracle prime
   NttPlan tplan;                  // plaintext-modulus transform (batch encoding)
   std::vector<Crt> crt_prefix;    // crt over the first k oracle primes, k = 1..
+  // key-switching digits: consecutive groups of DIGIT_PRIMES data primes,
+  // digit a = [d]_{Q_a}, Q_a the product of group a's primes
+  int D = 0;
+  std::vector<std::vector<uint64_t>> grp;
+  std::vector<Big> Qa;
   // relinearisation key and Galois keys (switching from s^2, resp. tau_g(s), to s)
   bool have_rk = false;
   KsKey rk;
@@ -693,29 +701,29 @@ static Ct ct_one_minus(const Ctx& c, const Ct& x) {
 }
 
 // Key switching of (d0, d1, d2), coefficients in [0, Q), where d2 is to be
-// multiplied by the key's source secret: (d0, d1) + round(sum_i [d2]_{q_i} k_i / P)
-// mod Q.  With the relinearisation key this is relinearisation (source s^2);
+// multiplied by the key's source secret: (d0, d1) + round(sum_a [d2]_{Q_a} k_a / P)
+// mod Q, digits a < D over groups of DIGIT_PRIMES data primes.  With the relinearisation key this is relinearisation (source s^2);
 // with a Galois key it completes an automorphism (source tau_g(s)).
 static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d1, const Poly& d2) {
-  int N = c.N, L = c.L, k = K.nprimes;
-  // u = sum_i digit_i * rk_i  (exact integer negacyclic products, then mod QP)
+  int N = c.N, D = c.D, k = K.nprimes;
+  // u = sum_a digit_a * k_a  (exact integer negacyclic products, then mod QP)
   std::vector<uint64_t> res0((size_t)k * N), res1((size_t)k * N);
-  std::vector<uint64_t> digit((size_t)L * N);  // digit_i = [d2]_{q_i}
-  for (int i = 0; i < L; ++i)
-    for (int j = 0; j < N; ++j) digit[(size_t)i * N + j] = big_mod_u64(d2[j], c.q[i]);
-  std::vector<uint64_t> D(N), acc0(N), acc1(N);
+  std::vector<Big> digit((size_t)D * N);  // digit_a = [d2]_{Q_a}
+  for (int a = 0; a < D; ++a)
+    for (int j = 0; j < N; ++j) digit[(size_t)a * N + j] = mod_primes(d2[j], c.Qa[a], c.grp[a]);
+  std::vector<uint64_t> Dg(N), acc0(N), acc1(N);
   for (int pi = 0; pi < k; ++pi) {
     uint64_t m = c.om[pi];
     std::fill(acc0.begin(), acc0.end(), 0);
     std::fill(acc1.begin(), acc1.end(), 0);
-    for (int i = 0; i < L; ++i) {
-      for (int j = 0; j < N; ++j) D[j] = digit[(size_t)i * N + j] % m;
-      c.plans[pi].forward(D.data());
-      const uint64_t* K0 = &K.ntt[(((size_t)i * 2 + 0) * k + pi) * N];
-      const uint64_t* K1 = &K.ntt[(((size_t)i * 2 + 1) * k + pi) * N];
+    for (int a = 0; a < D; ++a) {
+      for (int j = 0; j < N; ++j) Dg[j] = big_mod_u64(digit[(size_t)a * N + j], m);
+      c.plans[pi].forward(Dg.data());
+      const uint64_t* K0 = &K.ntt[(((size_t)a * 2 + 0) * k + pi) * N];
+      const uint64_t* K1 = &K.ntt[(((size_t)a * 2 + 1) * k + pi) * N];
       for (int j = 0; j < N; ++j) {
-        acc0[j] = addmod(acc0[j], mulmod(D[j], K0[j], m), m);
-        acc1[j] = addmod(acc1[j], mulmod(D[j], K1[j], m), m);
+        acc0[j] = addmod(acc0[j], mulmod(Dg[j], K0[j], m), m);
+        acc1[j] = addmod(acc1[j], mulmod(Dg[j], K1[j], m), m);
       }
     }
     c.plans[pi].inverse(acc0.data());
@@ -798,59 +806,67 @@ static Poly phase(const Ctx& c, const Ct& ct, const int8_t* s) {
 // extern "C" interface (consumed by oracle/__init__.py through ctypes)
 // ---------------------------------------------------------------------------
 // Key-switching key from source secret `src` (an integer polynomial: s^2 or
-// tau_g(s)) to s: k_i = (-(a_i s + e_i) + P g_i src, a_i) mod QP with
-// g_i = (Q/q_i) [(Q/q_i)^{-1}]_{q_i}; a_i uniform mod QP (residue j drawn with
-// counter (k, j, obj_base | i, dom_a)), e_i centred binomial (counter
-// (k, 0, obj_base | i, dom_e)).  `out` (may be null): uint64 [L][2][L+1][N].
+// tau_g(s)) to s: k_a = (-(a_a s + e_a) + P g_a src, a_a) mod QP for digit a,
+// with g_a = (Q/Q_a) [(Q/Q_a)^{-1}]_{Q_a} = sum over the group's primes q_i of
+// (Q/q_i) [(Q/q_i)^{-1}]_{q_i} (both are 1 mod Q_a and 0 mod Q/Q_a); a_a
+// uniform mod QP (residue j drawn with counter (k, j, obj_base | a, dom_a)),
+// e_a centred binomial (counter (k, 0, obj_base | a, dom_e)).
+// `out` (may be null): uint64 [D][2][L+1][N].
 static void make_ks_key(const Ctx& c, uint64_t seed, const Poly& s, const Poly& src, uint32_t dom_a, uint32_t dom_e,
                         uint32_t obj_base, KsKey& K, uint64_t* out) {
-  int N = c.N, L = c.L;
+  int N = c.N, L = c.L, D = c.D;
   uint32_t w[4];
-  K.k0.assign(L, Poly(N));
-  K.k1.assign(L, Poly(N));
+  K.k0.assign(D, Poly(N));
+  K.k1.assign(D, Poly(N));
   std::vector<uint64_t> res(L + 1);
-  for (int i = 0; i < L; ++i) {
-    uint64_t rr;
-    Big qhat = mag_divmod_u64(c.Q, c.q[i], &rr);
-    uint64_t qhat_inv = invmod(big_mod_u64(qhat, c.q[i]), c.q[i]);
-    Big Pg = big_mul_u64(big_mul_u64(qhat, qhat_inv), c.P);
-    Poly a(N), e(N);
+  for (int a = 0; a < D; ++a) {
+    Big g = big_zero();
+    for (int i = a * DIGIT_PRIMES; i < std::min(L, (a + 1) * DIGIT_PRIMES); ++i) {
+      uint64_t rr;
+      Big qhat = mag_divmod_u64(c.Q, c.q[i], &rr);
+      uint64_t qhat_inv = invmod(big_mod_u64(qhat, c.q[i]), c.q[i]);
+      g = big_add(g, big_mul_u64(qhat, qhat_inv));
+    }
+    Big Pg = big_mul_u64(g, c.P);
+    Poly av(N), e(N);
     for (int k = 0; k < N; ++k) {
       for (int j = 0; j <= L; ++j) {
-        draw(seed, k, j, obj_base | (uint32_t)i, dom_a, w);
+        draw(seed, k, j, obj_base | (uint32_t)a, dom_a, w);
         res[j] = sample_uniform(w, c.qp[j]);
       }
-      a[k] = c.crtQP.reconstruct(res.data());
-      draw(seed, k, 0, obj_base | (uint32_t)i, dom_e, w);
+      av[k] = c.crtQP.reconstruct(res.data());
+      draw(seed, k, 0, obj_base | (uint32_t)a, dom_e, w);
       int ev = sample_cbd21(w);
       e[k] = big_u64((uint64_t)std::abs(ev));
       if (ev < 0) e[k] = big_neg(e[k]);
     }
-    Poly as = poly_mul_exact(c, a, s);
+    Poly as = poly_mul_exact(c, av, s);
     for (int k = 0; k < N; ++k) {
       Big v = big_neg(big_add(as[k], e[k]));
       v = big_add(v, big_mul(Pg, src[k]));
-      K.k0[i][k] = mod_QP(c, v);
-      K.k1[i][k] = a[k];
+      K.k0[a][k] = mod_QP(c, v);
+      K.k1[a][k] = av[k];
     }
     if (out)
       for (int comp = 0; comp < 2; ++comp)
         for (int j = 0; j <= L; ++j)
           for (int k = 0; k < N; ++k) {
-            const Big& v = comp ? K.k1[i][k] : K.k0[i][k];
-            out[((((size_t)i * 2 + comp) * (L + 1)) + j) * N + k] = big_mod_u64(v, c.qp[j]);
+            const Big& v = comp ? K.k1[a][k] : K.k0[a][k];
+            out[((((size_t)a * 2 + comp) * (L + 1)) + j) * N + k] = big_mod_u64(v, c.qp[j]);
           }
   }
-  // transforms over the oracle primes: |u| < L N max(q) QP
-  int bound = 56 + big_bits(c.QP) + c.logn + (int)std::ceil(std::log2((double)L + 1)) + 1;
+  // transforms over the oracle primes: |u| < D N max(Q_a) QP
+  int dbits = 0;
+  for (const Big& M : c.Qa) dbits = std::max(dbits, big_bits(M));
+  int bound = dbits + big_bits(c.QP) + c.logn + (int)std::ceil(std::log2((double)D + 1)) + 1;
   int k = primes_needed(c, bound);
   K.nprimes = k;
-  K.ntt.assign((size_t)L * 2 * k * N, 0);
-  for (int i = 0; i < L; ++i)
+  K.ntt.assign((size_t)D * 2 * k * N, 0);
+  for (int a = 0; a < D; ++a)
     for (int comp = 0; comp < 2; ++comp)
       for (int pi = 0; pi < k; ++pi) {
-        uint64_t* dst = &K.ntt[(((size_t)i * 2 + comp) * k + pi) * N];
-        const Poly& srcp = comp ? K.k1[i] : K.k0[i];
+        uint64_t* dst = &K.ntt[(((size_t)a * 2 + comp) * k + pi) * N];
+        const Poly& srcp = comp ? K.k1[a] : K.k0[a];
         for (int j = 0; j < N; ++j) dst[j] = big_mod_u64(srcp[j], c.om[pi]);
         c.plans[pi].forward(dst);
       }
@@ -935,8 +951,21 @@ void* orc_create(int logn, int L, const uint64_t* q, uint64_t P, uint64_t t) {
   for (size_t k = 1; k <= c->om.size(); ++k)
     c->crt_prefix[k - 1].init(std::vector<uint64_t>(c->om.begin(), c->om.begin() + k));
   c->tplan.init(logn, t);
+  c->D = (L + DIGIT_PRIMES - 1) / DIGIT_PRIMES;
+  c->grp.resize(c->D);
+  c->Qa.resize(c->D);
+  for (int a = 0; a < c->D; ++a) {
+    Big M = big_u64(1);
+    for (int i = a * DIGIT_PRIMES; i < std::min(L, (a + 1) * DIGIT_PRIMES); ++i) {
+      c->grp[a].push_back(c->q[i]);
+      M = big_mul_u64(M, c->q[i]);
+    }
+    c->Qa[a] = M;
+  }
   return c;
 }
+
+int orc_num_digits(void* h) { return ((Ctx*)h)->D; }
 
 void orc_destroy(void* h) { delete (Ctx*)h; }
 
@@ -999,7 +1028,7 @@ int orc_decode(void* h, const uint64_t* m, uint32_t* slots) {
   return 0;
 }
 
-// secret key s (int8 [N]) and relinearisation key rk (uint64 [L][2][L+1][N],
+// secret key s (int8 [N]) and relinearisation key rk (uint64 [D][2][L+1][N],
 // residues mod q_0..q_{L-1}, P), both from `seed`.  The key is also kept in
 // the context for later multiplications.
 int orc_keygen(void* h, uint64_t seed, int8_t* s_out, uint64_t* rk_out) {
@@ -1315,7 +1344,7 @@ int orc_relin(void* h, const uint64_t* d3, uint64_t* out) {
 // ---------------------------------------------------------------------------
 
 // Galois key for element g (odd, < 2N) from the secret s: source tau_g(s).
-// gk_out (may be null): uint64 [L][2][L+1][N] residues mod q_0..q_{L-1}, P.
+// gk_out (may be null): uint64 [D][2][L+1][N] residues mod q_0..q_{L-1}, P.
 int orc_galois_keygen(void* h, uint64_t seed, const int8_t* s_in, uint64_t g, uint64_t* gk_out) {
   Ctx& c = *(Ctx*)h;
   if (g % 2 == 0 || g >= 2 * (uint64_t)c.N) return -1;

@@ -59,7 +59,7 @@ __global__ void k_secret_automorph(const int8_t* s, int8_t* out, uint32_t g, int
 __global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN, uint32_t dom, uint32_t obj_base) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)L * NKS * N) return;
+  if (gid >= (size_t)NDIG * NKS * N) return;
   int k = (int)(gid & (N - 1));
   size_t ij = gid >> logN;
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
@@ -69,13 +69,13 @@ __global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN
   rk[(((size_t)i * 2 + 1) * NKS + j) * N + k] = a;
 }
 
-// part 2: rk[i][0][j][k] = -(a s + e) + [i == j] [P]_{q_i} src  mod p_j, with
+// part 2: rk[i][0][j][k] = -(a s + e) + [q_j in digit i] [P]_{q_j} src  mod p_j, with
 // AS = a s and S2 = the source secret in coefficient domain (canonical).
 __global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2, uint64_t seed, int logN,
                             uint32_t dom, uint32_t obj_base) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)L * NKS * N) return;
+  if (gid >= (size_t)NDIG * NKS * N) return;
   int k = (int)(gid & (N - 1));
   size_t ij = gid >> logN;
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
@@ -84,9 +84,9 @@ __global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2
   int e = draw_cbd21(philox((uint32_t)k, 0u, obj_base | (uint32_t)i, dom, seed));
   uint64_t em = e < 0 ? p - (uint64_t)(-e) : (uint64_t)e;
   uint64_t v = sub_mod(0, add_mod(AS[gid], em, p), p);
-  if (j == i) {
+  if (j < L && j / DIGIT_PRIMES == i) {  // g_i = 1 mod the digit's primes, 0 mod the others and P
     uint64_t s2 = S2[(size_t)j * N + k];
-    uint64_t t = (uint64_t)(((unsigned __int128)s2 * cK.Pmodq[i]) % p);
+    uint64_t t = (uint64_t)(((unsigned __int128)s2 * cK.Pmodq[j]) % p);
     v = add_mod(v, t, p);
   }
   rk[(((size_t)i * 2 + 0) * NKS + j) * N + k] = v;

@@ -18,6 +18,9 @@ constexpr int ID_P = L + K;        // 31
 constexpr int ID_T = L + K + 1;    // 32
 constexpr int NPRIME = L + K + 2;  // 33
 constexpr int NKS = L + 1;         // key-switching targets: q_0..q_{L-1}, P
+constexpr int DIGIT_PRIMES = 3;    // data primes per key-switching digit
+constexpr int NDIG = L / DIGIT_PRIMES;  // digits: digit a = [d]_{q_3a q_3a+1 q_3a+2}
+static_assert(L % DIGIT_PRIMES == 0, "digits are whole groups of data primes");
 constexpr int LOGN_MIN = 12, LOGN_MAX = 15;
 
 // Constants for the exact RNS base conversions, relinearisation and the
@@ -57,6 +60,14 @@ struct Consts {
   uint64_t negQt;                         // [-Q 2^64]_t
   uint64_t Qinv_t;                        // [Q^{-1}]_t
   uint64_t Pmodq[L];                      // [P]_{q_i}   (key generation)
+  // key-switching digits in mixed radix: digit a = r0 + q_3a t1 + q_3a q_3a+1 t2
+  // with r0 = [d]_{q_3a}, t1 = (r1 - r0) q_3a^{-1} mod q_3a+1,
+  // t2 = ((r2 - r0) q_3a^{-1} - t1) q_3a+1^{-1} mod q_3a+2 (Garner)
+  uint64_t g01[NDIG], g01_s[NDIG];  // [q_3a^{-1}]_{q_3a+1}
+  uint64_t g02[NDIG], g02_s[NDIG];  // [q_3a^{-1}]_{q_3a+2}
+  uint64_t g12[NDIG], g12_s[NDIG];  // [q_3a+1^{-1}]_{q_3a+2}
+  uint64_t dig1[NDIG][NKS], dig1_s[NDIG][NKS];  // [q_3a]_{p_j}
+  uint64_t dig2[NDIG][NKS], dig2_s[NDIG][NKS];  // [q_3a q_3a+1]_{p_j}
 };
 
 // Host side: build the constant block for (q, P, t) with the auxiliary primes

@@ -213,6 +213,22 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->tqhatinv_s[i] = h_shoup(C->tqhatinv[i], q[i]);
     C->MQt[i] = to_mont(prod_mod(q, L, i, t), t);
   }
+  for (int a = 0; a < NDIG; ++a) {
+    const uint64_t q0 = q[3 * a], q1 = q[3 * a + 1], q2 = q[3 * a + 2];
+    C->g01[a] = h_invmod(q0 % q1, q1);
+    C->g01_s[a] = h_shoup(C->g01[a], q1);
+    C->g02[a] = h_invmod(q0 % q2, q2);
+    C->g02_s[a] = h_shoup(C->g02[a], q2);
+    C->g12[a] = h_invmod(q1 % q2, q2);
+    C->g12_s[a] = h_shoup(C->g12[a], q2);
+    for (int j = 0; j < NKS; ++j) {
+      const uint64_t pj = j < L ? q[j] : P;
+      C->dig1[a][j] = q0 % pj;
+      C->dig1_s[a][j] = h_shoup(C->dig1[a][j], pj);
+      C->dig2[a][j] = h_mulmod(q0 % pj, q1 % pj, pj);
+      C->dig2_s[a][j] = h_shoup(C->dig2[a][j], pj);
+    }
+  }
   C->negQt = to_mont((t - Qt) % t, t);
   // 28-bit limb splits of the conversion matrices (device multiply-accumulate)
   const uint64_t M28 = (1ULL << 28) - 1;
@@ -270,7 +286,6 @@ int lt_coefficients(uint32_t* out) {
 }
 
 int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {
-  (void)P;
   double lq = 0;
   for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
   double lt = log2((double)t);
@@ -279,7 +294,19 @@ int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t
   double fresh = lq - lt - log_n - 8.0;
   double per = lt + log_n + 2.0;
   if (fresh <= 0) return 0;
-  return (int)floor((fresh - 1.0) / per);
+  // key switching adds |digit| sqrt(N) 2^4 / P at every level; it bounds the
+  // budget left after the first squaring (digits: groups of DIGIT_PRIMES primes)
+  double dbits = 0;
+  for (int a = 0; a * DIGIT_PRIMES < nq; ++a) {
+    double g = 0;
+    for (int i = a * DIGIT_PRIMES; i < nq && i < (a + 1) * DIGIT_PRIMES; ++i) g += log2((double)q[i]);
+    dbits = dbits > g ? dbits : g;
+  }
+  double b1 = fresh - per;
+  const double ks = (lq - lt) - (dbits + 0.5 * log_n + 4.0 - log2((double)P));
+  if (ks < b1) b1 = ks;
+  if (b1 <= 1.0) return 0;
+  return 1 + (int)floor((b1 - 1.0) / per);
 }
 
 }  // namespace hp

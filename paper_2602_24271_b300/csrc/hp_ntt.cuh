@@ -51,9 +51,10 @@ struct NttTabs {
 };
 enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, NSCALE = 3 };
 
-// Optional fused load of the forward column pass: polynomial (b, i, j) of the
-// key-switching batch is digit i of ciphertext b reduced modulo target prime
-// j, read from w3[b][2][i][.] (the digits [d2]_{q_i}).
+// Optional fused load of the forward column pass: polynomial (b, g, j) of the
+// key-switching batch is digit g of ciphertext b reduced modulo target prime
+// j.  The digit is stored in mixed radix as (r0, t1, t2) in w3[b][2][3g .. 3g+2]
+// and recombined as r0 + [q_3g]_{p_j} t1 + [q_3g q_3g+1]_{p_j} t2 mod p_j.
 struct DigitSrc {
   const uint64_t* w3;  // nullptr: the pass transforms `data` in place
 };
@@ -150,18 +151,22 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restri
   const uint64_t p = f.p;
   const ulonglong2* tw = T.tw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
-  const uint64_t* src = a;
-  bool reduce = false;
-  if (dig.w3) {  // key-switching digits: poly = (b * L + i) * NKS + j
-    const int b = poly / (L * NKS), i = (poly / NKS) % L;
-    src = dig.w3 + ((size_t)(b * 3 + 2) * L + i) * N;
-    reduce = true;
-  }
   uint64_t x[16];
+  if (dig.w3) {  // key-switching digits: poly = (b * NDIG + g) * NKS + j
+    const int b = poly / (NDIG * NKS), g = (poly / NKS) % NDIG, j = poly % NKS;
+    const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g * DIGIT_PRIMES) * N;
+    const uint64_t c1 = cK.dig1[g][j], c1s = cK.dig1_s[g][j], c2 = cK.dig2[g][j], c2s = cK.dig2_s[g][j];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    uint64_t v = src[(size_t)(rb + u * RB) * C + k0 + k];
-    x[u] = reduce ? csub(v, p) : v;  // digit < q_i < 2 p_j
+    for (int u = 0; u < 16; ++u) {
+      const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
+      // r0 < 2p (primes within a factor 2) and two products in [0, 4p): sum < 10p
+      uint64_t v = src[off] + mul_shoup4(src[N + off], c1, c1s, f) + mul_shoup4(src[2 * N + off], c2, c2s, f);
+      v = csub(csub(v, 8 * p), 4 * p);
+      x[u] = csub(csub(v, 2 * p), p);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = a[(size_t)(rb + u * RB) * C + k0 + k];
   }
   fwd_block<4>(x, (uint32_t)(rb * C + k0 + k), 0, logN, tw, f);
 #pragma unroll
@@ -237,7 +242,6 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restri
   const int poly = blockIdx.y, row0 = blockIdx.x * ROWS, row = row0 + r;
   const int id = map.id(poly);
   const PForm f = pform(id);
-  const uint64_t p = f.p;
   const ulonglong2* itw = T.itw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
   for (int e = t; e < NTT_TILE; e += NTT_THREADS) {

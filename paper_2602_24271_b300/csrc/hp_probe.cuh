@@ -12,7 +12,6 @@ constexpr int PROBE_CHAINS = 8;
 __global__ void __launch_bounds__(256) k_probe_butterfly(uint64_t* sink, int iters, uint64_t p, uint64_t w,
                                                          uint64_t wp) {
   uint64_t X[PROBE_CHAINS], Y[PROBE_CHAINS];
-  const uint64_t p2 = 2 * p;
 #pragma unroll
   for (int c = 0; c < PROBE_CHAINS; ++c) {
     X[c] = (threadIdx.x * 7919u + c * 104729u + blockIdx.x) % p;

@@ -114,6 +114,20 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_gen(const uint64_t* __res
   dprod[((b * 3 + 2) * NQB + pi) * N + n] = mont_mul_lazy(a1, b1, p, pinv);
 }
 
+// Key-switching digit g of a coefficient from its residues r = (r0, r1, r2) mod
+// the group's primes (q0, q1, q2) = (q_3g, q_3g+1, q_3g+2): the digit [d]_{q0 q1 q2}
+// = r0 + q0 t1 + q0 q1 t2 is kept as its mixed-radix form (r0, t1, t2) with
+// t1 = (r1 - r0) q0^{-1} mod q1 and t2 = ((r2 - r0) q0^{-1} - t1) q1^{-1} mod q2
+// (Garner).  Data primes lie within a factor 2 of each other, so one conditional
+// subtraction reduces a residue of one prime modulo another.
+HPD void digit_mixed_radix(uint64_t (&r)[DIGIT_PRIMES], int g) {
+  const uint64_t q1 = cK.p[DIGIT_PRIMES * g + 1], q2 = cK.p[DIGIT_PRIMES * g + 2];
+  const uint64_t t1 = mul_shoup(sub_mod(r[1], csub(r[0], q1), q1), cK.g01[g], cK.g01_s[g], q1);
+  const uint64_t u = mul_shoup(sub_mod(r[2], csub(r[0], q2), q2), cK.g02[g], cK.g02_s[g], q2);
+  r[2] = mul_shoup(sub_mod(u, csub(t1, q2), q2), cK.g12[g], cK.g12_s[g], q2);
+  r[1] = t1;
+}
+
 // One thread per (b, j in {0,1,2}, n).  dprod holds t d (coefficient domain,
 // canonical) in Q u B.  Writes w = round(t d / Q) mod q_i to w3[b][j][i][n].
 //
@@ -164,24 +178,33 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
   uint32_t bl[K], bh[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) bl[k] = lo28(yb[k]), bh[k] = hi28(yb[k]);
+  const bool digits = (bj % 3) == 2;  // d2 is stored as key-switching digits (uniform per warp)
 #pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const uint64_t p = cK.p[i];
-    Acc3 a;
-    acc3_zero(a);
+  for (int g = 0; g < NDIG; ++g) {
+    uint64_t r[DIGIT_PRIMES];
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc3_mac(a, bl[k], bh[k], cK.MBQ_l[k][i], cK.MBQ_h[k][i]);
-    acc3_mac(a, (uint32_t)vb, 0, cK.negBQ_l[i], cK.negBQ_h[i]);
-    o[(size_t)i * N] = redc(acc3_fold(a), p, cK.pinv[i]);
+    for (int e = 0; e < DIGIT_PRIMES; ++e) {
+      const int i = g * DIGIT_PRIMES + e;
+      const uint64_t p = cK.p[i];
+      Acc3 a;
+      acc3_zero(a);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc3_mac(a, bl[k], bh[k], cK.MBQ_l[k][i], cK.MBQ_h[k][i]);
+      acc3_mac(a, (uint32_t)vb, 0, cK.negBQ_l[i], cK.negBQ_h[i]);
+      r[e] = redc(acc3_fold(a), p, cK.pinv[i]);
+    }
+    if (digits) digit_mixed_radix(r, g);
+#pragma unroll
+    for (int e = 0; e < DIGIT_PRIMES; ++e) o[(size_t)(g * DIGIT_PRIMES + e) * N] = r[e];
   }
 }
 
 HPD int ks_id(int j) { return j < L ? j : ID_P; }
 
 // One thread per (target j, n), looping over the tile's ciphertexts so that
-// each key word is read once per launch.  rk: [L][2][NKS][N], NTT domain,
-// Montgomery form (canonical); digits in [0, 8p): sums < 15 8 p^2 < p 2^64.
-// ksout: [nct][2][NKS][N] in [0, 2p).
+// each key word is read once per launch.  rk: [NDIG][2][NKS][N], NTT domain,
+// Montgomery form (canonical); digits in [0, 8p): sums < 5 8 p^2 < p 2^64.
+// ksin: [nct][NDIG][NKS][N]; ksout: [nct][2][NKS][N] in [0, 2p).
 __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restrict__ ksin, const uint64_t* __restrict__ rk,
                                                        uint64_t* __restrict__ ksout, int logN, int nct) {
   const int N = 1 << logN;
@@ -191,9 +214,9 @@ __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restric
   const int j = (int)(gid >> logN);
   const int id = ks_id(j);
   const uint64_t p = cK.p[id], pinv = cK.pinv[id];
-  uint64_t k0[L], k1[L];
+  uint64_t k0[NDIG], k1[NDIG];
 #pragma unroll
-  for (int i = 0; i < L; ++i) {
+  for (int i = 0; i < NDIG; ++i) {
     k0[i] = rk[((size_t)(i * 2 + 0) * NKS + j) * N + n];
     k1[i] = rk[((size_t)(i * 2 + 1) * NKS + j) * N + n];
   }
@@ -202,8 +225,8 @@ __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restric
     acc_zero(a0);
     acc_zero(a1);
 #pragma unroll
-    for (int i = 0; i < L; ++i) {
-      const uint64_t d = ksin[(((size_t)b * L + i) * NKS + j) * N + n];
+    for (int i = 0; i < NDIG; ++i) {
+      const uint64_t d = ksin[(((size_t)b * NDIG + i) * NKS + j) * N + n];
       acc_mac(a0, d, k0[i]);
       acc_mac(a1, d, k1[i]);
     }
@@ -326,33 +349,42 @@ __global__ void k_ct_group_sum(const uint64_t* x, size_t n_ct, size_t group, uin
 
 // Galois automorphism tau_g (rotation of the slots), gathered per output
 // coefficient: tau_g(a)_n = a_j with j = n g^{-1} mod 2N when j < N, else
-// -a_{j - N}.  One thread per (b, i, n); writes the key-switching input
+// -a_{j - N}.  One thread per (b, digit g, n), covering the digit's primes;
+// writes the key-switching input
 //   w3[b][0] = (acc ? c0 : 0) + tau_g(c0),  w3[b][1] = acc ? c1 : 0,
-//   w3[b][2] = tau_g(c1)   (switched from tau_g(s) to s by the Galois key),
+//   w3[b][2] = tau_g(c1) as key-switching digits (switched from tau_g(s) to s),
 // so the mod-down that follows yields ct + rotate(ct) (acc) or rotate(ct).
 __global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict__ w3, uint32_t ginv, int acc,
                             int logN, int nct) {
   const int N = 1 << logN;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)nct * L * N) return;
+  if (gid >= (size_t)nct * NDIG * N) return;
   const int n = (int)(gid & (N - 1));
-  const size_t bi = gid >> logN;
-  const int i = (int)(bi % L);
-  const size_t b = bi / L;
-  const uint64_t q = cK.p[i];
+  const size_t bg = gid >> logN;
+  const int g = (int)(bg % NDIG);
+  const size_t b = bg / NDIG;
   const uint32_t j = (uint32_t)(((uint64_t)n * ginv) & (2 * (uint64_t)N - 1));
   const uint32_t src = j < (uint32_t)N ? j : j - N;
-  const uint64_t* x0 = x + ((b * 2 + 0) * L + i) * N;
-  const uint64_t* x1 = x + ((b * 2 + 1) * L + i) * N;
-  uint64_t t0 = x0[src], t1 = x1[src];
-  if (j >= (uint32_t)N) {
-    t0 = sub_mod(0, t0, q);
-    t1 = sub_mod(0, t1, q);
+  uint64_t r[DIGIT_PRIMES];
+#pragma unroll
+  for (int e = 0; e < DIGIT_PRIMES; ++e) {
+    const int i = g * DIGIT_PRIMES + e;
+    const uint64_t q = cK.p[i];
+    const uint64_t* x0 = x + ((b * 2 + 0) * L + i) * N;
+    const uint64_t* x1 = x + ((b * 2 + 1) * L + i) * N;
+    uint64_t t0 = x0[src], t1 = x1[src];
+    if (j >= (uint32_t)N) {
+      t0 = sub_mod(0, t0, q);
+      t1 = sub_mod(0, t1, q);
+    }
+    uint64_t* o = w3 + (b * 3 * L + i) * N + n;
+    o[0] = acc ? add_mod(x0[n], t0, q) : t0;
+    o[(size_t)L * N] = acc ? x1[n] : 0;
+    r[e] = t1;
   }
-  uint64_t* o = w3 + (b * 3 * L + i) * N + n;
-  o[0] = acc ? add_mod(x0[n], t0, q) : t0;
-  o[(size_t)L * N] = acc ? x1[n] : 0;
-  o[(size_t)2 * L * N] = t1;
+  digit_mixed_radix(r, g);
+#pragma unroll
+  for (int e = 0; e < DIGIT_PRIMES; ++e) w3[((b * 3 + 2) * L + g * DIGIT_PRIMES + e) * N + n] = r[e];
 }
 
 // ---- Extract (JOIN, Sec. 4.2.2): product with a plaintext unit vector --------------

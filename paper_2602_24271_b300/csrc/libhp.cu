@@ -31,7 +31,7 @@ struct hp_handle {
   // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][2]
   ulonglong2 *tw = nullptr, *itw = nullptr;  // (value, Shoup) pairs
   uint64_t* scale = nullptr;
-  // relinearisation key, NTT domain, Montgomery form: [L][2][NKS][N]
+  // relinearisation key, NTT domain, Montgomery form: [NDIG][2][NKS][N]
   uint64_t* rkm = nullptr;
   bool have_rk = false;
   // workspace for one pipeline tile of `tile` ciphertexts
@@ -147,7 +147,7 @@ static size_t ws_words_per_ct(int N) {
                       + 2 * NQB    // ext2 (SELECT operand)
                       + 3 * NQB    // dprod
                       + 3 * L      // w3
-                      + L * NKS    // ksin
+                      + NDIG * NKS    // ksin
                       + 2 * NKS    // ksout
                       + 2 * L      // ctbuf
                       + 2 * L      // maskbuf
@@ -249,9 +249,9 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
   h->launches += 1;
   // key switching: digits [d2]_{q_i} mod p_j (reduction fused into the first
   // transform pass), key multiply-accumulate, inverse transform, mod-down
-  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s, h->w3);
+  ntt_fwd(h, h->ksin, (size_t)b * NDIG * NKS, MAP_KS, s, h->w3);
   {
-    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * L * NKS * N);
+    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * NDIG * NKS * N);
     k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
   }
   h->launches += 1;
@@ -549,11 +549,11 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
     uint64_t** p;
     size_t words;
   } allocs[] = {{&h->ext, T * 2 * NQB * N},  {&h->ext2, T * 2 * NQB * N}, {&h->dprod, T * 3 * NQB * N},
-                {&h->w3, T * 3 * L * N},     {&h->ksin, T * L * NKS * N}, {&h->ksout, T * 2 * NKS * N},
+                {&h->w3, T * 3 * L * N},     {&h->ksin, T * NDIG * NKS * N}, {&h->ksout, T * 2 * NKS * N},
                 {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
                 {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
                 {&h->stx2, T * 2 * L * N},   {&h->sty2, T * 2 * L * N},   {&h->sto2, T * 2 * L * N},
-                {&h->rkm, (size_t)L * 2 * NKS * N}};
+                {&h->rkm, (size_t)NDIG * 2 * NKS * N}};
   for (auto& a : allocs) {
     if (cudaMalloc(a.p, a.words * sizeof(uint64_t)) != cudaSuccess) {
       h->err = "device allocation failed for the workspace";
@@ -579,10 +579,10 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
 int hp_set_relin_key(hp_handle* h, const uint64_t* rk) {
   if (!h) return HP_ERR_ARG;
   if (!rk) HP_FAIL(h, HP_ERR_ARG, "null relinearisation key");
-  const size_t words = (size_t)L * 2 * NKS * h->N;
+  const size_t words = (size_t)NDIG * 2 * NKS * h->N;
   CU(h, cudaMemcpy(h->rkm, rk, words * sizeof(uint64_t), cudaMemcpyDeviceToDevice));
-  ntt_fwd(h, h->rkm, (size_t)L * 2 * NKS, MAP_KS, 0);
-  k_to_mont<<<ew_blocks(words), EW_THREADS>>>(h->rkm, NKS, 0, ID_P, (size_t)L * 2 * NKS, h->logn);
+  ntt_fwd(h, h->rkm, (size_t)NDIG * 2 * NKS, MAP_KS, 0);
+  k_to_mont<<<ew_blocks(words), EW_THREADS>>>(h->rkm, NKS, 0, ID_P, (size_t)NDIG * 2 * NKS, h->logn);
   CU(h, cudaGetLastError());
   CU(h, cudaDeviceSynchronize());
   h->have_rk = true;
@@ -952,14 +952,14 @@ int hp_galois_elements(int logn, uint64_t* g_out) {
   return HP_OK;
 }
 
-static size_t key_words(const hp_handle* h) { return (size_t)L * 2 * NKS * h->N; }
+static size_t key_words(const hp_handle* h) { return (size_t)NDIG * 2 * NKS * h->N; }
 
 static int install_galois_key(hp_handle* h, int st, const uint64_t* gk, cudaStream_t s) {
   const size_t kw = key_words(h);
   uint64_t* dst = h->gkm + (size_t)st * kw;
   CU(h, cudaMemcpyAsync(dst, gk, kw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-  ntt_fwd(h, dst, (size_t)L * 2 * NKS, MAP_KS, s);
-  k_to_mont<<<ew_blocks(kw), EW_THREADS, 0, s>>>(dst, NKS, 0, ID_P, (size_t)L * 2 * NKS, h->logn);
+  ntt_fwd(h, dst, (size_t)NDIG * 2 * NKS, MAP_KS, s);
+  k_to_mont<<<ew_blocks(kw), EW_THREADS, 0, s>>>(dst, NKS, 0, ID_P, (size_t)NDIG * 2 * NKS, h->logn);
   CU(h, cudaGetLastError());
   return HP_OK;
 }
@@ -995,7 +995,7 @@ int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk
   int8_t* ts = nullptr;
   CU(h, cudaMalloc(&S, (size_t)NKS * N * 8));
   CU(h, cudaMalloc(&S2, (size_t)NKS * N * 8));
-  CU(h, cudaMalloc(&A, (size_t)L * NKS * N * 8));
+  CU(h, cudaMalloc(&A, (size_t)NDIG * NKS * N * 8));
   CU(h, cudaMalloc(&ts, N));
   if (!gk) CU(h, cudaMalloc(&K, kw * 8));
   k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(sk, S, NKS, 0, ID_P, N);
@@ -1005,12 +1005,12 @@ int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk
     const uint32_t obj = (uint32_t)(g[st] << 5);
     k_secret_automorph<<<ew_blocks(N), EW_THREADS, 0, s>>>(sk, ts, (uint32_t)g[st], logN);
     k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(ts, S2, NKS, 0, ID_P, N);
-    k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(key, A, seed, logN, DOM_A_GK, obj);
-    ntt_fwd(h, A, (size_t)L * NKS, MAP_KS, s);
-    k_pointwise_mont<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P,
-                                                                          (size_t)L * NKS, logN);
-    ntt_inv(h, A, (size_t)L * NKS, MAP_KS, SCALE_NINV_R, s);
-    k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(key, A, S2, seed, logN, DOM_E_GK, obj);
+    k_rk_sample_a<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(key, A, seed, logN, DOM_A_GK, obj);
+    ntt_fwd(h, A, (size_t)NDIG * NKS, MAP_KS, s);
+    k_pointwise_mont<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P,
+                                                                          (size_t)NDIG * NKS, logN);
+    ntt_inv(h, A, (size_t)NDIG * NKS, MAP_KS, SCALE_NINV_R, s);
+    k_rk_finish<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(key, A, S2, seed, logN, DOM_E_GK, obj);
     if (int rc = install_galois_key(h, st, key, s)) return rc;
   }
   CU(h, cudaGetLastError());
@@ -1029,12 +1029,12 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
   const int N = h->N, logN = h->logn;
   {
     ProfScope ps(h, PK_AUTOMORPH, s, 3.0 * b * L * N);
-    k_automorph<<<ew_blocks((size_t)b * L * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+    k_automorph<<<ew_blocks((size_t)b * NDIG * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
   }
   h->launches += 1;
-  ntt_fwd(h, h->ksin, (size_t)b * L * NKS, MAP_KS, s, h->w3);
+  ntt_fwd(h, h->ksin, (size_t)b * NDIG * NKS, MAP_KS, s, h->w3);
   {
-    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * L * NKS * N);
+    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * NDIG * NKS * N);
     k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->gkm + (size_t)st * key_words(h), h->ksout,
                                                               logN, b);
   }
@@ -1266,18 +1266,18 @@ int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* strea
   uint64_t *S = nullptr, *S2 = nullptr, *A = nullptr;
   CU(h, cudaMalloc(&S, (size_t)NKS * N * 8));
   CU(h, cudaMalloc(&S2, (size_t)NKS * N * 8));
-  CU(h, cudaMalloc(&A, (size_t)L * NKS * N * 8));
+  CU(h, cudaMalloc(&A, (size_t)NDIG * NKS * N * 8));
   k_sample_secret<<<ew_blocks(N), EW_THREADS, 0, s>>>(sk, seed, N);
   k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(sk, S, NKS, 0, ID_P, N);
   ntt_fwd(h, S, NKS, MAP_KS, s);
   k_pointwise_mont<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(S, S, S2, NKS, NKS, 0, ID_P, NKS, logN);
   ntt_inv(h, S2, NKS, MAP_KS, SCALE_NINV_R, s);
-  k_rk_sample_a<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, seed, logN, DOM_A_RK, 0);
-  ntt_fwd(h, A, (size_t)L * NKS, MAP_KS, s);
-  k_pointwise_mont<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P, (size_t)L * NKS,
+  k_rk_sample_a<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(rk, A, seed, logN, DOM_A_RK, 0);
+  ntt_fwd(h, A, (size_t)NDIG * NKS, MAP_KS, s);
+  k_pointwise_mont<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P, (size_t)NDIG * NKS,
                                                                         logN);
-  ntt_inv(h, A, (size_t)L * NKS, MAP_KS, SCALE_NINV_R, s);
-  k_rk_finish<<<ew_blocks((size_t)L * NKS * N), EW_THREADS, 0, s>>>(rk, A, S2, seed, logN, DOM_E_RK, 0);
+  ntt_inv(h, A, (size_t)NDIG * NKS, MAP_KS, SCALE_NINV_R, s);
+  k_rk_finish<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(rk, A, S2, seed, logN, DOM_E_RK, 0);
   CU(h, cudaGetLastError());
   CU(h, cudaStreamSynchronize(s));
   cudaFree(S);
@@ -1423,8 +1423,8 @@ int hp_probe_peak(int kind, double* per_second) {
 // fixed-size array that lives in the library's own device memory image.
 // ---------------------------------------------------------------------------
 constexpr int NOALLOC_MAX_LOGN = 12;  // ring degree up to 4096
-constexpr size_t NOALLOC_WORDS_PER_COEFF = 2 * NQB + 3 * NQB + 3 * L + L * NKS + 2 * NKS;  // 472
-constexpr size_t NOALLOC_WORDS = NOALLOC_WORDS_PER_COEFF << NOALLOC_MAX_LOGN;            // 15.5 MB
+constexpr size_t NOALLOC_WORDS_PER_COEFF = 2 * NQB + 3 * NQB + 3 * L + NDIG * NKS + 2 * NKS;  // 312
+constexpr size_t NOALLOC_WORDS = NOALLOC_WORDS_PER_COEFF << NOALLOC_MAX_LOGN;               // 10.2 MB
 static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
 static uint64_t* g_noalloc_addr[64];  // device address of the array, per device (set up on first use)
 
@@ -1461,14 +1461,14 @@ int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, voi
   uint64_t* dprod = ext + (size_t)2 * NQB * N;
   uint64_t* w3 = dprod + (size_t)3 * NQB * N;
   uint64_t* ksin = w3 + (size_t)3 * L * N;
-  uint64_t* ksout = ksin + (size_t)L * NKS * N;
+  uint64_t* ksout = ksin + (size_t)NDIG * NKS * N;
   // every scratch word read below is written earlier in this call: nothing needs clearing
   k_lift<<<ew_blocks((size_t)2 * N), EW_THREADS, 0, s>>>(ct_in, nullptr, 0, LIFT_COPY, ext, logN, 1);
   ntt_fwd(h, ext, 2 * NQB, MAP_QB, s);
   k_tensor_sq<<<ew_blocks((size_t)NQB * N), EW_THREADS, 0, s>>>(ext, dprod, logN, 1);
   ntt_inv(h, dprod, 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
   k_scale_round<<<ew_blocks((size_t)3 * N), EW_THREADS, 0, s>>>(dprod, w3, h->status, logN, 1);
-  ntt_fwd(h, ksin, (size_t)L * NKS, MAP_KS, s, w3);
+  ntt_fwd(h, ksin, (size_t)NDIG * NKS, MAP_KS, s, w3);
   k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(ksin, h->rkm, ksout, logN, 1);
   ntt_inv(h, ksout, 2 * NKS, MAP_KS, SCALE_NINV, s);
   k_moddown<<<ew_blocks((size_t)2 * L * N), EW_THREADS, 0, s>>>(ksout, w3, ct_out, 0, logN, 1);

@@ -52,6 +52,9 @@ KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows", "k_ntt_inv_rows", "k_ntt_
                    "k_scale_round", "k_automorph", "k_ks_mac", "k_moddown"]
 
 
+DIGIT_PRIMES = 3  # data primes per key-switching digit (D = L / 3 digits)
+
+
 class HpError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("%s (%d): %s" % (_NAMES.get(code, "HP_ERR"), code, msg))
@@ -176,6 +179,7 @@ class Context:
         if q is None:
             q, P, t = default_params()
         self.log_n, self.N, self.L = log_n, 1 << log_n, len(q)
+        self.D = self.L // DIGIT_PRIMES  # key-switching digits
         self.q, self.P, self.t = list(q), int(P), int(t)
         self._q = (ctypes.c_uint64 * len(q))(*q)
         prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth)
@@ -204,7 +208,7 @@ class Context:
     def keygen(self, seed: int, stream=None):
         torch = self.torch
         sk = torch.empty(self.N, dtype=torch.int8, device="cuda")
-        rk = torch.empty((self.L, 2, self.L + 1, self.N), dtype=torch.int64, device="cuda")
+        rk = torch.empty((self.D, 2, self.L + 1, self.N), dtype=torch.int64, device="cuda")
         _check(self.lib.hp_keygen(self.h, seed, _ptr(sk), _ptr(rk), _stream(stream)), self.h)
         self.sk = sk
         return sk, rk
@@ -273,7 +277,7 @@ class Context:
         """Galois keys of the rotate-and-add reduction (installed); returned as
         [logN, L, 2, L+1, N] when `keep`."""
         sk = self.sk if sk is None else sk
-        gk = self.torch.empty((self.log_n, self.L, 2, self.L + 1, self.N), dtype=self.torch.int64,
+        gk = self.torch.empty((self.log_n, self.D, 2, self.L + 1, self.N), dtype=self.torch.int64,
                               device="cuda") if keep else None
         _check(self.lib.hp_galois_keygen(self.h, seed, _ptr(sk), _ptr(gk), _stream(stream)), self.h)
         return gk

@@ -97,11 +97,18 @@ def test_static_depth_estimate_is_conservative_against_oracle():
 
 def lib_depth(logn, q, P):
     # mirror of the C estimate (hp_host.cpp supported_depth): fresh budget
-    # log2 Q - log2 t - log N - 8, per squaring log2 t + log N + 2
+    # log2 Q - log2 t - log N - 8, per squaring log2 t + log N + 2; the budget
+    # after the first squaring is also bounded by the key-switching noise
+    # |digit| sqrt(N) 2^4 / P (digits: groups of 3 data primes)
     lq = sum(math.log2(x) for x in q)
     lt = math.log2(65537)
     fresh = lq - lt - logn - 8
-    return int((fresh - 1) // (lt + logn + 2)) if fresh > 0 else 0
+    per = lt + logn + 2
+    if fresh <= 0:
+        return 0
+    dbits = max(sum(math.log2(x) for x in q[a:a + 3]) for a in range(0, len(q), 3))
+    b1 = min(fresh - per, (lq - lt) - (dbits + 0.5 * logn + 4 - math.log2(P)))
+    return 1 + int((b1 - 1) // per) if b1 > 1 else 0
 
 
 def test_lt_coefficients_match_oracle(lib):
