@@ -322,6 +322,15 @@ int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, voi
 int hp_profile(hp_handle* h, uint32_t class_mask);
 int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches, double* work_total);
 
+/* Tensor-core probe (no counterpart in the paper): one CTA computes
+ * D = A B^T with tcgen05.mma kind::f16 (accumulator in tensor memory) for
+ * A [128][112] and B [n][112] f16 matrices (host memory, row-major f16 bits),
+ * D [128][n] f32 (host), n a multiple of 16 in [16, 256].  Used by the tests to
+ * check the operand layout and that sums of products of 8-bit integers are
+ * exact.  Synchronous; HP_ERR_TIMEOUT if the MMA did not complete within the
+ * kernel's bounded wait. */
+int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n);
+
 /* Register-only peak probe on the current device (no handle needed):
  * kind 0 = the 64-bit Shoup butterfly of the NTT kernels (butterflies/s),
  * kind 1 = the 64x64->128-bit multiply-accumulate of the base conversions and

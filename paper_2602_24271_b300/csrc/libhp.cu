@@ -16,6 +16,7 @@
 #include "hp_ntt.cuh"
 #include "hp_probe.cuh"
 #include "hp_rns.cuh"
+#include "hp_tc.cuh"
 
 using namespace hp;
 
@@ -1372,6 +1373,35 @@ int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches,
   *launches = n;
   *work_total = work;
   return HP_OK;
+}
+
+int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n) {
+  if (!A || !B || !D || n < 16 || n > 256 || n % 16) return HP_ERR_ARG;
+  hp_handle* h = nullptr;
+  uint16_t *dA = nullptr, *dB = nullptr;
+  float* dD = nullptr;
+  int* dst = nullptr;
+  CU(h, cudaMalloc(&dA, (size_t)TCP_M * TCP_K * 2));
+  CU(h, cudaMalloc(&dB, (size_t)256 * TCP_K * 2));
+  CU(h, cudaMalloc(&dD, (size_t)TCP_M * n * 4));
+  CU(h, cudaMalloc(&dst, sizeof(int)));
+  CU(h, cudaMemset(dB, 0, (size_t)256 * TCP_K * 2));
+  CU(h, cudaMemset(dst, 0, sizeof(int)));
+  CU(h, cudaMemcpy(dA, A, (size_t)TCP_M * TCP_K * 2, cudaMemcpyHostToDevice));
+  CU(h, cudaMemcpy(dB, B, (size_t)n * TCP_K * 2, cudaMemcpyHostToDevice));
+  const int smem = (TCP_M + 256) * TCP_K * 2 + 16;
+  CU(h, cudaFuncSetAttribute(k_tc_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k_tc_probe<<<1, 128, smem>>>(dA, dB, dD, n, dst);
+  CU(h, cudaGetLastError());
+  CU(h, cudaDeviceSynchronize());
+  int st = 0;
+  CU(h, cudaMemcpy(&st, dst, sizeof(int), cudaMemcpyDeviceToHost));
+  CU(h, cudaMemcpy(D, dD, (size_t)TCP_M * n * 4, cudaMemcpyDeviceToHost));
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(dst);
+  return st ? HP_ERR_TIMEOUT : HP_OK;
 }
 
 int hp_probe_peak(int kind, double* per_second) {

@@ -43,7 +43,7 @@ EXPORTED = [
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
-    "hp_extract_broadcast", "hp_join", "hp_ct_sum",
+    "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -125,6 +125,7 @@ def load():
         "hp_set_galois_keys": (ctypes.c_int, [H, P64]),
         "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_ct_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
+        "hp_probe_tc_gemm": (ctypes.c_int, [V, V, V, ctypes.c_int]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }
@@ -345,6 +346,16 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
         _check(self.lib.hp_profile_read(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)), self.h)
         return ms.value, int(n.value), w.value
+
+
+def probe_tc_gemm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Tensor-core probe: A [128, 112] and B [n, 112] f16 -> A @ B.T as f32 [128, n]."""
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.float16)
+    B = np.ascontiguousarray(B, dtype=np.float16)
+    D = np.zeros((128, B.shape[0]), dtype=np.float32)
+    _check(lib.hp_probe_tc_gemm(A.ctypes.data, B.ctypes.data, D.ctypes.data, B.shape[0]))
+    return D
 
 
 def galois_elements(log_n: int):
