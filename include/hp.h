@@ -324,12 +324,13 @@ int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches,
 
 /* Tensor-core probe (no counterpart in the paper): one CTA computes
  * D = A B^T with tcgen05.mma kind::f16 (accumulator in tensor memory) for
- * A [128][112] and B [n][112] f16 matrices (host memory, row-major f16 bits),
+ * A [128][112] and B [n][112] matrices of f16 (bf16 = 0) or bf16 (bf16 = 1)
+ * values (host memory, row-major 16-bit patterns),
  * D [128][n] f32 (host), n a multiple of 16 in [16, 256].  Used by the tests to
  * check the operand layout and that sums of products of 8-bit integers are
  * exact.  Synchronous; HP_ERR_TIMEOUT if the MMA did not complete within the
  * kernel's bounded wait. */
-int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n);
+int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16);
 
 /* Register-only peak probe on the current device (no handle needed):
  * kind 0 = the 64-bit Shoup butterfly of the NTT kernels (butterflies/s),

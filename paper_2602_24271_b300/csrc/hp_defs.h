@@ -68,6 +68,7 @@ struct Consts {
   uint64_t g12[NDIG], g12_s[NDIG];  // [q_3a+1^{-1}]_{q_3a+2}
   uint64_t dig1[NDIG][NKS], dig1_s[NDIG][NKS];  // [q_3a]_{p_j}
   uint64_t dig2[NDIG][NKS], dig2_s[NDIG][NKS];  // [q_3a q_3a+1]_{p_j}
+  uint64_t r32b[K], r32b_s[K];                  // [2^32]_{b_k}
 };
 
 // Host side: build the constant block for (q, P, t) with the auxiliary primes
@@ -86,6 +87,17 @@ uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t m);
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);
 uint64_t h_invmod(uint64_t a, uint64_t m);
 uint64_t h_shoup(uint64_t w, uint64_t p);
+
+// Tables of the tensor-core base conversions (8-bit limbs, bf16 operands).
+//   B1 [128][112]: row 8k+b (k < K, b < 7), column 7i+a (i < L, a < 7):
+//                  limb b of [2^(8a) (Q/q_i)]_{b_k}; other entries 0.
+//   B2 [128][112]: row 8i+b (i < L, b < 7), column 7k+a (k < K, a < 7):
+//                  limb b of [2^(8a) (B/b_k)]_{q_i}; other entries 0.
+// Both as bf16 bit patterns in the no-swizzle K-major core-matrix layout.
+//   T1 [16][16]:   [-v Q]_{b_k} for v < 16 (k < K)
+//   T2 [17][16]:   [-v B]_{q_i} for v <= K (i < L; column 15 unused)
+constexpr int TC_ROWS = 128, TC_K = 112, TC_T1 = 16 * 16, TC_T2 = 17 * 16;
+void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, uint64_t* T2);
 
 // LT polynomial's odd coefficients (32768 words), see hp_host.cpp.
 int lt_coefficients(uint32_t* out);

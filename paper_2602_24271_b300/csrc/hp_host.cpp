@@ -213,6 +213,10 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->tqhatinv_s[i] = h_shoup(C->tqhatinv[i], q[i]);
     C->MQt[i] = to_mont(prod_mod(q, L, i, t), t);
   }
+  for (int k = 0; k < K; ++k) {
+    C->r32b[k] = (uint64_t)(((unsigned __int128)1 << 32) % b[k]);
+    C->r32b_s[k] = h_shoup(C->r32b[k], b[k]);
+  }
   for (int a = 0; a < NDIG; ++a) {
     const uint64_t q0 = q[3 * a], q1 = q[3 * a + 1], q2 = q[3 * a + 2];
     C->g01[a] = h_invmod(q0 % q1, q1);
@@ -283,6 +287,48 @@ int lt_coefficients(uint32_t* out) {
   }
   for (uint64_t m = 0; m < (p - 1) / 2; ++m) out[m] = (uint32_t)a[(p - 2 - 2 * m) % n];
   return 0;
+}
+
+// bf16 bit pattern of an integer below 256 (exact: at most 8 significant bits)
+static uint16_t bf16_of_byte(uint32_t v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return (uint16_t)(u >> 16);
+}
+static int tc_cm_host(int r, int k) { return ((r >> 3) * (TC_K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, uint64_t* T2) {
+  const uint64_t* q = C.p;
+  const uint64_t* b = C.p + L;
+  memset(B1, 0, sizeof(uint16_t) * TC_ROWS * TC_K);
+  memset(B2, 0, sizeof(uint16_t) * TC_ROWS * TC_K);
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < L; ++i) {
+      uint64_t c = prod_mod(q, L, i, b[k]);  // [Q/q_i]_{b_k}
+      for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, b[k]))
+        for (int l = 0; l < 7; ++l) B1[tc_cm_host(8 * k + l, 7 * i + a)] = bf16_of_byte((uint32_t)(c >> (8 * l)) & 255);
+    }
+  for (int i = 0; i < L; ++i)
+    for (int k = 0; k < K; ++k) {
+      uint64_t c = prod_mod(b, K, k, q[i]);  // [B/b_k]_{q_i}
+      for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, q[i]))
+        for (int l = 0; l < 7; ++l) B2[tc_cm_host(8 * i + l, 7 * k + a)] = bf16_of_byte((uint32_t)(c >> (8 * l)) & 255);
+    }
+  for (int v = 0; v < 16; ++v)
+    for (int k = 0; k < 16; ++k) {
+      const uint64_t Qb = prod_mod(q, L, -1, b[k]);
+      T1[v * 16 + k] = (b[k] - h_mulmod((uint64_t)v, Qb, b[k])) % b[k];
+    }
+  for (int v = 0; v < 17; ++v)
+    for (int i = 0; i < 16; ++i) {
+      if (i >= L) {
+        T2[v * 16 + i] = 0;
+        continue;
+      }
+      const uint64_t Bq = prod_mod(b, K, -1, q[i]);
+      T2[v * 16 + i] = (q[i] - h_mulmod((uint64_t)v, Bq, q[i])) % q[i];
+    }
 }
 
 int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {

@@ -13,7 +13,7 @@ namespace hp {
 constexpr int EW_THREADS = 256;
 
 // status bits written by kernels (never expected; checked by the host)
-enum { ST_BQ_WINDOW = 1 };
+enum { ST_BQ_WINDOW = 1, ST_TC_TIMEOUT = 2 };  // device status bits
 
 // Difference modes of the first lift (row a1).  LIFT_SUB_PT subtracts
 // (Delta m, 0) for a plaintext polynomial m per ciphertext (sub: [nct][N],

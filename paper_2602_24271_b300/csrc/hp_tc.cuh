@@ -23,11 +23,12 @@ HPD uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
          ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), f16 A
-// and B (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 in bits
-// 17-22, M >> 4 in bits 24-28.
-HPD constexpr uint32_t tc_idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), A and B
+// both f16 (bits 7-9, 10-12 = 0) or both bf16 (= 1), both K-major (bits 15, 16
+// = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+HPD constexpr uint32_t tc_idesc_f16(int M, int N, int bf16 = 0) {
+  return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 // TMEM allocation of `ncols` columns (a power of two >= 32) by one whole warp;
@@ -94,13 +95,14 @@ HPD void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memor
 // with `kdim` columns in the core-matrix layout above.
 HPD int tc_cm(int r, int k, int kdim) { return ((r >> 3) * (kdim >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
-// ---- probe: one CTA computes D = A B^T for f16 operands holding integers ----------
-// A: [128][112], B: [n][112] (row-major f16 bits), D: [128][n] f32; n a multiple
-// of 16 in [16, 256].  Checks the descriptor encodings and the exactness of the
-// f32 accumulation of limb products on the hardware.
+// ---- probe: one CTA computes D = A B^T for f16 or bf16 operands holding integers ----
+// A: [128][112], B: [n][112] (row-major 16-bit patterns), D: [128][n] f32; n a
+// multiple of 16 in [16, 256]; bf16 selects the operand type.  Checks the
+// descriptor encodings and the exactness of the f32 accumulation of limb
+// products on the hardware.
 constexpr int TCP_M = 128, TCP_K = 112;
 __global__ void __launch_bounds__(128) k_tc_probe(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B,
-                                                  float* __restrict__ D, int n, int* status) {
+                                                  float* __restrict__ D, int n, int bf16, int* status) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint16_t* As = (uint16_t*)tsm;
   uint16_t* Bs = As + TCP_M * TCP_K;
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(128) k_tc_probe(const uint16_t* __restrict__ A
   tc_fence_after();
   const uint32_t tbase = *tslot;
   if (t == 0) {
-    const uint32_t idesc = tc_idesc_f16(TCP_M, n);
+    const uint32_t idesc = tc_idesc_f16(TCP_M, n, bf16);
     for (int ks = 0; ks < TCP_K / 16; ++ks) {
       const uint64_t ad = tc_desc(smem_u32(As) + ks * 256, 128, (TCP_K / 8) * 128);
       const uint64_t bd = tc_desc(smem_u32(Bs) + ks * 256, 128, (TCP_K / 8) * 128);

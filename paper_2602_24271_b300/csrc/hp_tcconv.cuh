@@ -1,0 +1,219 @@
+// Exact scale-and-round with the base conversions on the tensor cores.
+//
+// The two RNS base conversions of round(t d / Q) (Q -> B for r = [t d]_Q and
+// B -> Q for w = (t d - r) / Q, see k_scale_round) are dense contractions of
+// every coefficient's residue vector with a fixed matrix: 15 x 16 and 16 x 15
+// products of 55-bit numbers.  Here each residue y is split into seven 8-bit
+// limbs y^(a) and the matrix entries are pre-multiplied by 2^(8a), so that
+//   sum_i y_i c_ik = sum_{i,a} y_i^(a) [2^(8a) c_ik]_{b_k}   (mod b_k)
+// and every [2^(8a) c_ik] is itself split into limbs.  One bf16 MMA
+// (tcgen05.mma, M = 128 coefficients, N = 128 = 16 primes x 8 limb columns,
+// K = 112 = 16 residues x 7 limbs) then gives, per coefficient and prime, the
+// seven limb sums D_l = sum y^(a) c^(l) < 112 * 255^2 < 2^23: exact in the f32
+// accumulator.  The value sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime
+// on the CUDA cores.  Everything else (the exact centring decisions, the
+// subtraction, the mixed-radix digits) is the same arithmetic as k_scale_round,
+// so the outputs are bit-identical.
+#pragma once
+#include "hp_rns.cuh"
+#include "hp_tc.cuh"
+
+namespace hp {
+
+constexpr int SRT_GROUPS = 4;                    // tiles of 128 coefficients in flight per CTA
+constexpr int SRT_THREADS = 128 * SRT_GROUPS;    // one thread per coefficient
+constexpr int SRT_OPER = TC_ROWS * TC_K;         // bf16 elements of one operand tile
+constexpr size_t SRT_SMEM = (size_t)(2 + SRT_GROUPS) * SRT_OPER * 2 + (TC_T1 + TC_T2) * 8 + SRT_GROUPS * 8 + 32;
+
+HPD void named_sync(int id, int count) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
+
+// 32 TMEM lanes x 8 consecutive 32-bit columns
+HPD void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// bf16 of byte `a` of the 32-bit word w (exact: 2^23 + byte in f32, minus 2^23)
+HPD uint32_t byte_as_f32bits(uint32_t w, int a) {
+  const float f = __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)a | 0x7540u)) - 8388608.0f;
+  return __float_as_uint(f);
+}
+
+// Row `m` of an operand tile: the 8-bit limbs of R residues (column 7 i + a is
+// limb a of y[i]), zero beyond 7 R, as bf16 in the core-matrix layout.
+template <int R>
+HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
+#pragma unroll
+  for (int kc = 0; kc < TC_K / 8; ++kc) {
+    uint32_t f[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = kc * 8 + e, i = c / 7, a = c % 7;
+      if (i < R) {
+        const uint32_t w = a < 4 ? (uint32_t)y[i] : (uint32_t)(y[i] >> 32);
+        f[e] = byte_as_f32bits(w, a & 3);
+      } else {
+        f[e] = 0;
+      }
+    }
+    uint4 v;
+    v.x = __byte_perm(f[0], f[1], 0x7632);
+    v.y = __byte_perm(f[2], f[3], 0x7632);
+    v.z = __byte_perm(f[4], f[5], 0x7632);
+    v.w = __byte_perm(f[6], f[7], 0x7632);
+    *(uint4*)(tile + tc_cm(m, kc * 8, TC_K)) = v;
+  }
+}
+
+// value of an exact integer below 2^23 held in an f32 accumulator word
+HPD uint32_t acc_int(uint32_t bits) { return __float_as_uint(__uint_as_float(bits) + 8388608.0f) & 0x7FFFFFu; }
+
+// sum_l D_l 2^(8l) + corr mod p, for the limb sums D_0..D_6 of one prime;
+// c32 = [2^32]_p (Shoup pair).  The low part is < 2^48 < p, the high part
+// times 2^32 reduces to [0, 2p), corr < p: the total is below 4p.
+HPD uint64_t limb_sum_mod(const uint32_t (&r)[8], uint64_t corr, uint64_t p, uint64_t c32, uint64_t c32s) {
+  const uint64_t lo = (uint64_t)acc_int(r[0]) + ((uint64_t)acc_int(r[1]) << 8) + ((uint64_t)acc_int(r[2]) << 16) +
+                      ((uint64_t)acc_int(r[3]) << 24);
+  const uint64_t hi = (uint64_t)acc_int(r[4]) + ((uint64_t)acc_int(r[5]) << 8) + ((uint64_t)acc_int(r[6]) << 16);
+  const uint64_t x = lo + mul_shoup_lazy(hi, c32, c32s, p) + corr;
+  return csub(csub(x, 2 * p), p);
+}
+
+// Persistent: SRT_GROUPS groups of four warps, each taking tiles of 128
+// consecutive coefficients (one per thread) of the nct x 3 coefficient
+// polynomials.  tables = B1 | B2 | T1 | T2 (see build_tc_tables).
+__global__ void __launch_bounds__(SRT_THREADS, 1)
+    k_scale_round_tc(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3, int* __restrict__ status,
+                     const uint16_t* __restrict__ tables, int logN, int nct) {
+  extern __shared__ __align__(1024) uint8_t srt_smem[];
+  uint16_t* B1s = (uint16_t*)srt_smem;
+  uint16_t* B2s = B1s + SRT_OPER;
+  uint16_t* As = B2s + SRT_OPER;  // SRT_GROUPS tiles
+  uint64_t* T1s = (uint64_t*)(As + SRT_GROUPS * SRT_OPER);
+  uint64_t* T2s = T1s + TC_T1;
+  uint64_t* mbar = T2s + TC_T2;
+  uint32_t* tslot = (uint32_t*)(mbar + SRT_GROUPS);
+  uint32_t* okf = tslot + 1;  // per group: the last MMA batch completed
+  const int N = 1 << logN, t = threadIdx.x, warp = t >> 5, g = warp >> 2, m = t & 127;
+  {  // constant operands and tables, once per CTA
+    const uint4* src = (const uint4*)tables;
+    uint4* dst = (uint4*)srt_smem;
+    for (int e = t; e < 2 * SRT_OPER / 8; e += SRT_THREADS) dst[e] = src[e];
+    const uint64_t* tsrc = (const uint64_t*)(tables + 2 * SRT_OPER);
+    for (int e = t; e < TC_T1 + TC_T2; e += SRT_THREADS) T1s[e] = tsrc[e];
+  }
+  if (t < SRT_GROUPS) mbar_init(mbar + t, 1);
+  fence_async_smem();
+  if (warp == 0) tc_alloc(tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot + (uint32_t)(g * 128) + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t tcol = *tslot + (uint32_t)(g * 128);
+  uint16_t* A = As + g * SRT_OPER;
+  const uint32_t idesc = tc_idesc_f16(128, 128, 1);
+  const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s), b2_addr = smem_u32(B2s);
+  const size_t ntiles = ((size_t)nct * 3) << (logN - 7);
+  uint32_t phase = 0;
+  for (size_t tile = (size_t)blockIdx.x * SRT_GROUPS + g; tile < ntiles; tile += (size_t)gridDim.x * SRT_GROUPS) {
+    const size_t gid = (tile << 7) + m;
+    const int n = (int)(gid & (N - 1));
+    const size_t bj = gid >> logN;
+    const uint64_t* d = dprod + bj * NQB * N + n;
+    // ---- r = [t d]_Q: y_i and the centring decision v (as k_scale_round) ----
+    uint64_t y[L];
+    Fix F = {0, 0};
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      y[i] = mul_shoup(d[(size_t)i * N], cK.qhatinv[i], cK.qhatinv_s[i], cK.p[i]);
+      fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
+    }
+    const int v = lift_v_mem(F, d, N);
+    put_limb_row<L>(A, m, y);
+    fence_async_smem();
+    named_sync(1 + g, 128);
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < TC_K / 16; ++ks)
+        tc_mma_f16(tcol, tc_desc(a_addr + ks * 256, 128, TC_K * 16), tc_desc(b1_addr + ks * 256, 128, TC_K * 16),
+                   idesc, ks > 0);
+      tc_commit(mbar + g);
+      okf[g] = mbar_wait(mbar + g, phase, 1u << 22) ? 1u : 0u;  // one bounded waiter per group
+    }
+    named_sync(1 + g, 128);
+    if (!okf[g]) {  // uniform in the group: leave the loop, free TMEM below
+      if (m == 0) atomicOr(status, ST_TC_TIMEOUT);
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    // ---- r in B, w = (t d - r) Q^{-1} in B, the centring decision vb ----
+    uint64_t yb[K];
+    Fix G = {0, 0};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      uint32_t r8[8];
+      tc_ld8(tmem + 8 * k, r8);
+      tc_wait_ld();
+      const uint64_t b = cK.p[L + k];
+      const uint64_t r = limb_sum_mod(r8, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]);
+      const uint64_t z = sub_mod(d[(size_t)(L + k) * N], r, b);
+      yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
+      fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
+    }
+    int vb = fix_round(G, 2 * K);
+    if (vb < 0) {  // cannot happen for |w| < B / 2^24; recorded for the host
+      atomicOr(status, ST_BQ_WINDOW);
+      vb = (int)G.hi;
+    }
+    tc_fence_before();
+    named_sync(1 + g, 128);  // every lane has read D; the first MMA finished with A
+    put_limb_row<K>(A, m, yb);
+    fence_async_smem();
+    named_sync(1 + g, 128);
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < TC_K / 16; ++ks)
+        tc_mma_f16(tcol, tc_desc(a_addr + ks * 256, 128, TC_K * 16), tc_desc(b2_addr + ks * 256, 128, TC_K * 16),
+                   idesc, ks > 0);
+      tc_commit(mbar + g);
+      okf[g] = mbar_wait(mbar + g, phase, 1u << 22) ? 1u : 0u;  // one bounded waiter per group
+    }
+    named_sync(1 + g, 128);
+    if (!okf[g]) {  // uniform in the group: leave the loop, free TMEM below
+      if (m == 0) atomicOr(status, ST_TC_TIMEOUT);
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    // ---- w mod q_i (B -> Q), stored; d2 as key-switching digits ----
+    uint64_t* o = w3 + bj * L * N + n;
+    const bool digits = (bj % 3) == 2;
+#pragma unroll
+    for (int gq = 0; gq < NDIG; ++gq) {
+      uint64_t out[DIGIT_PRIMES];
+#pragma unroll
+      for (int e = 0; e < DIGIT_PRIMES; ++e) {
+        const int i = gq * DIGIT_PRIMES + e;
+        uint32_t r8[8];
+        tc_ld8(tmem + 8 * i, r8);
+        tc_wait_ld();
+        out[e] = limb_sum_mod(r8, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
+      }
+      if (digits) digit_mixed_radix(out, gq);
+#pragma unroll
+      for (int e = 0; e < DIGIT_PRIMES; ++e) o[(size_t)(gq * DIGIT_PRIMES + e) * N] = out[e];
+    }
+    tc_fence_before();
+    named_sync(1 + g, 128);  // D and A free for the next tile
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(*tslot, 512);
+}
+
+}  // namespace hp

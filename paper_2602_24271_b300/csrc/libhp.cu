@@ -17,6 +17,7 @@
 #include "hp_probe.cuh"
 #include "hp_rns.cuh"
 #include "hp_tc.cuh"
+#include "hp_tcconv.cuh"
 
 using namespace hp;
 
@@ -64,6 +65,9 @@ struct hp_handle {
   // galois_elements, same layout and form as rkm), allocated on first use
   uint64_t* gkm = nullptr;
   bool have_gk = false;
+  // tensor-core conversion operands and tables (build_tc_tables), SM count
+  uint16_t* tct = nullptr;
+  int sms = 0;
   int* status = nullptr;  // device status word (ST_* bits)
   uint64_t launches = 0;
   std::string err;
@@ -245,7 +249,9 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
   ntt_inv(h, h->dprod, (size_t)b * 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
   {
     ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
-    k_scale_round<<<ew_blocks((size_t)b * 3 * N), EW_THREADS, 0, s>>>(h->dprod, h->w3, h->status, logN, b);
+    const size_t tiles = ((size_t)b * 3 * N) >> 7, ctas = (tiles + SRT_GROUPS - 1) / SRT_GROUPS;
+    k_scale_round_tc<<<(unsigned)std::min<size_t>(ctas, (size_t)h->sms), SRT_THREADS, SRT_SMEM, s>>>(
+        h->dprod, h->w3, h->status, h->tct, logN, b);
   }
   h->launches += 1;
   // key switching: digits [d2]_{q_i} mod p_j (reduction fused into the first
@@ -404,6 +410,19 @@ static int brv(int x, int bits) {
   return r;
 }
 
+// Operands and correction tables of the tensor-core scale-and-round, and the
+// kernel's shared-memory limit.
+static int build_tc(hp_handle* h) {
+  std::vector<uint16_t> buf(2 * TC_ROWS * TC_K + 4 * (TC_T1 + TC_T2));
+  build_tc_tables(h->C, buf.data(), buf.data() + TC_ROWS * TC_K, (uint64_t*)(buf.data() + 2 * TC_ROWS * TC_K),
+                  (uint64_t*)(buf.data() + 2 * TC_ROWS * TC_K) + TC_T1);
+  CU(h, cudaMalloc((void**)&h->tct, buf.size() * sizeof(uint16_t)));
+  CU(h, cudaMemcpy(h->tct, buf.data(), buf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  CU(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+  CU(h, cudaFuncSetAttribute(k_scale_round_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SRT_SMEM));
+  return HP_OK;
+}
+
 static int build_tables(hp_handle* h) {
   const int N = h->N;
   std::vector<ulonglong2> tw((size_t)NPRIME * N), itw(tw.size());
@@ -475,7 +494,7 @@ static void free_all(hp_handle* h) {
   }
   void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->ext, h->ext2, h->dprod, h->w3,
                   h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
-                  h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef, h->gkm};
+                  h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef, h->gkm, h->tct};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->status) cudaFree(h->status);
@@ -541,6 +560,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   if ((rc = load_consts(h)) != HP_OK) return fail(rc);
 
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
+  if ((rc = build_tc(h)) != HP_OK) return fail(rc);
   size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
   h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)5 << 30) / per);  // ~5 GB of workspace
   if (h->tile < 1) h->tile = 1;
@@ -1375,8 +1395,8 @@ int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches,
   return HP_OK;
 }
 
-int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n) {
-  if (!A || !B || !D || n < 16 || n > 256 || n % 16) return HP_ERR_ARG;
+int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16) {
+  if (!A || !B || !D || n < 16 || n > 256 || n % 16 || (bf16 != 0 && bf16 != 1)) return HP_ERR_ARG;
   hp_handle* h = nullptr;
   uint16_t *dA = nullptr, *dB = nullptr;
   float* dD = nullptr;
@@ -1391,7 +1411,7 @@ int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n) {
   CU(h, cudaMemcpy(dB, B, (size_t)n * TCP_K * 2, cudaMemcpyHostToDevice));
   const int smem = (TCP_M + 256) * TCP_K * 2 + 16;
   CU(h, cudaFuncSetAttribute(k_tc_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_tc_probe<<<1, 128, smem>>>(dA, dB, dD, n, dst);
+  k_tc_probe<<<1, 128, smem>>>(dA, dB, dD, n, bf16, dst);
   CU(h, cudaGetLastError());
   CU(h, cudaDeviceSynchronize());
   int st = 0;

@@ -49,7 +49,7 @@ EXPORTED = [
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
                    "scale_round", "automorph", "ks_mac", "moddown"]
 KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows", "k_ntt_inv_rows", "k_ntt_inv_cols", "k_lift", "k_tensor_sq",
-                   "k_scale_round", "k_automorph", "k_ks_mac", "k_moddown"]
+                   "k_scale_round_tc", "k_automorph", "k_ks_mac", "k_moddown"]
 
 
 DIGIT_PRIMES = 3  # data primes per key-switching digit (D = L / 3 digits)
@@ -125,7 +125,7 @@ def load():
         "hp_set_galois_keys": (ctypes.c_int, [H, P64]),
         "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_ct_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
-        "hp_probe_tc_gemm": (ctypes.c_int, [V, V, V, ctypes.c_int]),
+        "hp_probe_tc_gemm": (ctypes.c_int, [V, V, V, ctypes.c_int, ctypes.c_int]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }
@@ -348,13 +348,22 @@ class Context:
         return ms.value, int(n.value), w.value
 
 
-def probe_tc_gemm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """Tensor-core probe: A [128, 112] and B [n, 112] f16 -> A @ B.T as f32 [128, n]."""
+def _bf16_bits(x: np.ndarray) -> np.ndarray:
+    """bf16 bit patterns of values exactly representable in bf16 (top half of f32)."""
+    return (np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def probe_tc_gemm(A: np.ndarray, B: np.ndarray, bf16: bool = False) -> np.ndarray:
+    """Tensor-core probe: A [128, 112] and B [n, 112] (f16, or bf16 when `bf16`;
+    given as numbers) -> A @ B.T as f32 [128, n]."""
     lib = load()
-    A = np.ascontiguousarray(A, dtype=np.float16)
-    B = np.ascontiguousarray(B, dtype=np.float16)
+    if bf16:
+        A, B = _bf16_bits(A), _bf16_bits(B)
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float16).view(np.uint16)
+        B = np.ascontiguousarray(B, dtype=np.float16).view(np.uint16)
     D = np.zeros((128, B.shape[0]), dtype=np.float32)
-    _check(lib.hp_probe_tc_gemm(A.ctypes.data, B.ctypes.data, D.ctypes.data, B.shape[0]))
+    _check(lib.hp_probe_tc_gemm(A.ctypes.data, B.ctypes.data, D.ctypes.data, B.shape[0], int(bf16)))
     return D
 
 

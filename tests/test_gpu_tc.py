@@ -16,21 +16,23 @@ def lib():
     return hp.load()
 
 
-@pytest.mark.parametrize("n", [256, 208, 16])
-def test_tc_gemm_exact_random_limbs(n):
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("n", [256, 208, 112, 16])
+def test_tc_gemm_exact_random_limbs(n, bf16):
     rng = np.random.default_rng(n)
     A = rng.integers(0, 256, (128, 112))
     B = rng.integers(0, 256, (n, 112))
-    D = hp.probe_tc_gemm(A.astype(np.float16), B.astype(np.float16))
+    D = hp.probe_tc_gemm(A, B, bf16=bf16)
     assert np.array_equal(D.astype(np.int64), A @ B.T)
 
 
-def test_tc_gemm_exact_at_the_largest_sums():
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tc_gemm_exact_at_the_largest_sums(bf16):
     """112 products of 255 x 255: 7,282,800 < 2^23, still exact in f32."""
     A = np.full((128, 112), 255)
     B = np.full((208, 112), 255)
     B[5, :] = np.arange(112) % 256
-    D = hp.probe_tc_gemm(A.astype(np.float16), B.astype(np.float16))
+    D = hp.probe_tc_gemm(A, B, bf16=bf16)
     assert np.array_equal(D.astype(np.int64), A @ B.T)
 
 
@@ -38,5 +40,6 @@ def test_tc_gemm_structured_positions():
     """Distinct values per (row, k) expose any mix-up of the operand layout."""
     A = (np.arange(128)[:, None] * 3 + np.arange(112)[None, :] * 5) % 251
     B = (np.arange(256)[:, None] * 7 + np.arange(112)[None, :] * 11) % 241
-    D = hp.probe_tc_gemm(A.astype(np.float16), B.astype(np.float16))
-    assert np.array_equal(D.astype(np.int64), A @ B.T)
+    for bf16 in (False, True):
+        D = hp.probe_tc_gemm(A, B, bf16=bf16)
+        assert np.array_equal(D.astype(np.int64), A @ B.T)
