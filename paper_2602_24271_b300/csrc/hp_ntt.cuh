@@ -226,9 +226,11 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restri
     }
   }
   __syncthreads();
-  for (int e = t; e < NTT_TILE; e += NTT_THREADS) {
-    const int rr = e / C, kk = e % C;
-    a[(size_t)(row0 + rr) * C + kk] = s[rr * PADC + kk + (kk >> 4)];
+  uint64_t* dst = a + (size_t)row0 * C;
+#pragma unroll
+  for (int u = 0; u < NTT_TILE / NTT_THREADS; ++u) {
+    const int e = t + u * NTT_THREADS, rr = e / C, kk = e % C;
+    dst[e] = s[rr * PADC + kk + (kk >> 4)];
   }
 }
 
@@ -244,9 +246,16 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restri
   const PForm f = pform(id);
   const ulonglong2* itw = T.itw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
-  for (int e = t; e < NTT_TILE; e += NTT_THREADS) {
-    const int rr = e / C, kk = e % C;
-    s[rr * PADC + kk + (kk >> 4)] = a[(size_t)(row0 + rr) * C + kk];
+  {  // the tile is contiguous: all 16 loads of a thread in flight, then the padded stores
+    const uint64_t* src = a + (size_t)row0 * C;
+    uint64_t v[NTT_TILE / NTT_THREADS];
+#pragma unroll
+    for (int u = 0; u < NTT_TILE / NTT_THREADS; ++u) v[u] = src[t + u * NTT_THREADS];
+#pragma unroll
+    for (int u = 0; u < NTT_TILE / NTT_THREADS; ++u) {
+      const int e = t + u * NTT_THREADS, rr = e / C, kk = e % C;
+      s[rr * PADC + kk + (kk >> 4)] = v[u];
+    }
   }
   __syncthreads();
 #pragma unroll

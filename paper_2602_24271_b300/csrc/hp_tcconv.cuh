@@ -35,6 +35,20 @@ HPD void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "memory");
 }
 
+// 32 TMEM lanes x 32 (resp. 64) consecutive 32-bit columns
+HPD void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr)
+               : "memory");
+}
+HPD void tc_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+               : "r"(taddr)
+               : "memory");
+}
+
 // bf16 of byte `a` of the 32-bit word w (exact: 2^23 + byte in f32, minus 2^23)
 HPD uint32_t byte_as_f32bits(uint32_t w, int a) {
   const float f = __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)a | 0x7540u)) - 8388608.0f;
@@ -73,7 +87,8 @@ HPD uint32_t acc_int(uint32_t bits) { return __float_as_uint(__uint_as_float(bit
 // sum_l D_l 2^(8l) + corr mod p, for the limb sums D_0..D_6 of one prime;
 // c32 = [2^32]_p (Shoup pair).  The low part is < 2^48 < p, the high part
 // times 2^32 reduces to [0, 2p), corr < p: the total is below 4p.
-HPD uint64_t limb_sum_mod(const uint32_t (&r)[8], uint64_t corr, uint64_t p, uint64_t c32, uint64_t c32s) {
+// r points at the prime's 8 accumulator columns (constant offsets into a register array).
+HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t c32, uint64_t c32s) {
   const uint64_t lo = (uint64_t)acc_int(r[0]) + ((uint64_t)acc_int(r[1]) << 8) + ((uint64_t)acc_int(r[2]) << 16) +
                       ((uint64_t)acc_int(r[3]) << 24);
   const uint64_t hi = (uint64_t)acc_int(r[4]) + ((uint64_t)acc_int(r[5]) << 8) + ((uint64_t)acc_int(r[6]) << 16);
@@ -133,6 +148,9 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     const int v = lift_v_mem(F, d, N);
     put_limb_row<L>(A, m, y);
     fence_async_smem();
+    uint64_t dB[K];  // residues mod B, loaded while the MMA runs
+#pragma unroll
+    for (int k = 0; k < K; ++k) dB[k] = d[(size_t)(L + k) * N];
     named_sync(1 + g, 128);
     if (m == 0) {
       tc_fence_after();
@@ -154,15 +172,19 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     uint64_t yb[K];
     Fix G = {0, 0};
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      uint32_t r8[8];
-      tc_ld8(tmem + 8 * k, r8);
+    for (int kb = 0; kb < K / 4; ++kb) {  // four primes (32 columns) per TMEM load
+      uint32_t r32[32];
+      tc_ld32(tmem + 32 * kb, r32);
       tc_wait_ld();
-      const uint64_t b = cK.p[L + k];
-      const uint64_t r = limb_sum_mod(r8, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]);
-      const uint64_t z = sub_mod(d[(size_t)(L + k) * N], r, b);
-      yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
-      fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int k = kb * 4 + kk;
+        const uint64_t b = cK.p[L + k];
+        const uint64_t r = limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]);
+        const uint64_t z = sub_mod(dB[k], r, b);
+        yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
+        fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
+      }
     }
     int vb = fix_round(G, 2 * K);
     if (vb < 0) {  // cannot happen for |w| < B / 2^24; recorded for the host
@@ -192,24 +214,134 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     tc_fence_after();
     // ---- w mod q_i (B -> Q), stored; d2 as key-switching digits ----
     uint64_t* o = w3 + bj * L * N + n;
-    const bool digits = (bj % 3) == 2;
+    uint64_t out[L];
 #pragma unroll
-    for (int gq = 0; gq < NDIG; ++gq) {
-      uint64_t out[DIGIT_PRIMES];
+    for (int ib = 0; ib < 4; ++ib) {  // four primes (32 columns) per TMEM load
+      uint32_t r32[32];
+      tc_ld32(tmem + 32 * ib, r32);
+      tc_wait_ld();
 #pragma unroll
-      for (int e = 0; e < DIGIT_PRIMES; ++e) {
-        const int i = gq * DIGIT_PRIMES + e;
-        uint32_t r8[8];
-        tc_ld8(tmem + 8 * i, r8);
-        tc_wait_ld();
-        out[e] = limb_sum_mod(r8, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
+      for (int ii = 0; ii < 4; ++ii) {
+        const int i = ib * 4 + ii;
+        if (i < L) out[i] = limb_sum_mod(r32 + 8 * ii, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
       }
-      if (digits) digit_mixed_radix(out, gq);
-#pragma unroll
-      for (int e = 0; e < DIGIT_PRIMES; ++e) o[(size_t)(gq * DIGIT_PRIMES + e) * N] = out[e];
     }
+    if ((bj % 3) == 2) {  // d2 as key-switching digits
+#pragma unroll
+      for (int gq = 0; gq < NDIG; ++gq) {
+        uint64_t r3[DIGIT_PRIMES] = {out[3 * gq], out[3 * gq + 1], out[3 * gq + 2]};
+        digit_mixed_radix(r3, gq);
+        out[3 * gq + 1] = r3[1];
+        out[3 * gq + 2] = r3[2];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) o[(size_t)i * N] = out[i];
     tc_fence_before();
     named_sync(1 + g, 128);  // D and A free for the next tile
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(*tslot, 512);
+}
+
+// ---- exact centred lift Q -> B (k_lift) with the conversion on the tensor cores ----
+// Same first-lift modes and residue outputs as k_lift; the auxiliary residues
+// come from one bf16 MMA per 128-coefficient tile with the operand B1 (the Q ->
+// B conversion of the scale-and-round) and the correction table T1.
+constexpr size_t LFT_SMEM = (size_t)(1 + SRT_GROUPS) * SRT_OPER * 2 + TC_T1 * 8 + SRT_GROUPS * 8 + 32;
+
+__global__ void __launch_bounds__(SRT_THREADS, 1)
+    k_lift_tc(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, uint64_t const_val, int mode,
+              uint64_t* __restrict__ ext, int* __restrict__ status, const uint16_t* __restrict__ tables, int logN,
+              int nct) {
+  extern __shared__ __align__(1024) uint8_t lft_smem[];
+  uint16_t* B1s = (uint16_t*)lft_smem;
+  uint16_t* As = B1s + SRT_OPER;
+  uint64_t* T1s = (uint64_t*)(As + SRT_GROUPS * SRT_OPER);
+  uint64_t* mbar = T1s + TC_T1;
+  uint32_t* tslot = (uint32_t*)(mbar + SRT_GROUPS);
+  uint32_t* okf = tslot + 1;
+  const int N = 1 << logN, t = threadIdx.x, warp = t >> 5, g = warp >> 2, m = t & 127;
+  {
+    const uint4* bsrc = (const uint4*)tables;
+    uint4* dst = (uint4*)lft_smem;
+    for (int e = t; e < SRT_OPER / 8; e += SRT_THREADS) dst[e] = bsrc[e];
+    const uint64_t* tsrc = (const uint64_t*)(tables + 2 * SRT_OPER);
+    for (int e = t; e < TC_T1; e += SRT_THREADS) T1s[e] = tsrc[e];
+  }
+  if (t < SRT_GROUPS) mbar_init(mbar + t, 1);
+  fence_async_smem();
+  if (warp == 0) tc_alloc(tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot + (uint32_t)(g * 128) + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t tcol = *tslot + (uint32_t)(g * 128);
+  uint16_t* A = As + g * SRT_OPER;
+  const uint32_t idesc = tc_idesc_f16(128, 128, 1);
+  const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s);
+  const size_t ntiles = ((size_t)nct * 2) << (logN - 7);
+  uint32_t phase = 0;
+  for (size_t tile = (size_t)blockIdx.x * SRT_GROUPS + g; tile < ntiles; tile += (size_t)gridDim.x * SRT_GROUPS) {
+    const size_t gid = (tile << 7) + m;
+    const int n = (int)(gid & (N - 1));
+    const size_t bc = gid >> logN;  // b * 2 + c
+    const int comp = (int)(bc & 1);
+    const uint64_t* x = src + bc * L * N + n;
+    uint64_t* o = ext + bc * NQB * N + n;
+    uint64_t y[L];
+    Fix F = {0, 0};
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      const uint64_t p = cK.p[i];
+      uint64_t v = x[(size_t)i * N];
+      if (mode == LIFT_SUB_CT) {
+        v = sub_mod(v, sub[bc * L * N + (size_t)i * N + n], p);
+      } else if (mode == LIFT_SUB_CONST && comp == 0 && n == 0) {
+        v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
+      } else if (mode == LIFT_SUB_PT && comp == 0) {
+        v = sub_mod(v, mul_shoup(sub[(bc >> 1) * N + n], cK.delta[i], cK.delta_s[i], p), p);
+      } else if (mode == LIFT_SUB_CONSTS && comp == 0 && n == 0) {
+        v = sub_mod(v, mul_shoup(sub[bc >> 1], cK.delta[i], cK.delta_s[i], p), p);
+      }
+      o[(size_t)i * N] = v;
+      y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
+      fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
+    }
+    const int v = lift_v_mem(F, o, N);  // the exact path re-reads the residues written above
+    put_limb_row<L>(A, m, y);
+    fence_async_smem();
+    named_sync(1 + g, 128);
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < TC_K / 16; ++ks)
+        tc_mma_f16(tcol, tc_desc(a_addr + ks * 256, 128, TC_K * 16), tc_desc(b1_addr + ks * 256, 128, TC_K * 16),
+                   idesc, ks > 0);
+      tc_commit(mbar + g);
+      okf[g] = mbar_wait(mbar + g, phase, 1u << 22) ? 1u : 0u;
+    }
+    named_sync(1 + g, 128);
+    if (!okf[g]) {
+      if (m == 0) atomicOr(status, ST_TC_TIMEOUT);
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {  // eight primes (64 columns) per TMEM load
+      uint32_t r64[64];
+      tc_ld64(tmem + 64 * kb, r64);
+      tc_wait_ld();
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int k = kb * 8 + kk;
+        o[(size_t)(L + k) * N] = limb_sum_mod(r64 + 8 * kk, T1s[v * 16 + k], cK.p[L + k], cK.r32b[k], cK.r32b_s[k]);
+      }
+    }
+    tc_fence_before();
+    named_sync(1 + g, 128);
   }
   tc_fence_before();
   __syncthreads();

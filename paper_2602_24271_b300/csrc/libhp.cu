@@ -273,7 +273,9 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
 static void lift(hp_handle* h, const uint64_t* src, const uint64_t* sub, uint64_t cval, int mode, uint64_t* ext, int b,
                  cudaStream_t s) {
   ProfScope ps(h, PK_LIFT, s, 2.0 * b * h->N);
-  k_lift<<<ew_blocks((size_t)b * 2 * h->N), EW_THREADS, 0, s>>>(src, sub, cval, mode, ext, h->logn, b);
+  const size_t tiles = ((size_t)b * 2 * h->N) >> 7, ctas = (tiles + SRT_GROUPS - 1) / SRT_GROUPS;
+  k_lift_tc<<<(unsigned)std::min<size_t>(ctas, (size_t)h->sms), SRT_THREADS, LFT_SMEM, s>>>(
+      src, sub, cval, mode, ext, h->status, h->tct, h->logn, b);
   h->launches += 1;
 }
 
@@ -420,6 +422,7 @@ static int build_tc(hp_handle* h) {
   CU(h, cudaMemcpy(h->tct, buf.data(), buf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   CU(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
   CU(h, cudaFuncSetAttribute(k_scale_round_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SRT_SMEM));
+  CU(h, cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LFT_SMEM));
   return HP_OK;
 }
 
