@@ -234,6 +234,72 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restri
   }
 }
 
+// ---- forward rows of both components + squaring tensor ----------------------------
+// The row pass of k_ntt_fwd_rows on components 0 and 1 of one ciphertext's
+// lifted polynomial for one prime (blockIdx.y = b * NQB + pi), followed by the
+// squaring tensor of k_tensor_sq on the two finished tiles:
+//   d0 = a0 a0 2^-64, d1 = 2 a0 a1 2^-64 (reduced to [0, 2p)), d2 = a1 a1 2^-64.
+// ext: [nct][2][NQB][N] after the column pass; dprod: [nct][3][NQB][N].
+template <int LOGR, int LOGC>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows_sq(const uint64_t* __restrict__ ext,
+                                                                 uint64_t* __restrict__ dprod, NttTabs T) {
+  constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
+  constexpr int ROWS = NTT_TILE >> LOGC, TPR = C / 16, B2 = LOGC - 4, PADC = C + C / 16;
+  __shared__ uint64_t s[ROWS * PADC];   // exchange, then component 1's result
+  __shared__ uint64_t s0[ROWS * PADC];  // component 0's result
+  const int t = threadIdx.x, r = t / TPR, kb = t % TPR;
+  const int bp = blockIdx.y, pi = bp % NQB, row0 = blockIdx.x * ROWS, row = row0 + r;
+  const size_t b = bp / NQB;
+  const PForm f = pform(pi);
+  const uint64_t p = f.p, pinv = cK.pinv[pi];
+  const ulonglong2* tw = T.tw + (size_t)pi * N;
+#pragma unroll 1
+  for (int comp = 0; comp < 2; ++comp) {
+    const uint64_t* a = ext + ((b * 2 + comp) * NQB + pi) * N;
+    uint64_t* res = comp ? s : s0;
+    uint64_t x[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = a[(size_t)row * C + kb + u * TPR];
+    fwd_block<4>(x, (uint32_t)(row * C + kb), LOGR, logN, tw, f);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int kk = kb + u * TPR;
+      s[r * PADC + kk + (kk >> 4)] = x[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < (16 / TPR); ++m) {
+      const int g = kb + m * TPR;
+      uint64_t y[1 << B2];
+#pragma unroll
+      for (int u = 0; u < (1 << B2); ++u) {
+        const int kk = (g << B2) + u;
+        y[u] = s[r * PADC + kk + (kk >> 4)];
+      }
+      fwd_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, tw, f);
+#pragma unroll
+      for (int u = 0; u < (1 << B2); ++u) {
+        const int kk = (g << B2) + u;
+        res[r * PADC + kk + (kk >> 4)] = red64to8(y[u], p);
+      }
+    }
+    __syncthreads();
+  }
+  const uint64_t p2 = 2 * p;
+  uint64_t* d0 = dprod + ((b * 3 + 0) * NQB + pi) * N + (size_t)row0 * C;
+  uint64_t* d1 = d0 + (size_t)NQB * N;
+  uint64_t* d2 = d1 + (size_t)NQB * N;
+#pragma unroll
+  for (int u = 0; u < NTT_TILE / NTT_THREADS; ++u) {
+    const int e = t + u * NTT_THREADS, rr = e / C, kk = e % C, si = rr * PADC + kk + (kk >> 4);
+    const uint64_t a0 = s0[si], a1 = s[si];
+    const uint64_t m01 = 2 * mont_mul_lazy(a0, a1, p, pinv);
+    d0[e] = mont_mul_lazy(a0, a0, p, pinv);
+    d1[e] = m01 >= p2 ? m01 - p2 : m01;
+    d2[e] = mont_mul_lazy(a1, a1, p, pinv);
+  }
+}
+
 // ---- inverse, rows (stages logN-1 .. LOGR); input in [0, 2p) --------------------
 template <int LOGR, int LOGC>
 __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restrict__ data, PolyMap map, NttTabs T) {
@@ -287,14 +353,28 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restri
 }
 
 // ---- inverse, columns (stages LOGR-1 .. 0) and scaling; canonical output --------
-template <int LOGR, int LOGC>
+// Optional fused key-switching mod-down (MD = true): block y transforms the
+// key-switching sum u_i of (ciphertext-component bc = y / L, data prime
+// i = y % L), polynomial bc NKS + i of `data`, whose special-prime
+// polynomial u_P (bc NKS + L) is already transformed, and writes
+//   out[bc][i] = w3[b][c][i] + (u_i - [u_P]) P^{-1} mod q_i   ([u_P] centred),
+// or its "1 -" form, instead of u_i.  Otherwise (MD = false) block y
+// transforms polynomial y pstride + poff in place.
+struct ModDown {
+  const uint64_t* w3;  // [nct][3][L][N]: (d0, d1) to add to
+  uint64_t* out;       // [nct][2][L][N]
+  int one_minus;
+  int pstride, poff;
+};
+template <int LOGR, int LOGC, bool MD>
 __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
-                                                              int scale_mode) {
+                                                              int scale_mode, ModDown md) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
   __shared__ uint64_t s[NTT_TILE];
   const int t = threadIdx.x, k = t % COLS, rb = t / COLS;
-  const int poly = blockIdx.y, k0 = blockIdx.x * COLS;
+  const int y0 = blockIdx.y, k0 = blockIdx.x * COLS;
+  const int poly = MD ? (y0 / L) * NKS + (y0 % L) : y0 * md.pstride + md.poff;
   const int id = map.id(poly);
   const PForm f = pform(id);
   const uint64_t p = f.p;
@@ -317,10 +397,33 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restri
   inv_block<4>(x, (uint32_t)(rb * C + k0 + k), 0, logN, itw, f);
   const uint64_t* sc = T.scale + ((size_t)scale_mode * NPRIME + id) * 2;
   const uint64_t w = sc[0], wp = sc[1];
+  if (!MD) {
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const uint64_t y = mul_shoup4(x[u], w, wp, f);  // [0, 4p)
-    a[(size_t)(rb + u * RB) * C + k0 + k] = csub(csub(y, 2 * p), p);
+    for (int u = 0; u < 16; ++u) {
+      const uint64_t y = mul_shoup4(x[u], w, wp, f);  // [0, 4p)
+      a[(size_t)(rb + u * RB) * C + k0 + k] = csub(csub(y, 2 * p), p);
+    }
+  } else {
+    const size_t bc = (size_t)(y0 / L);
+    const int i = y0 % L, comp = (int)(bc & 1);
+    const uint64_t P = cK.p[ID_P];
+    const uint64_t* uP = data + (bc * NKS + L) * N;
+    const uint64_t* wv = md.w3 + (((bc >> 1) * 3 + comp) * L + i) * N;
+    uint64_t* o = md.out + (bc * L + i) * N;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int n = (rb + u * RB) * C + k0 + k;
+      const uint64_t ui = csub(csub(mul_shoup4(x[u], w, wp, f), 2 * p), p);
+      const uint64_t up = uP[n];
+      const uint64_t diff = up <= (P - 1) / 2 ? sub_mod(ui, csub(csub(up, 2 * p), p), p)
+                                              : add_mod(ui, csub(csub(P - up, 2 * p), p), p);
+      uint64_t r = add_mod(wv[n], mul_shoup(diff, cK.Pinv[i], cK.Pinv_s[i], p), p);
+      if (md.one_minus) {
+        r = sub_mod(0, r, p);
+        if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], p);
+      }
+      o[n] = r;
+    }
   }
 }
 

@@ -191,6 +191,27 @@ static void ntt_fwd_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, Dig
   h->launches += 2;
 }
 
+// Forward transform of the lifted squaring operand (nct x 2 x NQB polynomials)
+// with the squaring tensor fused into the row pass: ext -> dprod.
+template <int LR, int LC>
+static void ntt_fwd_sq_t(hp_handle* h, uint64_t* ext, uint64_t* dprod, int nct, cudaStream_t s) {
+  const size_t npoly = (size_t)nct * 2 * NQB;
+  const dim3 gc((1u << LC) / (NTT_TILE >> LR), (unsigned)npoly),
+      gr((1u << LR) / (NTT_TILE >> LC), (unsigned)(nct * NQB));
+  const double half = (double)npoly * (h->N / 2);
+  DigitSrc d;
+  d.w3 = nullptr;
+  {
+    ProfScope ps(h, PK_NTT_FWD_COLS, s, half * LR);
+    k_ntt_fwd_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(ext, MAP_QB, tabs(h), d);
+  }
+  {
+    ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * LC);
+    k_ntt_fwd_rows_sq<LR, LC><<<gr, NTT_THREADS, 0, s>>>(ext, dprod, tabs(h));
+  }
+  h->launches += 2;
+}
+
 template <int LR, int LC>
 static void ntt_inv_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int scale_mode, cudaStream_t s) {
   const dim3 gc((1u << LC) / (NTT_TILE >> LR), (unsigned)npoly), gr((1u << LR) / (NTT_TILE >> LC), (unsigned)npoly);
@@ -201,9 +222,43 @@ static void ntt_inv_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int
   }
   {
     ProfScope ps(h, PK_NTT_INV_COLS, s, half * LR);
-    k_ntt_inv_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), scale_mode);
+    ModDown md = {nullptr, nullptr, 0, 1, 0};
+    k_ntt_inv_cols<LR, LC, false><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), scale_mode, md);
   }
   h->launches += 2;
+}
+
+// Inverse transform of the key-switching sums (nct x 2 x NKS polynomials) with
+// the mod-down fused into the column pass of the data primes: the special
+// prime's polynomials first, then out[bc][i] = w3 + round(u / P) (or "1 -").
+template <int LR, int LC>
+static void ntt_inv_moddown_t(hp_handle* h, uint64_t* ksout, int nct, uint64_t* out, int one_minus, cudaStream_t s) {
+  const size_t npoly = (size_t)nct * 2 * NKS;
+  const unsigned cx = (1u << LC) / (NTT_TILE >> LR);
+  const dim3 gr((1u << LR) / (NTT_TILE >> LC), (unsigned)npoly);
+  const double half = (double)(h->N / 2);
+  {
+    ProfScope ps(h, PK_NTT_INV_ROWS, s, half * npoly * LC);
+    k_ntt_inv_rows<LR, LC><<<gr, NTT_THREADS, 0, s>>>(ksout, MAP_KS, tabs(h));
+  }
+  {
+    ProfScope ps(h, PK_NTT_INV_COLS, s, half * npoly * LR);
+    ModDown mp = {nullptr, nullptr, 0, NKS, L};  // polynomials bc NKS + L: the special prime
+    k_ntt_inv_cols<LR, LC, false><<<dim3(cx, (unsigned)(nct * 2)), NTT_THREADS, 0, s>>>(ksout, MAP_KS, tabs(h),
+                                                                                        SCALE_NINV, mp);
+    ModDown md = {h->w3, out, one_minus, 0, 0};
+    k_ntt_inv_cols<LR, LC, true><<<dim3(cx, (unsigned)(nct * 2 * L)), NTT_THREADS, 0, s>>>(ksout, MAP_KS, tabs(h),
+                                                                                           SCALE_NINV, md);
+  }
+  h->launches += 3;
+}
+static void ntt_inv_moddown(hp_handle* h, uint64_t* ksout, int nct, uint64_t* out, int one_minus, cudaStream_t s) {
+  switch (h->logn) {
+    case 12: ntt_inv_moddown_t<6, 6>(h, ksout, nct, out, one_minus, s); break;
+    case 13: ntt_inv_moddown_t<6, 7>(h, ksout, nct, out, one_minus, s); break;
+    case 14: ntt_inv_moddown_t<7, 7>(h, ksout, nct, out, one_minus, s); break;
+    default: ntt_inv_moddown_t<7, 8>(h, ksout, nct, out, one_minus, s); break;
+  }
 }
 
 // N = R x C with log R = floor(log N / 2)
@@ -217,6 +272,15 @@ static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaS
     case 13: ntt_fwd_t<6, 7>(h, data, npoly, m, d, s); break;
     case 14: ntt_fwd_t<7, 7>(h, data, npoly, m, d, s); break;
     default: ntt_fwd_t<7, 8>(h, data, npoly, m, d, s); break;
+  }
+}
+
+static void ntt_fwd_sq(hp_handle* h, uint64_t* ext, uint64_t* dprod, int nct, cudaStream_t s) {
+  switch (h->logn) {
+    case 12: ntt_fwd_sq_t<6, 6>(h, ext, dprod, nct, s); break;
+    case 13: ntt_fwd_sq_t<6, 7>(h, ext, dprod, nct, s); break;
+    case 14: ntt_fwd_sq_t<7, 7>(h, ext, dprod, nct, s); break;
+    default: ntt_fwd_sq_t<7, 8>(h, ext, dprod, nct, s); break;
   }
 }
 
@@ -236,16 +300,15 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
 // ---------------------------------------------------------------------------
 static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int one_minus, cudaStream_t s) {
   const int N = h->N, logN = h->logn;
-  ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
   if (general) {  // SELECT: general product
+    ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
     ProfScope ps(h, PK_TENSOR, s, 4.0 * b * NQB * N);
     k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->ext2, h->dprod, logN, b);
-  } else {
-    ProfScope ps(h, PK_TENSOR, s, 3.0 * b * NQB * N);
-    k_tensor_sq<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->dprod, logN, b);
+    h->launches += 1;
+  } else {  // squaring: the tensor is fused into the forward row pass
+    ntt_fwd_sq(h, h->ext, h->dprod, b, s);
   }
-  h->launches += 1;
   ntt_inv(h, h->dprod, (size_t)b * 3 * NQB, MAP_QB, SCALE_T_NINV_R, s);
   {
     ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
@@ -262,12 +325,7 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
     k_ks_mac<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
   }
   h->launches += 1;
-  ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
-  {
-    ProfScope ps(h, PK_MODDOWN, s, 2.0 * b * L * N);
-    k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, out, one_minus, logN, b);
-  }
-  h->launches += 1;
+  ntt_inv_moddown(h, h->ksout, b, out, one_minus, s);
 }
 
 static void lift(hp_handle* h, const uint64_t* src, const uint64_t* sub, uint64_t cval, int mode, uint64_t* ext, int b,
@@ -1063,12 +1121,7 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
                                                               logN, b);
   }
   h->launches += 1;
-  ntt_inv(h, h->ksout, (size_t)b * 2 * NKS, MAP_KS, SCALE_NINV, s);
-  {
-    ProfScope ps(h, PK_MODDOWN, s, 2.0 * b * L * N);
-    k_moddown<<<ew_blocks((size_t)b * 2 * L * N), EW_THREADS, 0, s>>>(h->ksout, h->w3, ct, 0, logN, b);
-  }
-  h->launches += 1;
+  ntt_inv_moddown(h, h->ksout, b, ct, 0, s);
 }
 
 int hp_ct_sum(hp_handle* h, const uint64_t* x, size_t n_ct, size_t group, uint64_t* out, void* stream) {

@@ -48,7 +48,8 @@ EXPORTED = [
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
                    "scale_round", "automorph", "ks_mac", "moddown"]
-KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows", "k_ntt_inv_rows", "k_ntt_inv_cols", "k_lift_tc", "k_tensor_sq",
+KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows(_sq)", "k_ntt_inv_rows", "k_ntt_inv_cols(+mod-down)", "k_lift_tc",
+                   "k_tensor_gen",
                    "k_scale_round_tc", "k_automorph", "k_ks_mac", "k_moddown"]
 
 
