@@ -251,6 +251,20 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
 // B conversion of the scale-and-round) and the correction table T1.
 constexpr size_t LFT_SMEM = (size_t)(1 + SRT_GROUPS) * SRT_OPER * 2 + TC_T1 * 8 + SRT_GROUPS * 8 + 32;
 
+// the input residues of coefficient `m` of a lift tile (and the subtrahend's, for LIFT_SUB_CT)
+HPD void lift_tile_load(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, int mode, size_t tile,
+                        int m, int logN, uint64_t (&xv)[L], uint64_t (&sv)[L]) {
+  const int N = 1 << logN;
+  const size_t gid = (tile << 7) + m, bc = gid >> logN;
+  const size_t off = bc * L * N + (gid & (N - 1));
+#pragma unroll
+  for (int i = 0; i < L; ++i) xv[i] = src[off + (size_t)i * N];
+  if (mode == LIFT_SUB_CT) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) sv[i] = sub[off + (size_t)i * N];
+  }
+}
+
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_lift_tc(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, uint64_t const_val, int mode,
               uint64_t* __restrict__ ext, int* __restrict__ status, const uint16_t* __restrict__ tables, int logN,
@@ -281,23 +295,25 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
   uint16_t* A = As + g * SRT_OPER;
   const uint32_t idesc = tc_idesc_f16(128, 128, 1);
   const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s);
-  const size_t ntiles = ((size_t)nct * 2) << (logN - 7);
+  const size_t ntiles = ((size_t)nct * 2) << (logN - 7), stride = (size_t)gridDim.x * SRT_GROUPS;
   uint32_t phase = 0;
-  for (size_t tile = (size_t)blockIdx.x * SRT_GROUPS + g; tile < ntiles; tile += (size_t)gridDim.x * SRT_GROUPS) {
+  uint64_t xv[L], sv[L];  // this tile's inputs; the next tile's are loaded during the MMA
+  size_t tile = (size_t)blockIdx.x * SRT_GROUPS + g;
+  if (tile < ntiles) lift_tile_load(src, sub, mode, tile, m, logN, xv, sv);
+  for (; tile < ntiles; tile += stride) {
     const size_t gid = (tile << 7) + m;
     const int n = (int)(gid & (N - 1));
     const size_t bc = gid >> logN;  // b * 2 + c
     const int comp = (int)(bc & 1);
-    const uint64_t* x = src + bc * L * N + n;
     uint64_t* o = ext + bc * NQB * N + n;
     uint64_t y[L];
     Fix F = {0, 0};
 #pragma unroll
     for (int i = 0; i < L; ++i) {
       const uint64_t p = cK.p[i];
-      uint64_t v = x[(size_t)i * N];
+      uint64_t v = xv[i];
       if (mode == LIFT_SUB_CT) {
-        v = sub_mod(v, sub[bc * L * N + (size_t)i * N + n], p);
+        v = sub_mod(v, sv[i], p);
       } else if (mode == LIFT_SUB_CONST && comp == 0 && n == 0) {
         v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
       } else if (mode == LIFT_SUB_PT && comp == 0) {
@@ -312,6 +328,7 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     const int v = lift_v_mem(F, o, N);  // the exact path re-reads the residues written above
     put_limb_row<L>(A, m, y);
     fence_async_smem();
+    if (tile + stride < ntiles) lift_tile_load(src, sub, mode, tile + stride, m, logN, xv, sv);
     named_sync(1 + g, 128);
     if (m == 0) {
       tc_fence_after();
@@ -330,14 +347,14 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     phase ^= 1;
     tc_fence_after();
 #pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {  // eight primes (64 columns) per TMEM load
-      uint32_t r64[64];
-      tc_ld64(tmem + 64 * kb, r64);
+    for (int kb = 0; kb < 4; ++kb) {  // four primes (32 columns) per TMEM load
+      uint32_t r32[32];
+      tc_ld32(tmem + 32 * kb, r32);
       tc_wait_ld();
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        const int k = kb * 8 + kk;
-        o[(size_t)(L + k) * N] = limb_sum_mod(r64 + 8 * kk, T1s[v * 16 + k], cK.p[L + k], cK.r32b[k], cK.r32b_s[k]);
+      for (int kk = 0; kk < 4; ++kk) {
+        const int k = kb * 4 + kk;
+        o[(size_t)(L + k) * N] = limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], cK.p[L + k], cK.r32b[k], cK.r32b_s[k]);
       }
     }
     tc_fence_before();
