@@ -88,15 +88,15 @@ uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);
 uint64_t h_invmod(uint64_t a, uint64_t m);
 uint64_t h_shoup(uint64_t w, uint64_t p);
 
-// Tables of the tensor-core base conversions (8-bit limbs, bf16 operands).
-//   B1 [128][112]: row 8k+b (k < K, b < 7), column 7i+a (i < L, a < 7):
+// Tables of the tensor-core base conversions (8-bit limbs, f16 operands).
+//   B1 [128][128]: row 8k+b (k < K, b < 7), column 8i+a (i < L, a < 7):
 //                  limb b of [2^(8a) (Q/q_i)]_{b_k}; other entries 0.
-//   B2 [128][112]: row 8i+b (i < L, b < 7), column 7k+a (k < K, a < 7):
+//   B2 [128][128]: row 8i+b (i < L, b < 7), column 8k+a (k < K, a < 7):
 //                  limb b of [2^(8a) (B/b_k)]_{q_i}; other entries 0.
-// Both as bf16 bit patterns in the no-swizzle K-major core-matrix layout.
+// Both as f16 bit patterns in the no-swizzle K-major core-matrix layout.
 //   T1 [16][16]:   [-v Q]_{b_k} for v < 16 (k < K)
 //   T2 [17][16]:   [-v B]_{q_i} for v <= K (i < L; column 15 unused)
-constexpr int TC_ROWS = 128, TC_K = 112, TC_T1 = 16 * 16, TC_T2 = 17 * 16;
+constexpr int TC_ROWS = 128, TC_K = 128, TC_T1 = 16 * 16, TC_T2 = 17 * 16;
 void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, uint64_t* T2);
 
 // LT polynomial's odd coefficients (32768 words), see hp_host.cpp.

@@ -289,12 +289,11 @@ int lt_coefficients(uint32_t* out) {
   return 0;
 }
 
-// bf16 bit pattern of an integer below 256 (exact: at most 8 significant bits)
-static uint16_t bf16_of_byte(uint32_t v) {
-  float f = (float)v;
-  uint32_t u;
-  memcpy(&u, &f, 4);
-  return (uint16_t)(u >> 16);
+// f16 bit pattern of an integer below 2048 (exact: at most 11 significant bits)
+static uint16_t f16_of_int(uint32_t v) {
+  if (v == 0) return 0;
+  int e = 31 - __builtin_clz(v);  // v = 1.m 2^e
+  return (uint16_t)(((uint32_t)(e + 15) << 10) | ((v << (10 - e)) & 0x3FFu));
 }
 static int tc_cm_host(int r, int k) { return ((r >> 3) * (TC_K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
@@ -307,13 +306,13 @@ void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, 
     for (int i = 0; i < L; ++i) {
       uint64_t c = prod_mod(q, L, i, b[k]);  // [Q/q_i]_{b_k}
       for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, b[k]))
-        for (int l = 0; l < 7; ++l) B1[tc_cm_host(8 * k + l, 7 * i + a)] = bf16_of_byte((uint32_t)(c >> (8 * l)) & 255);
+        for (int l = 0; l < 7; ++l) B1[tc_cm_host(8 * k + l, 8 * i + a)] = f16_of_int((uint32_t)(c >> (8 * l)) & 255);
     }
   for (int i = 0; i < L; ++i)
     for (int k = 0; k < K; ++k) {
       uint64_t c = prod_mod(b, K, k, q[i]);  // [B/b_k]_{q_i}
       for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, q[i]))
-        for (int l = 0; l < 7; ++l) B2[tc_cm_host(8 * i + l, 7 * k + a)] = bf16_of_byte((uint32_t)(c >> (8 * l)) & 255);
+        for (int l = 0; l < 7; ++l) B2[tc_cm_host(8 * i + l, 8 * k + a)] = f16_of_int((uint32_t)(c >> (8 * l)) & 255);
     }
   for (int v = 0; v < 16; ++v)
     for (int k = 0; k < 16; ++k) {

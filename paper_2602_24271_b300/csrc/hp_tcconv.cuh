@@ -6,15 +6,17 @@
 // products of 55-bit numbers.  Here each residue y is split into seven 8-bit
 // limbs y^(a) and the matrix entries are pre-multiplied by 2^(8a), so that
 //   sum_i y_i c_ik = sum_{i,a} y_i^(a) [2^(8a) c_ik]_{b_k}   (mod b_k)
-// and every [2^(8a) c_ik] is itself split into limbs.  One bf16 MMA
+// and every [2^(8a) c_ik] is itself split into limbs.  One f16 MMA
 // (tcgen05.mma, M = 128 coefficients, N = 128 = 16 primes x 8 limb columns,
-// K = 112 = 16 residues x 7 limbs) then gives, per coefficient and prime, the
-// seven limb sums D_l = sum y^(a) c^(l) < 112 * 255^2 < 2^23: exact in the f32
-// accumulator.  The value sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime
+// K = 128 = 16 residues x 8 columns, the eighth zero) then gives, per
+// coefficient and prime, the seven limb sums D_l = sum y^(a) c^(l)
+// < 112 * 255^2 < 2^23: exact in the f32 accumulator.  The value sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime
 // on the CUDA cores.  Everything else (the exact centring decisions, the
 // subtraction, the mixed-radix digits) is the same arithmetic as k_scale_round,
 // so the outputs are bit-identical.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "hp_rns.cuh"
 #include "hp_tc.cuh"
 
@@ -22,7 +24,7 @@ namespace hp {
 
 constexpr int SRT_GROUPS = 4;                    // tiles of 128 coefficients in flight per CTA
 constexpr int SRT_THREADS = 128 * SRT_GROUPS;    // one thread per coefficient
-constexpr int SRT_OPER = TC_ROWS * TC_K;         // bf16 elements of one operand tile
+constexpr int SRT_OPER = TC_ROWS * TC_K;         // f16 elements of one operand tile
 constexpr size_t SRT_SMEM = (size_t)(2 + SRT_GROUPS) * SRT_OPER * 2 + (TC_T1 + TC_T2) * 8 + SRT_GROUPS * 8 + 32;
 
 HPD void named_sync(int id, int count) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
@@ -49,35 +51,29 @@ HPD void tc_ld64(uint32_t taddr, uint32_t (&r)[64]) {
                : "memory");
 }
 
-// bf16 of byte `a` of the 32-bit word w (exact: 2^23 + byte in f32, minus 2^23)
-HPD uint32_t byte_as_f32bits(uint32_t w, int a) {
-  const float f = __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)a | 0x7540u)) - 8388608.0f;
-  return __float_as_uint(f);
+// Row `m` of an operand tile: residue i occupies columns 8 i .. 8 i + 7, its
+// seven 8-bit limbs as f16 and a zero; columns of residues i >= R are zero.
+// Two limbs at a time: a byte permute builds the f16 pair (1024 + u, 1024 + v)
+// (bit patterns 0x64uu, 0x64vv), and one packed subtraction of 1024 leaves
+// the exact f16 values u, v.
+HPD uint32_t limb_pair(uint32_t w, uint32_t sel) {
+  const uint32_t biased = __byte_perm(w, 0x64006400u, sel);
+  const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&biased), __float2half2_rn(1024.0f));
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
-
-// Row `m` of an operand tile: the 8-bit limbs of R residues (column 7 i + a is
-// limb a of y[i]), zero beyond 7 R, as bf16 in the core-matrix layout.
 template <int R>
 HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
 #pragma unroll
-  for (int kc = 0; kc < TC_K / 8; ++kc) {
-    uint32_t f[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int c = kc * 8 + e, i = c / 7, a = c % 7;
-      if (i < R) {
-        const uint32_t w = a < 4 ? (uint32_t)y[i] : (uint32_t)(y[i] >> 32);
-        f[e] = byte_as_f32bits(w, a & 3);
-      } else {
-        f[e] = 0;
-      }
+  for (int i = 0; i < TC_K / 8; ++i) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (i < R) {
+      const uint32_t lo = (uint32_t)y[i], hi = (uint32_t)(y[i] >> 32);
+      v.x = limb_pair(lo, 0x7150u);  // bytes 0, 1
+      v.y = limb_pair(lo, 0x7352u);  // bytes 2, 3
+      v.z = limb_pair(hi, 0x7150u);  // bytes 4, 5
+      v.w = limb_pair(hi, 0x7452u);  // byte 6 and 0 (the constant's zero byte)
     }
-    uint4 v;
-    v.x = __byte_perm(f[0], f[1], 0x7632);
-    v.y = __byte_perm(f[2], f[3], 0x7632);
-    v.z = __byte_perm(f[4], f[5], 0x7632);
-    v.w = __byte_perm(f[6], f[7], 0x7632);
-    *(uint4*)(tile + tc_cm(m, kc * 8, TC_K)) = v;
+    *(uint4*)(tile + tc_cm(m, 8 * i, TC_K)) = v;
   }
 }
 
@@ -128,7 +124,7 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
   const uint32_t tmem = *tslot + (uint32_t)(g * 128) + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t tcol = *tslot + (uint32_t)(g * 128);
   uint16_t* A = As + g * SRT_OPER;
-  const uint32_t idesc = tc_idesc_f16(128, 128, 1);
+  const uint32_t idesc = tc_idesc_f16(128, 128, 0);
   const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s), b2_addr = smem_u32(B2s);
   const size_t ntiles = ((size_t)nct * 3) << (logN - 7);
   uint32_t phase = 0;
@@ -293,7 +289,7 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
   const uint32_t tmem = *tslot + (uint32_t)(g * 128) + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t tcol = *tslot + (uint32_t)(g * 128);
   uint16_t* A = As + g * SRT_OPER;
-  const uint32_t idesc = tc_idesc_f16(128, 128, 1);
+  const uint32_t idesc = tc_idesc_f16(128, 128, 0);
   const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s);
   const size_t ntiles = ((size_t)nct * 2) << (logN - 7), stride = (size_t)gridDim.x * SRT_GROUPS;
   uint32_t phase = 0;
