@@ -135,14 +135,15 @@ MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-
 
 KERNEL_SOURCES = {  # files whose text determines a kernel's code
     "ntt": ["hp_defs.h", "hp_device.cuh", "hp_ntt.cuh"],
+    "tc": ["hp_defs.h", "hp_device.cuh", "hp_rns.cuh", "hp_tc.cuh", "hp_tcconv.cuh"],
     "rns": ["hp_defs.h", "hp_device.cuh", "hp_rns.cuh"],
 }
 
 
 def source_hash(kernel: str) -> str:
-    files = KERNEL_SOURCES["ntt" if kernel.startswith("k_ntt") else "rns"]
+    group = "ntt" if kernel.startswith("k_ntt") else ("tc" if kernel.endswith("_tc") else "rns")
     h = hashlib.sha256()
-    for f in files:
+    for f in KERNEL_SOURCES[group]:
         h.update(open(os.path.join(ROOT, "paper_2602_24271_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
