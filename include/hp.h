@@ -332,6 +332,14 @@ int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches,
  * kernel's bounded wait. */
 int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16);
 
+/* Failure path of the tensor-core kernels' bounded waits, exercised without a
+ * fault (no counterpart in the paper): the probe issues no MMA, so its mbarrier
+ * never completes; after `polls` polls (1 .. 2^20) the kernel sets its status
+ * word, frees its tensor memory and returns.  Returns HP_ERR_TIMEOUT when the
+ * wait expired as intended (the device stays usable), HP_ERR_ARG for a bad
+ * count. */
+int hp_probe_tc_timeout(uint32_t polls);
+
 /* Register-only peak probe on the current device (no handle needed):
  * kind 0 = the 64-bit Shoup butterfly of the NTT kernels (butterflies/s),
  * kind 1 = the 64x64->128-bit multiply-accumulate of the base conversions and

@@ -101,8 +101,12 @@ HPD int tc_cm(int r, int k, int kdim) { return ((r >> 3) * (kdim >> 3) + (k >> 3
 // descriptor encodings and the exactness of the f32 accumulation of limb
 // products on the hardware.
 constexpr int TCP_M = 128, TCP_K = 112;
+// With issue = 0 no MMA is issued and nothing arrives on the mbarrier: the
+// bounded wait (`polls` polls) expires, the status word records it and the
+// kernel frees its TMEM and returns (the failure path, exercised without a fault).
 __global__ void __launch_bounds__(128) k_tc_probe(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B,
-                                                  float* __restrict__ D, int n, int bf16, int* status) {
+                                                  float* __restrict__ D, int n, int bf16, int issue, uint32_t polls,
+                                                  int* status) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint16_t* As = (uint16_t*)tsm;
   uint16_t* Bs = As + TCP_M * TCP_K;
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(128) k_tc_probe(const uint16_t* __restrict__ A
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  if (t == 0) {
+  if (t == 0 && issue) {
     const uint32_t idesc = tc_idesc_f16(TCP_M, n, bf16);
     for (int ks = 0; ks < TCP_K / 16; ++ks) {
       const uint64_t ad = tc_desc(smem_u32(As) + ks * 256, 128, (TCP_K / 8) * 128);
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(128) k_tc_probe(const uint16_t* __restrict__ A
     tc_commit(mbar);
   }
   __syncwarp();
-  const bool ok = mbar_wait(mbar, 0, 1u << 20);
+  const bool ok = mbar_wait(mbar, 0, polls);
   if (!ok) atomicOr(status, 1);
   tc_fence_after();
   if (ok) {

@@ -1451,8 +1451,7 @@ int hp_profile_read(hp_handle* h, int cls, double* ms_total, uint64_t* launches,
   return HP_OK;
 }
 
-int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16) {
-  if (!A || !B || !D || n < 16 || n > 256 || n % 16 || (bf16 != 0 && bf16 != 1)) return HP_ERR_ARG;
+static int tc_probe_run(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16, int issue, uint32_t polls) {
   hp_handle* h = nullptr;
   uint16_t *dA = nullptr, *dB = nullptr;
   float* dD = nullptr;
@@ -1467,7 +1466,7 @@ int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int 
   CU(h, cudaMemcpy(dB, B, (size_t)n * TCP_K * 2, cudaMemcpyHostToDevice));
   const int smem = (TCP_M + 256) * TCP_K * 2 + 16;
   CU(h, cudaFuncSetAttribute(k_tc_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_tc_probe<<<1, 128, smem>>>(dA, dB, dD, n, bf16, dst);
+  k_tc_probe<<<1, 128, smem>>>(dA, dB, dD, n, bf16, issue, polls, dst);
   CU(h, cudaGetLastError());
   CU(h, cudaDeviceSynchronize());
   int st = 0;
@@ -1478,6 +1477,18 @@ int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int 
   cudaFree(dD);
   cudaFree(dst);
   return st ? HP_ERR_TIMEOUT : HP_OK;
+}
+
+int hp_probe_tc_gemm(const uint16_t* A, const uint16_t* B, float* D, int n, int bf16) {
+  if (!A || !B || !D || n < 16 || n > 256 || n % 16 || (bf16 != 0 && bf16 != 1)) return HP_ERR_ARG;
+  return tc_probe_run(A, B, D, n, bf16, 1, 1u << 20);
+}
+
+int hp_probe_tc_timeout(uint32_t polls) {
+  if (polls == 0 || polls > (1u << 20)) return HP_ERR_ARG;
+  std::vector<uint16_t> A((size_t)TCP_M * TCP_K, 0), B((size_t)16 * TCP_K, 0);
+  std::vector<float> D((size_t)TCP_M * 16);
+  return tc_probe_run(A.data(), B.data(), D.data(), 16, 0, 0, polls);
 }
 
 int hp_probe_peak(int kind, double* per_second) {

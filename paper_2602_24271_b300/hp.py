@@ -43,7 +43,7 @@ EXPORTED = [
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
-    "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm",
+    "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm", "hp_probe_tc_timeout",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -127,6 +127,7 @@ def load():
         "hp_rotate_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_ct_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_probe_tc_gemm": (ctypes.c_int, [V, V, V, ctypes.c_int, ctypes.c_int]),
+        "hp_probe_tc_timeout": (ctypes.c_int, [ctypes.c_uint32]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }

@@ -43,3 +43,15 @@ def test_tc_gemm_structured_positions():
     for bf16 in (False, True):
         D = hp.probe_tc_gemm(A, B, bf16=bf16)
         assert np.array_equal(D.astype(np.int64), A @ B.T)
+
+
+def test_bounded_wait_expires_without_fault():
+    """No MMA is issued, so the mbarrier never completes: the kernel's bounded
+    wait expires, it reports HP_ERR_TIMEOUT through its status word, frees its
+    tensor memory, and the device keeps working (a product right after is exact)."""
+    lib = hp.load()
+    assert lib.hp_probe_tc_timeout(1024) == hp.HP_ERR_TIMEOUT
+    assert lib.hp_probe_tc_timeout(0) == hp.HP_ERR_ARG
+    A = np.full((128, 112), 3)
+    B = np.full((16, 112), 5)
+    assert np.array_equal(hp.probe_tc_gemm(A, B).astype(np.int64), A @ B.T)
