@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restri
 //   d0 = a0 a0 2^-64, d1 = 2 a0 a1 2^-64 (reduced to [0, 2p)), d2 = a1 a1 2^-64.
 // ext: [nct][2][NQB][N] after the column pass; dprod: [nct][3][NQB][N].
 template <int LOGR, int LOGC>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows_sq(const uint64_t* __restrict__ ext,
+__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_rows_sq(const uint64_t* __restrict__ ext,
                                                                  uint64_t* __restrict__ dprod, NttTabs T) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int ROWS = NTT_TILE >> LOGC, TPR = C / 16, B2 = LOGC - 4, PADC = C + C / 16;
