@@ -254,8 +254,10 @@ const char* hp_last_error(const hp_handle* h);
  * pointers are device memory; calls are stream-ordered. */
 
 /* Secret key s (int8 [N]) and relinearisation key (layout above), drawn with
- * Philox4x32-10 keyed by `seed` (see DESIGN: sampling).  Also loads the key
- * into the handle. */
+ * Philox4x32-10 keyed by `seed` with counter (coefficient, prime, object,
+ * domain): s ternary floor(3 w0 / 2^32) - 1, errors centred binomial with
+ * eta = 21, uniform residues floor(r m / 2^128).  Also loads the key into the
+ * handle. */
 int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk_out, uint64_t* relin_key_out, void* stream);
 
 /* Encrypt n_ct slot vectors (uint32 [n_ct][N], values < t): ciphertext i uses

@@ -104,7 +104,9 @@ int lt_coefficients(uint32_t* out);
 
 // Static noise estimate: how many successive squarings (each relinearised)
 // the parameters support with a positive invariant-noise budget, from the
-// standard heuristic growth bound (see DESIGN).  Used by hp_create.
+// heuristic growth bound (fresh budget log Q - log t - log N - 8 bits, log t +
+// log N + 2 bits per squaring, the key-switching noise bounding the budget
+// after the first), below the oracle's measured budgets.  Used by hp_create.
 int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t);
 
 }  // namespace hp

@@ -335,7 +335,8 @@ int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t
   for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
   double lt = log2((double)t);
   // fresh invariant-noise budget and the per-squaring cost, both on the
-  // conservative side of the oracle's measurements (DESIGN: noise model)
+  // conservative side of the oracle's measured budgets (e.g. 793 bits fresh,
+  // about 31 bits per squaring at N = 32768)
   double fresh = lq - lt - log_n - 8.0;
   double per = lt + log_n + 2.0;
   if (fresh <= 0) return 0;

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
 
 // ---- exact centred lift Q -> B (k_lift) with the conversion on the tensor cores ----
 // Same first-lift modes and residue outputs as k_lift; the auxiliary residues
-// come from one bf16 MMA per 128-coefficient tile with the operand B1 (the Q ->
+// come from one f16 MMA per 128-coefficient tile with the operand B1 (the Q ->
 // B conversion of the scale-and-round) and the correction table T1.
 constexpr size_t LFT_SMEM = (size_t)(1 + SRT_GROUPS) * SRT_OPER * 2 + TC_T1 * 8 + SRT_GROUPS * 8 + 32;
 
