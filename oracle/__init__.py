@@ -99,6 +99,7 @@ def _load():
         "orc_rotate": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, _u64p]),
         "orc_rotate_sum": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, _u64p]),
         "orc_mul_plain": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
+        "orc_between": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -396,6 +397,14 @@ class Oracle:
         rc = self.lib.orc_lt(self.h, _p(X, ctypes.c_uint64), _p(Y, ctypes.c_uint64), _p(out, ctypes.c_uint64))
         if rc != 0:
             raise RuntimeError("orc_lt failed (%d)" % rc)
+        return out
+
+    def between(self, x, lo: int, hi: int):
+        """BETWEEN: (1 - LT(x, lo)) (1 - LT(hi, x)) = [lo <= x <= hi] for constants lo, hi."""
+        X, out = _c(x, np.uint64), self._ct_out()
+        rc = self.lib.orc_between(self.h, _p(X, ctypes.c_uint64), lo, hi, _p(out, ctypes.c_uint64))
+        if rc != 0:
+            raise RuntimeError("orc_between failed (%d)" % rc)
         return out
 
     def square_chain(self, x, squarings: int):

@@ -1281,6 +1281,35 @@ int orc_linear(void* h, const uint64_t* cts, int n, const uint64_t* coef, uint64
   return 0;
 }
 // LT(x, y) = [x - y in {-(t-1)/2 .. -1}] by the schedule above (t = 65537)
+// v - x for a plaintext constant v: (Delta v - c0, -c1) mod Q
+static Ct ct_const_minus(const Ctx& c, const Ct& x, uint64_t v) {
+  Ct r;
+  r.c0.resize(c.N);
+  r.c1.resize(c.N);
+  for (int j = 0; j < c.N; ++j) {
+    r.c0[j] = mod_Q(c, big_neg(x.c0[j]));
+    r.c1[j] = mod_Q(c, big_neg(x.c1[j]));
+  }
+  r.c0[0] = mod_Q(c, big_add(r.c0[0], big_mul_u64(c.Delta, v)));
+  return r;
+}
+
+// BETWEEN (Sec. 4.2.2): the product of the two comparisons x >= lo and x <= hi,
+// (1 - LT(x, lo)) (1 - LT(hi, x)) with LT(x, lo) = f(x - lo) and
+// LT(hi, x) = f(hi - x), f the comparison polynomial of Eq. 4 (valid while
+// x, lo, hi lie in [0, (p-1)/2]).
+int orc_between(void* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk) return -2;
+  if (c.t != 65537 || lo >= c.t || hi >= c.t) return -1;
+  const std::vector<uint32_t>& hc = lt_coeffs(c);
+  Ct X = ct_from_rns(c, x);
+  Ct below = lt_eval(c, ct_sub_const(c, X, lo), hc);    // [x < lo]
+  Ct above = lt_eval(c, ct_const_minus(c, X, hi), hc);  // [hi < x]
+  ct_to_rns(c, ct_mul_relin(c, ct_one_minus(c, below), ct_one_minus(c, above)), out);
+  return 0;
+}
+
 int orc_lt(void* h, const uint64_t* x, const uint64_t* y, uint64_t* out) {
   Ctx& c = *(Ctx*)h;
   if (!c.have_rk) return -2;

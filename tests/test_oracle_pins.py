@@ -603,3 +603,18 @@ def test_join_closed_form_n16(orc16):
         assert np.array_equal(got, ref) and nb > 0, k
     semi = o.join(ca, cb, [], 3)
     assert np.array_equal(o.decrypt(semi[0, 0]), np.isin(akey, bkey[:3]).astype(np.uint32))
+
+
+def test_between_closed_form_n16(orc16):
+    """BETWEEN (Sec. 4.2.2) = (1 - LT(x, lo)) (1 - LT(hi, x)) decrypts to
+    [lo <= x <= hi] on 15-bit inputs, including both bounds, lo = hi and an
+    empty range."""
+    o = orc16
+    rng = np.random.default_rng(40)
+    x = rng.integers(0, (T - 1) // 2 + 1, o.N).astype(np.uint32)
+    x[:6] = [100, 200, 99, 201, 0, 32768]
+    cx = o.encrypt(x, 41, 0)
+    for lo, hi in [(100, 200), (0, 32768), (150, 150), (300, 200)]:
+        got, nb = o.decrypt(o.between(cx, lo, hi), with_noise=True)
+        assert np.array_equal(got, ((x >= lo) & (x <= hi)).astype(np.uint32)), (lo, hi)
+        assert nb > 0
