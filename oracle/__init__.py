@@ -400,7 +400,7 @@ class Oracle:
         return out
 
     def between(self, x, lo: int, hi: int):
-        """BETWEEN: (1 - LT(x, lo)) (1 - LT(hi, x)) = [lo <= x <= hi] for constants lo, hi."""
+        """BETWEEN: 1 - LT(x, lo) - LT(hi, x) = [lo <= x <= hi] for constants lo <= hi."""
         X, out = _c(x, np.uint64), self._ct_out()
         rc = self.lib.orc_between(self.h, _p(X, ctypes.c_uint64), lo, hi, _p(out, ctypes.c_uint64))
         if rc != 0:

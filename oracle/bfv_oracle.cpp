@@ -1294,19 +1294,21 @@ static Ct ct_const_minus(const Ctx& c, const Ct& x, uint64_t v) {
   return r;
 }
 
-// BETWEEN (Sec. 4.2.2): the product of the two comparisons x >= lo and x <= hi,
-// (1 - LT(x, lo)) (1 - LT(hi, x)) with LT(x, lo) = f(x - lo) and
-// LT(hi, x) = f(hi - x), f the comparison polynomial of Eq. 4 (valid while
-// x, lo, hi lie in [0, (p-1)/2]).
+// BETWEEN (Sec. 4.2.2): the combination of the two comparisons x >= lo and
+// x <= hi.  With a = LT(x, lo) = f(x - lo) and b = LT(hi, x) = f(hi - x), f the
+// comparison polynomial of Eq. 4 (valid while x, lo, hi lie in [0, (p-1)/2]),
+// the product (1 - a)(1 - b) equals 1 - a - b for lo <= hi, because x < lo
+// and x > hi exclude each other; the difference form is evaluated, one level
+// shallower than the product.  Empty ranges (lo > hi) are rejected.
 int orc_between(void* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* out) {
   Ctx& c = *(Ctx*)h;
   if (!c.have_rk) return -2;
-  if (c.t != 65537 || lo >= c.t || hi >= c.t) return -1;
+  if (c.t != 65537 || lo >= c.t || hi >= c.t || lo > hi) return -1;
   const std::vector<uint32_t>& hc = lt_coeffs(c);
   Ct X = ct_from_rns(c, x);
   Ct below = lt_eval(c, ct_sub_const(c, X, lo), hc);    // [x < lo]
   Ct above = lt_eval(c, ct_const_minus(c, X, hi), hc);  // [hi < x]
-  ct_to_rns(c, ct_mul_relin(c, ct_one_minus(c, below), ct_one_minus(c, above)), out);
+  ct_to_rns(c, ct_sub(c, ct_one_minus(c, above), below), out);  // (1 - b) - a
   return 0;
 }
 

@@ -606,15 +606,21 @@ def test_join_closed_form_n16(orc16):
 
 
 def test_between_closed_form_n16(orc16):
-    """BETWEEN (Sec. 4.2.2) = (1 - LT(x, lo)) (1 - LT(hi, x)) decrypts to
-    [lo <= x <= hi] on 15-bit inputs, including both bounds, lo = hi and an
-    empty range."""
+    """BETWEEN (Sec. 4.2.2) decrypts to [lo <= x <= hi] on 15-bit inputs,
+    including both bounds and lo = hi.  The difference form 1 - LT(x, lo) -
+    LT(hi, x) equals the product (1 - LT(x, lo)) (1 - LT(hi, x)) slot by slot,
+    checked here after decryption; an empty range (lo > hi) is rejected."""
     o = orc16
     rng = np.random.default_rng(40)
     x = rng.integers(0, (T - 1) // 2 + 1, o.N).astype(np.uint32)
     x[:6] = [100, 200, 99, 201, 0, 32768]
     cx = o.encrypt(x, 41, 0)
-    for lo, hi in [(100, 200), (0, 32768), (150, 150), (300, 200)]:
+    for lo, hi in [(100, 200), (0, 32768), (150, 150)]:
         got, nb = o.decrypt(o.between(cx, lo, hi), with_noise=True)
         assert np.array_equal(got, ((x >= lo) & (x <= hi)).astype(np.uint32)), (lo, hi)
         assert nb > 0
+        a = o.decrypt(o.lt(cx, o.encrypt(np.full(o.N, lo, dtype=np.uint32), 42, 1)))
+        b = o.decrypt(o.lt(o.encrypt(np.full(o.N, hi, dtype=np.uint32), 42, 2), cx))
+        assert np.array_equal(got, ((1 - a.astype(np.int64)) * (1 - b.astype(np.int64)) % T).astype(np.uint32))
+    with pytest.raises(RuntimeError):
+        o.between(cx, 300, 200)
