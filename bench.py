@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhp", choices=["libhp", "reference"])
-    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "in", "sum", "rotsum", "join"])
+    ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "between", "in", "sum", "rotsum", "join"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +51,10 @@ def parse():
 
 
 def workload(cfg: str):
+    if cfg == "between":
+        return dict(n_ct=64, op="between", desc="x BETWEEN 1000 AND 20000 (Sec. 4.2.2: 1 - LT(x, lo) - LT(hi, x)): "
+                    "2^21 slots = 64 BFV ciphertexts, x in [0, 2^15], N=32768, L=15, p=65537; two LT evaluations "
+                    "(1022 multiplications) per ciphertext, bit-exact")
     if cfg == "join":
         return dict(n_ct=64, op="join", n_rows=16, desc="equi-join A.key = B.key (Sec. 4.2.2, Extract + Broadcast): "
                     "A = 2^21 rows (64 BFV ciphertexts), 16 B rows with 2 attributes; 1024 EQ chains, 2048 products, "
@@ -243,7 +247,8 @@ def run_libhp(args):
         ctx.autotune()
     N = ctx.N
     # inputs: rank r encrypts its own share (weak scaling, no exchange)
-    x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank), value_bits=15 if wl["op"] == "lt" else 16)
+    x, y = eq_pair_columns(n_ct * N, seed=rank_seed(SEED_DATA, rank),
+                           value_bits=15 if wl["op"] in ("lt", "between") else 16)
     const_val = 4242
     if wl["op"] == "sum":  # WHERE x = c holds in about a quarter of the rows; y is the summed column
         x[np.random.default_rng(rank_seed(SEED_DATA + 1, rank)).random(n_ct * N) < 0.25] = const_val
@@ -277,6 +282,8 @@ def run_libhp(args):
             ctx.run(hp.HP_LT, cx, cy, 0, out=out, stream=stream)
         elif wl["op"] == "in":
             ctx.eq_fanout(cx, in_consts, masks=False, in_set=out, stream=stream)
+        elif wl["op"] == "between":
+            ctx.between(cx, 1000, 20000, out=out, stream=stream)
         elif wl["op"] == "sum":
             ctx.run(hp.HP_SELECT, cx, cy, const_val, out=out, stream=stream)
             n = ctx.launch_count()
@@ -367,6 +374,8 @@ def run_libhp(args):
             ref = xs < y[c * N:(c + 1) * N]
         elif wl["op"] == "in":
             ref = np.isin(xs, in_consts)
+        elif wl["op"] == "between":
+            ref = (xs >= 1000) & (xs <= 20000)
         else:
             ref = (xs == y[c * N:(c + 1) * N]) if cy is not None else (xs == const_val)
         assert np.array_equal(dec[k], ref.astype(np.uint32)), "EQ result wrong in benchmark run"
@@ -420,7 +429,7 @@ def run_libhp(args):
             "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
 
     # ---- end to end through the public API with pinned host buffers ----
-    if not args.no_e2e and wl["op"] not in ("lt", "in", "sum", "rotsum", "join"):
+    if not args.no_e2e and wl["op"] not in ("lt", "between", "in", "sum", "rotsum", "join"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1 and wl["op"] not in ("rotsum", "join"):

@@ -161,6 +161,19 @@ int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst,
  * tile) for the process.  Synchronous. */
 int hp_autotune(hp_handle* h, size_t* best_tile);
 
+/* BETWEEN (Sec. 4.2.2): out[c] = [lo <= x <= hi] slot-wise for plaintext bounds
+ * lo <= hi.  The paper's product of the two comparisons, (1 - LT(x, lo))
+ * (1 - LT(hi, x)), equals 1 - LT(x, lo) - LT(hi, x) because x < lo and x > hi
+ * exclude each other; that form is computed: two LT evaluations (511
+ * multiplications each, the Eq. 4 polynomial on x - lo and hi - x, see HP_LT)
+ * and no product, so BETWEEN has LT's depth (the product's extra level is more
+ * than the noise budget leaves at N = 32768).  Exact when x, lo, hi lie in
+ * [0, (t-1)/2]; bounds outside that range or lo > hi give HP_ERR_ARG.  x, out:
+ * n_ct device ciphertexts; tiles of up to 8 ciphertexts share the LT
+ * workspace.  Needs t = 65537 and the relinearisation key. */
+int hp_between(hp_handle* h, const uint64_t* ct_x, size_t n_ct, uint64_t lo, uint64_t hi, uint64_t* ct_out,
+               void* stream);
+
 /* One column against many constants (device memory, n_ct ciphertexts of x,
  * n_const constants in host memory, each < t):
  *   GROUP BY (Sec. 4.2.2): masks[k][c] = EQ(x[c], consts[k])   (masks: [n_const][n_ct] ciphertexts)

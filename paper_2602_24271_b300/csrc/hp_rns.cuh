@@ -311,6 +311,20 @@ __global__ void k_ct_addsub(const uint64_t* __restrict__ a, const uint64_t* __re
   out[w] = subtract ? sub_mod(a[w], b[w], q) : add_mod(a[w], b[w], q);
 }
 
+// out = x - (Delta v, 0), or (Delta v, 0) - x when `from_const` (BETWEEN's
+// differences against plaintext bounds); v < t
+__global__ void k_ct_const_diff(const uint64_t* __restrict__ x, uint64_t v, int from_const, uint64_t* __restrict__ out,
+                                int logN, size_t nwords) {
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwords) return;
+  const size_t poly = w >> logN;
+  const int i = (int)(poly % L), comp = (int)((poly / L) & 1);
+  const uint64_t q = cK.p[i];
+  uint64_t r = x[w];
+  if (comp == 0 && (w & ((1u << logN) - 1)) == 0) r = sub_mod(r, mul_shoup(v, cK.delta[i], cK.delta_s[i], q), q);
+  out[w] = from_const ? sub_mod(0, r, q) : r;
+}
+
 // out += a (IN accumulation of one tile of masks into the running sum; out
 // and a are distinct buffers, out is read and written in place)
 __global__ void k_ct_acc(uint64_t* out, const uint64_t* __restrict__ a, int logN, size_t nwords) {

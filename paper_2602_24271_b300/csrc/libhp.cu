@@ -394,17 +394,31 @@ static void ct_addsub(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64
   h->launches += 1;
 }
 
-static void run_lt_tile(hp_handle* h, const uint64_t* x, const uint64_t* y, uint64_t* out, int b, cudaStream_t s) {
+// LT workspace of a tile: B_1 .. B_255, G_1 .. G_128, 8 inner sums, then the
+// ciphertext arrays z (the difference), acc, tmp and r (BETWEEN's first result)
+struct LtWs {
+  uint64_t *Bp, *Gp, *Hp, *z, *acc, *tmp, *r;
+};
+static LtWs lt_ws(hp_handle* h) {
+  const size_t T = h->lt_tile * words_ct(h);
+  LtWs w;
+  w.Bp = h->ltws;
+  w.Gp = w.Bp + 255 * T;
+  w.Hp = w.Gp + 128 * T;
+  w.z = w.Hp + LT_J * T;
+  w.acc = w.z + T;
+  w.tmp = w.acc + T;
+  w.r = w.tmp + T;
+  return w;
+}
+
+// f(z) of Eq. 4 for the tile's differences already in the workspace's z.
+static void run_lt_z(hp_handle* h, uint64_t* out, int b, cudaStream_t s) {
   const size_t W = words_ct(h), bw = (size_t)b * W, T = h->lt_tile * W;
-  uint64_t* Bp = h->ltws;              // B_1 .. B_255
-  uint64_t* Gp = Bp + 255 * T;         // G_1 .. G_128
-  uint64_t* Hp = Gp + 128 * T;         // 8 inner sums
-  uint64_t* z = Hp + LT_J * T;
-  uint64_t* acc = z + T;
-  uint64_t* tmp = acc + T;
+  const LtWs ws = lt_ws(h);
+  uint64_t *Bp = ws.Bp, *Gp = ws.Gp, *Hp = ws.Hp, *z = ws.z, *acc = ws.acc, *tmp = ws.tmp;
   auto B = [&](int i) { return Bp + (size_t)(i - 1) * T; };
   auto G = [&](int j) { return Gp + (size_t)(j - 1) * T; };
-  ct_addsub(h, x, y, z, 1, b, s);
   hsquare(h, z, B(1), b, s);
   for (int i = 2; i < 256; ++i) {
     if (i % 2 == 0)
@@ -445,10 +459,32 @@ static void run_lt_tile(hp_handle* h, const uint64_t* x, const uint64_t* y, uint
   h->launches += 1;
 }
 
+static void run_lt_tile(hp_handle* h, const uint64_t* x, const uint64_t* y, uint64_t* out, int b, cudaStream_t s) {
+  ct_addsub(h, x, y, lt_ws(h).z, 1, b, s);
+  run_lt_z(h, out, b, s);
+}
+
+// BETWEEN on a tile: (1 - f(hi - x)) - f(x - lo) = [lo <= x <= hi] for lo <= hi
+// (the product (1 - a)(1 - b) of the two comparisons, since a b = 0).
+static void run_between_tile(hp_handle* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* out, int b,
+                             cudaStream_t s) {
+  const LtWs ws = lt_ws(h);
+  const size_t bw = (size_t)b * words_ct(h);
+  k_ct_const_diff<<<ew_blocks(bw), EW_THREADS, 0, s>>>(x, lo, 0, ws.z, h->logn, bw);
+  h->launches += 1;
+  run_lt_z(h, ws.r, b, s);  // [x < lo]
+  k_ct_const_diff<<<ew_blocks(bw), EW_THREADS, 0, s>>>(x, hi, 1, ws.z, h->logn, bw);
+  h->launches += 1;
+  run_lt_z(h, out, b, s);  // [hi < x]
+  k_one_minus<<<ew_blocks(bw), EW_THREADS, 0, s>>>(out, ws.acc, h->logn, b);
+  h->launches += 1;
+  ct_addsub(h, ws.acc, ws.r, out, 1, b, s);
+}
+
 static int lt_prepare(hp_handle* h) {
   if (h->ltws) return HP_OK;
   h->lt_tile = h->tile < 8 ? h->tile : 8;
-  const size_t words = (size_t)(255 + 128 + LT_J + 3) * h->lt_tile * words_ct(h);
+  const size_t words = (size_t)(255 + 128 + LT_J + 4) * h->lt_tile * words_ct(h);
   if (cudaMalloc(&h->ltws, words * sizeof(uint64_t)) != cudaSuccess) {
     cudaGetLastError();
     h->ltws = nullptr;
@@ -1303,6 +1339,34 @@ int hp_join(hp_handle* h, const uint64_t* a_key, size_t n_a, const uint64_t* b_k
   cudaFreeAsync(BC, s);
   h->launches += launches;
   CU(h, cudaGetLastError());
+  return HP_OK;
+}
+
+// BETWEEN (Sec. 4.2.2) against plaintext bounds: out = [lo <= x <= hi].
+int hp_between(hp_handle* h, const uint64_t* x, size_t n_ct, uint64_t lo, uint64_t hi, uint64_t* out, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  h->launches = 0;
+  if (n_ct == 0) return HP_OK;
+  if (!x || !out) HP_FAIL(h, HP_ERR_ARG, "null ciphertext pointer");
+  if (h->t != 65537) HP_FAIL(h, HP_ERR_UNSUPPORTED, "BETWEEN needs t = 65537");
+  if (lo > (h->t - 1) / 2 || hi > (h->t - 1) / 2) HP_FAIL(h, HP_ERR_ARG, "bounds must be in [0, (t-1)/2]");
+  if (lo > hi) HP_FAIL(h, HP_ERR_ARG, "empty range: lo > hi");
+  if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
+  if (18 > supported_depth(h->logn, h->q, L, h->P, h->t)) HP_FAIL(h, HP_ERR_DEPTH, "depth 18 exceeds the budget");
+  if (!is_device_ptr(x) || !is_device_ptr(out)) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be device memory");
+  if (((uintptr_t)x | (uintptr_t)out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
+  if (int rc = lt_prepare(h)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t W = words_ct(h);
+  uint64_t total = 0;
+  for (size_t c0 = 0; c0 < n_ct; c0 += h->lt_tile) {
+    const int b = (int)((n_ct - c0 < h->lt_tile) ? n_ct - c0 : h->lt_tile);
+    h->launches = 0;
+    run_between_tile(h, x + c0 * W, lo, hi, out + c0 * W, b, s);
+    total += h->launches;
+    CU(h, cudaGetLastError());
+  }
+  h->launches = total;
   return HP_OK;
 }
 

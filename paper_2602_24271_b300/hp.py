@@ -43,7 +43,7 @@ EXPORTED = [
     "hp_check_status", "hp_profile", "hp_profile_read", "hp_probe_peak", "hp_tile_size",
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
-    "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm", "hp_probe_tc_timeout",
+    "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm", "hp_probe_tc_timeout", "hp_between",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -128,6 +128,7 @@ def load():
         "hp_ct_sum": (ctypes.c_int, [H, P64, SZ, SZ, P64, V]),
         "hp_probe_tc_gemm": (ctypes.c_int, [V, V, V, ctypes.c_int, ctypes.c_int]),
         "hp_probe_tc_timeout": (ctypes.c_int, [ctypes.c_uint32]),
+        "hp_between": (ctypes.c_int, [H, P64, SZ, ctypes.c_uint64, ctypes.c_uint64, P64, V]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
     }
@@ -258,6 +259,14 @@ class Context:
             out = self.ct_empty(n)
         _check(self.lib.hp_run_batched(self.h, op, arr, len(instances), _ptr(x), _ptr(y), _ptr(out), n,
                                        _stream(stream)), self.h)
+        return out
+
+    def between(self, x, lo: int, hi: int, out=None, stream=None):
+        """[lo <= x <= hi] slot-wise for plaintext bounds (device ciphertexts)."""
+        n = x.shape[0]
+        if out is None:
+            out = self.ct_empty(n)
+        _check(self.lib.hp_between(self.h, _ptr(x), n, lo, hi, _ptr(out), _stream(stream)), self.h)
         return out
 
     def eq_fanout(self, x, consts, masks=True, in_set=True, stream=None):

@@ -25,7 +25,10 @@ def read_golden_kv(name: str) -> dict:
             if not line:
                 continue
             k, v = [s.strip() for s in line.split("=", 1)]
-            out[k] = float(v) if "." in v else int(v)
+            try:
+                out[k] = float(v) if "." in v else int(v)
+            except ValueError:
+                out[k] = v  # text values (digests)
     return out
 
 
