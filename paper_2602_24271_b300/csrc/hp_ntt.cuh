@@ -14,6 +14,15 @@
 // load per butterfly group), then the tile is exchanged once through shared
 // memory for the remaining stages of the pass.
 //
+// Twiddle tables.  Entry j of a prime's table holds psi^{brv(j)} (inverse:
+// psi^{-brv(j)}) and its Shoup companion; stage s reads entries [2^s, 2^{s+1}).
+// The stages of the row pass's second half (s = LOGR + 4 + l, 0 <= l < LOGC - 4)
+// give every thread its own twiddles: row `row`, column group g < 16 and
+// butterfly group g' < 2^l need entry 2^s + row 2^{4+l} + g 2^l + g'.  Those
+// entries are stored transposed within each row's range, at
+// 2^s + row 2^{4+l} + g' 16 + g, so that the threads of a row (consecutive g)
+// read consecutive entries.  Entries of the earlier stages keep their order.
+//
 // Ranges.  The twiddle product uses a Shoup quotient from three 32-bit partial
 // products, which is at most 2 below the exact one, so W Y mod p is returned
 // in [0, 4p) for any 64-bit Y.  Forward (CT) butterflies then need no
@@ -112,6 +121,31 @@ HPD void fwd_block(uint64_t (&x)[1 << A], uint32_t base, int s0, int logN, const
   }
 }
 
+// The same stages for the second half of the row pass (s0 = logR + 4): the
+// elements are 2^A consecutive columns of group `grp` of row `row`, and the
+// twiddles come from the transposed layout described above.
+template <int A>
+HPD void fwd_block_tr(uint64_t (&x)[1 << A], uint32_t row, uint32_t grp, int s0, const ulonglong2* __restrict__ tw,
+                      const PForm& f) {
+  const uint64_t p4 = 4 * f.p;
+#pragma unroll
+  for (int l = 0; l < A; ++l) {
+    const uint32_t tb = (1u << (s0 + l)) + (row << (4 + l)) + grp;
+#pragma unroll
+    for (int g = 0; g < (1 << l); ++g) {
+      const ulonglong2 W = __ldg(tw + tb + (g << 4));
+#pragma unroll
+      for (int o = 0; o < (1 << (A - l - 1)); ++o) {
+        const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
+        const uint64_t X = x[u];
+        const uint64_t V = mul_shoup4(x[v], W.x, W.y, f);
+        x[u] = X + V;
+        x[v] = X - V + p4;
+      }
+    }
+  }
+}
+
 // Inverse stages s0 + A - 1 .. s0 on the same element set; values in [0, 4p).
 template <int A>
 HPD void inv_block(uint64_t (&x)[1 << A], uint32_t base, int s0, int logN, const ulonglong2* __restrict__ itw,
@@ -124,6 +158,28 @@ HPD void inv_block(uint64_t (&x)[1 << A], uint32_t base, int s0, int logN, const
 #pragma unroll
     for (int g = 0; g < (1 << l); ++g) {
       const ulonglong2 W = __ldg(itw + tb + g);
+#pragma unroll
+      for (int o = 0; o < (1 << (A - l - 1)); ++o) {
+        const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
+        const uint64_t X = x[u], Y = x[v];
+        x[u] = csub(X + Y, p4);
+        x[v] = mul_shoup4(X - Y + p4, W.x, W.y, f);
+      }
+    }
+  }
+}
+
+// inv_block for the second half of the row pass (transposed twiddles, as fwd_block_tr)
+template <int A>
+HPD void inv_block_tr(uint64_t (&x)[1 << A], uint32_t row, uint32_t grp, int s0, const ulonglong2* __restrict__ itw,
+                      const PForm& f) {
+  const uint64_t p4 = 4 * f.p;
+#pragma unroll
+  for (int l = A - 1; l >= 0; --l) {
+    const uint32_t tb = (1u << (s0 + l)) + (row << (4 + l)) + grp;
+#pragma unroll
+    for (int g = 0; g < (1 << l); ++g) {
+      const ulonglong2 W = __ldg(itw + tb + (g << 4));
 #pragma unroll
       for (int o = 0; o < (1 << (A - l - 1)); ++o) {
         const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
@@ -218,7 +274,7 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restri
       const int kk = (g << B2) + u;
       y[u] = s[r * PADC + kk + (kk >> 4)];
     }
-    fwd_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, tw, f);
+    fwd_block_tr<B2>(y, (uint32_t)row, (uint32_t)g, LOGR + 4, tw, f);
 #pragma unroll
     for (int u = 0; u < (1 << B2); ++u) {
       const int kk = (g << B2) + u;
@@ -276,7 +332,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_rows_sq(const uint64
         const int kk = (g << B2) + u;
         y[u] = s[r * PADC + kk + (kk >> 4)];
       }
-      fwd_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, tw, f);
+      fwd_block_tr<B2>(y, (uint32_t)row, (uint32_t)g, LOGR + 4, tw, f);
 #pragma unroll
       for (int u = 0; u < (1 << B2); ++u) {
         const int kk = (g << B2) + u;
@@ -333,7 +389,7 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(uint64_t* __restri
       const int kk = (g << B2) + u;
       y[u] = s[r * PADC + kk + (kk >> 4)];
     }
-    inv_block<B2>(y, (uint32_t)(row * C + (g << B2)), LOGR + 4, logN, itw, f);
+    inv_block_tr<B2>(y, (uint32_t)row, (uint32_t)g, LOGR + 4, itw, f);
 #pragma unroll
     for (int u = 0; u < (1 << B2); ++u) {
       const int kk = (g << B2) + u;

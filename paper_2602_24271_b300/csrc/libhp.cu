@@ -520,6 +520,21 @@ static int build_tc(hp_handle* h) {
   return HP_OK;
 }
 
+// Position of twiddle entry j in the device table: entries of the stages
+// s >= logR + 4 (the second half of the row pass) are transposed within each
+// row's range of 2^{4+l} entries, l = s - logR - 4: entry 2^s + row 2^{4+l} +
+// g 2^l + g' (column group g < 16, butterfly group g' < 2^l) is stored at
+// 2^s + row 2^{4+l} + g' 16 + g, the order in which a row's threads read them.
+static size_t row_pass_twiddle_pos(size_t j, int logR) {
+  if (j < ((size_t)1 << (logR + 4))) return j;
+  int s = 0;
+  while ((j >> (s + 1)) != 0) ++s;
+  const int l = s - logR - 4;
+  const size_t off = j - ((size_t)1 << s), row = off >> (4 + l), w = off & (((size_t)1 << (4 + l)) - 1);
+  const size_t g = w >> l, gp = w & (((size_t)1 << l) - 1);
+  return ((size_t)1 << s) + (row << (4 + l)) + (gp << 4) + g;
+}
+
 static int build_tables(hp_handle* h) {
   const int N = h->N;
   std::vector<ulonglong2> tw((size_t)NPRIME * N), itw(tw.size());
@@ -535,7 +550,7 @@ static int build_tables(hp_handle* h) {
       ipw[e] = h_mulmod(ipw[e - 1], ipsi, p);
     }
     for (int j = 0; j < N; ++j) {
-      size_t o = (size_t)id * N + j;
+      size_t o = (size_t)id * N + row_pass_twiddle_pos(j, h->logR);
       const uint64_t w = pw[brv(j, h->logn)], iw = ipw[brv(j, h->logn)];
       tw[o] = make_ulonglong2(w, h_shoup(w, p));
       itw[o] = make_ulonglong2(iw, h_shoup(iw, p));
