@@ -56,9 +56,12 @@ struct PolyMap {
 struct NttTabs {
   const ulonglong2* tw;   // [NPRIME][N] (psi^{brv(j)}, Shoup companion)
   const ulonglong2* itw;  // [NPRIME][N] (psi^{-brv(j)}, Shoup companion)
-  const uint64_t* scale;  // [NSCALE][NPRIME][2] (value, Shoup)
+  // [NSCALE][NPRIME][4]: the output scale c and c W1 (W1 = psi^{-brv(1)}, the
+  // twiddle of the last inverse stage), each with its Shoup companion
+  const uint64_t* scale;
 };
-enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, NSCALE = 3 };
+// c = N^{-1}; t N^{-1} 2^64; N^{-1} 2^64; N^{-1} P^{-1} (data primes, mod-down)
+enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3, NSCALE = 4 };
 
 // Optional fused load of the forward column pass: polynomial (b, g, j) of the
 // key-switching batch is digit g of ciphertext b reduced modulo target prime
@@ -188,6 +191,38 @@ HPD void inv_block_tr(uint64_t (&x)[1 << A], uint32_t row, uint32_t grp, int s0,
         x[v] = mul_shoup4(X - Y + p4, W.x, W.y, f);
       }
     }
+  }
+}
+
+// Inverse stages A - 1 .. 0 of the column pass (s0 = 0) with the output scale
+// c folded into stage 0, whose single twiddle is W1: (X + Y, W1 (X - Y)) becomes
+// (c (X + Y), c W1 (X - Y)); sc = (c, Shoup, c W1, Shoup).  Values in [0, 4p).
+template <int A>
+HPD void inv_block_scaled(uint64_t (&x)[1 << A], uint32_t base, int logN, const ulonglong2* __restrict__ itw,
+                          const PForm& f, const uint64_t* __restrict__ sc) {
+  const uint64_t p4 = 4 * f.p;
+#pragma unroll
+  for (int l = A - 1; l >= 1; --l) {
+    const uint32_t tb = (1u << l) + (base >> (logN - l));
+#pragma unroll
+    for (int g = 0; g < (1 << l); ++g) {
+      const ulonglong2 W = __ldg(itw + tb + g);
+#pragma unroll
+      for (int o = 0; o < (1 << (A - l - 1)); ++o) {
+        const int u = (g << (A - l)) + o, v = u + (1 << (A - l - 1));
+        const uint64_t X = x[u], Y = x[v];
+        x[u] = csub(X + Y, p4);
+        x[v] = mul_shoup4(X - Y + p4, W.x, W.y, f);
+      }
+    }
+  }
+  const uint64_t c = __ldg(sc), cs = __ldg(sc + 1), cw = __ldg(sc + 2), cws = __ldg(sc + 3);
+#pragma unroll
+  for (int u = 0; u < (1 << (A - 1)); ++u) {
+    const int v = u + (1 << (A - 1));
+    const uint64_t X = x[u], Y = x[v];
+    x[u] = mul_shoup4(X + Y, c, cs, f);
+    x[v] = mul_shoup4(X - Y + p4, cw, cws, f);
   }
 }
 
@@ -423,7 +458,7 @@ struct ModDown {
   int pstride, poff;
 };
 template <int LOGR, int LOGC, bool MD>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
                                                               int scale_mode, ModDown md) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
@@ -450,15 +485,12 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restri
   uint64_t x[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) x[u] = s[(rb + u * RB) * COLS + k];
-  inv_block<4>(x, (uint32_t)(rb * C + k0 + k), 0, logN, itw, f);
-  const uint64_t* sc = T.scale + ((size_t)scale_mode * NPRIME + id) * 2;
-  const uint64_t w = sc[0], wp = sc[1];
+  // scaled by c (MD: N^{-1} P^{-1}, so that x holds u_i P^{-1})
+  inv_block_scaled<4>(x, (uint32_t)(rb * C + k0 + k), logN, itw, f,
+                      T.scale + ((size_t)(MD ? SCALE_NINV_PINV : scale_mode) * NPRIME + id) * 4);
   if (!MD) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const uint64_t y = mul_shoup4(x[u], w, wp, f);  // [0, 4p)
-      a[(size_t)(rb + u * RB) * C + k0 + k] = csub(csub(y, 2 * p), p);
-    }
+    for (int u = 0; u < 16; ++u) a[(size_t)(rb + u * RB) * C + k0 + k] = csub(csub(x[u], 2 * p), p);
   } else {
     const size_t bc = (size_t)(y0 / L);
     const int i = y0 % L, comp = (int)(bc & 1);
@@ -469,11 +501,11 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t* __restri
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int n = (rb + u * RB) * C + k0 + k;
-      const uint64_t ui = csub(csub(mul_shoup4(x[u], w, wp, f), 2 * p), p);
+      const uint64_t uiP = csub(csub(x[u], 2 * p), p);  // u_i P^{-1}
       const uint64_t up = uP[n];
-      const uint64_t diff = up <= (P - 1) / 2 ? sub_mod(ui, csub(csub(up, 2 * p), p), p)
-                                              : add_mod(ui, csub(csub(P - up, 2 * p), p), p);
-      uint64_t r = add_mod(wv[n], mul_shoup(diff, cK.Pinv[i], cK.Pinv_s[i], p), p);
+      const bool low = up <= (P - 1) / 2;  // [u_P] = up or up - P
+      const uint64_t m = mul_shoup(csub(csub(low ? up : P - up, 2 * p), p), cK.Pinv[i], cK.Pinv_s[i], p);
+      uint64_t r = add_mod(wv[n], low ? sub_mod(uiP, m, p) : add_mod(uiP, m, p), p);
       if (md.one_minus) {
         r = sub_mod(0, r, p);
         if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], p);

@@ -30,7 +30,7 @@ struct hp_handle {
   uint32_t max_depth = 0;
   Consts C;
   int device = 0;
-  // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][2]
+  // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][4]
   ulonglong2 *tw = nullptr, *itw = nullptr;  // (value, Shoup) pairs
   uint64_t* scale = nullptr;
   // relinearisation key, NTT domain, Montgomery form: [NDIG][2][NKS][N]
@@ -538,7 +538,7 @@ static size_t row_pass_twiddle_pos(size_t j, int logR) {
 static int build_tables(hp_handle* h) {
   const int N = h->N;
   std::vector<ulonglong2> tw((size_t)NPRIME * N), itw(tw.size());
-  std::vector<uint64_t> sc((size_t)NSCALE * NPRIME * 2);
+  std::vector<uint64_t> sc((size_t)NSCALE * NPRIME * 4);
   std::vector<uint64_t> pw(N), ipw(N);
   for (int id = 0; id < NPRIME; ++id) {
     const uint64_t p = h->C.p[id];
@@ -557,10 +557,17 @@ static int build_tables(hp_handle* h) {
     }
     const uint64_t ninv = h_invmod((uint64_t)N % p, p);
     const uint64_t r64 = (uint64_t)(((unsigned __int128)1 << 64) % p);
-    const uint64_t vals[NSCALE] = {ninv, h_mulmod(h_mulmod(h->t % p, ninv, p), r64, p), h_mulmod(ninv, r64, p)};
+    // N^{-1} P^{-1} is used for the data primes only (the mod-down)
+    const uint64_t vals[NSCALE] = {ninv, h_mulmod(h_mulmod(h->t % p, ninv, p), r64, p), h_mulmod(ninv, r64, p),
+                                   id < L ? h_mulmod(ninv, h->C.Pinv[id], p) : ninv};
+    const uint64_t w1 = ipw[brv(1, h->logn)];  // the last inverse stage's twiddle
     for (int m = 0; m < NSCALE; ++m) {
-      sc[((size_t)m * NPRIME + id) * 2 + 0] = vals[m];
-      sc[((size_t)m * NPRIME + id) * 2 + 1] = h_shoup(vals[m], p);
+      const uint64_t cw = h_mulmod(vals[m], w1, p);
+      uint64_t* e = &sc[((size_t)m * NPRIME + id) * 4];
+      e[0] = vals[m];
+      e[1] = h_shoup(vals[m], p);
+      e[2] = cw;
+      e[3] = h_shoup(cw, p);
     }
   }
   size_t tb = tw.size() * sizeof(ulonglong2);
