@@ -152,18 +152,20 @@ def source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
+def load_traffic(kernel: str, tile: int):
     """dram bytes per launch for `kernel` from the committed ncu counter summary,
-    or None if the summary is missing or was taken on different kernel sources."""
+    scaled from the summary's tile to `tile` ciphertexts per launch (a transform
+    launch's traffic is proportional to its polynomials), or None if the summary
+    is missing or was taken on different kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_counters.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     k = d.get("kernels", {}).get(kernel)
-    if not k or k.get("source_hash") != source_hash(kernel):
+    if not k or k.get("source_hash") != source_hash(kernel) or not d.get("tile_ct"):
         return None
-    return k.get("dram_bytes_per_launch_full")
+    return k.get("dram_bytes_per_launch_full") * tile / d["tile_ct"]
 
 
 # ---------------------------------------------------------------------------
@@ -416,7 +418,7 @@ def run_libhp(args):
         roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
     roof["probe_butterfly_per_s"] = hp.probe_peak(0)
     roof["probe_mac_per_s"] = hp.probe_peak(1)
-    roof["traffic"] = load_traffic(kernel)
+    roof["traffic"] = load_traffic(kernel, ctx_tile(ctx))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
