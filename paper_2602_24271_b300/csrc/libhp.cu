@@ -681,7 +681,8 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
   if ((rc = build_tc(h)) != HP_OK) return fail(rc);
   size_t per = ws_words_per_ct(h->N) * sizeof(uint64_t);
-  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)5 << 30) / per);  // ~5 GB of workspace
+  // default: about 11 GB of workspace, i.e. the largest tile (64 ciphertexts at N = 32768)
+  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)11 << 30) / per);
   if (h->tile < 1) h->tile = 1;
   if (h->tile > 64) h->tile = 64;
   const size_t T = h->tile, N = h->N;
