@@ -247,13 +247,25 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restri
     const int b = poly / (NDIG * NKS), g = (poly / NKS) % NDIG, j = poly % NKS;
     const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g * DIGIT_PRIMES) * N;
     const uint64_t c1 = cK.dig1[g][j], c1s = cK.dig1_s[g][j], c2 = cK.dig2[g][j], c2s = cK.dig2_s[g][j];
+    if (j == DIGIT_PRIMES * g) {  // the digit's own first prime: the value is r0 (canonical)
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
-      // r0 < 2p (primes within a factor 2) and two products in [0, 4p): sum < 10p
-      uint64_t v = src[off] + mul_shoup4(src[N + off], c1, c1s, f) + mul_shoup4(src[2 * N + off], c2, c2s, f);
-      v = csub(csub(v, 8 * p), 4 * p);
-      x[u] = csub(csub(v, 2 * p), p);
+      for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + k0 + k];
+    } else if (j == DIGIT_PRIMES * g + 1) {  // [q_3g q_3g+1] = 0 here: no t2 term
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
+        const uint64_t v = csub(src[off] + mul_shoup4(src[N + off], c1, c1s, f), 4 * p);  // < 6p, then < 4p
+        x[u] = csub(csub(v, 2 * p), p);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
+        // r0 < 2p (primes within a factor 2) and two products in [0, 4p): sum < 10p
+        uint64_t v = src[off] + mul_shoup4(src[N + off], c1, c1s, f) + mul_shoup4(src[2 * N + off], c2, c2s, f);
+        v = csub(csub(v, 8 * p), 4 * p);
+        x[u] = csub(csub(v, 2 * p), p);
+      }
     }
   } else {
 #pragma unroll
