@@ -3,17 +3,32 @@
 the constant form at 2^28 slots (8192 ciphertexts).  Every slot of every
 result is checked against the closed form [x == y] after GPU decryption (whose
 own parity with the oracle is tested at N = 4096 and again here on samples),
-and sampled ciphertexts are compared with the oracle bit for bit."""
+and 16 seeded sampled ciphertexts of each workload (the first and the last
+among them) are compared with the oracle bit for bit; the oracle evaluates the
+samples in parallel processes on the host's cores (one EQ at N = 32768 is
+about half a minute of single-threaded oracle time)."""
 import numpy as np
 import pytest
 
 import oracle
+from oracle.parallel import eq_many
 from paper_2602_24271_b300 import build, hp
 from paper_2602_24271_b300.inputs import eq_pair_columns
 
 pytestmark = pytest.mark.gpu
 LOGN = 15
 SEED_KEY = 1
+N_SAMPLES = 16
+
+
+def sample_indices(n_ct: int, seed: int):
+    """N_SAMPLES distinct ciphertext indices: the first, the last and seeded
+    uniform draws."""
+    rng = np.random.default_rng(seed)
+    idx = {0, n_ct - 1}
+    while len(idx) < N_SAMPLES:
+        idx.add(int(rng.integers(0, n_ct)))
+    return sorted(idx)
 
 
 @pytest.fixture(scope="module")
@@ -60,8 +75,10 @@ def test_plain_workload_2048_pairs(big):
     dec = decrypt_chunked(ctx, out)
     assert np.array_equal(dec.reshape(-1), (x == y).astype(np.uint32))
     ctx.check_status()
-    for c in (0, 1537):  # sampled ciphertexts, bit for bit
-        assert np.array_equal(hp.to_u64(out[c]), o.eq(hp.to_u64(cx[c]), hp.to_u64(cy[c])))
+    idx = sample_indices(n_ct, 101)
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], [hp.to_u64(cy[c]) for c in idx])
+    for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
+        assert np.array_equal(hp.to_u64(out[c]), w), c
     import torch
 
     del cx, cy, out
@@ -83,7 +100,9 @@ def test_const_workload_2_28_slots(big):
         c1 = min(n_ct, c0 + 512)
         dec = decrypt_chunked(ctx, out[c0:c1])
         assert np.array_equal(dec.reshape(-1), (x[c0 * N:c1 * N] == cval).astype(np.uint32))
-    c = 8191
-    assert np.array_equal(hp.to_u64(out[c]), o.eq(hp.to_u64(cx[c]), None, const_val=cval))
+    idx = sample_indices(n_ct, 103)
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], None, const_val=cval)
+    for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
+        assert np.array_equal(hp.to_u64(out[c]), w), c
     del cx, out
     torch.cuda.empty_cache()
