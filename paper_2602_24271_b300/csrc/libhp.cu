@@ -1633,6 +1633,9 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
 static uint64_t* g_noalloc_addr[64];  // device address of the array, per device (set up on first use)
 
 static int noalloc_scratch(hp_handle* h, uint64_t** out) {
+  if (h->device < 0 || h->device >= (int)(sizeof(g_noalloc_addr) / sizeof(g_noalloc_addr[0])))
+    HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: device ordinal %d beyond the 64 it keeps addresses for",
+            h->device);
   if (!g_noalloc_addr[h->device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
