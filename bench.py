@@ -172,33 +172,70 @@ def load_traffic(kernel: str, tile: int):
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
 class OracleSample:
-    """One ciphertext pair of the workload (N = 32768) on the CPU oracle: keys
-    and encryptions are made once; `time(k)` times the difference, k of the 16
-    squarings and "1 -", extrapolated to one full EQ."""
+    """One ciphertext of the workload (N = 32768) on the CPU oracle, keys and
+    encryptions made once.  `time(op, n_mul)` times the oracle's primitives on it
+    single-threaded (difference, `n_mul` multiplications with relinearisation,
+    "1 -", and one rotation with key switching where the workload rotates) and
+    composes the time of one unit of the workload from the counts below.  The
+    composition counts the multiplications and rotations the workload performs
+    and the difference and "1 -" of each EQ chain; ciphertext additions, the
+    plaintext products of Extract and LT's inner sums (255 scalar products per
+    giant step) are left out, so for those workloads the rate is an upper bound
+    on the oracle's."""
 
-    def __init__(self):
+    # per ciphertext (per ciphertext and B row for join): (differences, multiplications,
+    # "1 -", rotations, what is left out)
+    COUNTS = {
+        "ctct": (1, 16, 1, 0, ""),
+        "const": (1, 16, 1, 0, ""),
+        "batched": (1, 16, 1, 0, ""),
+        "in": (1, 16, 1, 0, "the additions of the IN sum"),
+        "lt": (1, 511, 0, 0, "the 128 inner sums of 255 scalar products and the additions"),
+        "between": (3, 1022, 1, 0, "the 2 x 128 inner sums of 255 scalar products and the additions"),
+        "sum": (1, 17, 1, 15 / 2048, "the additions"),
+        "rotsum": (0, 0, 0, 15, "the additions"),
+        "join": (1, 18, 1, 45 / 64, "the plaintext products of Extract and the additions"),
+    }
+
+    def __init__(self, op: str = "ctct"):
         import oracle
         from paper_2602_24271_b300.inputs import eq_pair_columns
 
+        self.op = op
         self.o = oracle.Oracle(LOGN)
         self.o.keygen(SEED_KEY)
         x, y = eq_pair_columns(self.o.N, seed=SEED_DATA)
         self.cx, self.cy = self.o.encrypt(x, 7, 0), self.o.encrypt(y, 7, 1)
+        self.g = None
+        if self.COUNTS[op][3]:
+            self.g = self.o.galois_elements()[0]
+            self.o.galois_keygen(SEED_KEY, self.g)
 
-    def time(self, squarings_timed: int):
+    def time(self, n_mul: int = 1):
         o = self.o
+        n_sub, n_m, n_1m, n_rot, left_out = self.COUNTS[self.op]
+        n_mul = n_mul if n_m else 0  # a workload without multiplications times none
         t0 = time.perf_counter()
         d = o.sub(self.cx, self.cy)
         t1 = time.perf_counter()
-        for _ in range(squarings_timed):
+        for _ in range(n_mul):
             d = o.mul_relin(d, d)
         t2 = time.perf_counter()
         o.one_minus(d)
         t3 = time.perf_counter()
-        per_eq = (t1 - t0) + 16 * (t2 - t1) / squarings_timed + (t3 - t2)
-        desc = ("1 ciphertext pair at N=32768 (32768 slots): difference, %d of the 16 squarings+relinearisations "
-                "and '1 -' timed single-threaded; squarings extrapolated to 16" % squarings_timed)
-        return o.N / per_eq, t3 - t0, desc
+        t_rot = 0.0
+        if self.g is not None:
+            o.rotate(d, self.g)
+            t_rot = time.perf_counter() - t3
+        t_sub, t_mul, t_1m = t1 - t0, (t2 - t1) / max(1, n_mul), t3 - t2
+        per_unit = n_sub * t_sub + n_m * t_mul + n_1m * t_1m + n_rot * t_rot
+        desc = ("1 ciphertext at N=32768 (32768 slots) on the oracle, single-threaded: a difference, %d "
+                "multiplication(s) with relinearisation, '1 -'%s timed; one unit of the workload composed as "
+                "%d difference(s) + %d multiplications + %d x '1 -'%s%s" % (
+                    n_mul, " and one rotation" if self.g is not None else "", n_sub, n_m, n_1m,
+                    " + %.3g rotations" % n_rot if n_rot else "",
+                    "; not counted: %s (the rate is an upper bound)" % left_out if left_out else ""))
+        return o.N / per_unit, time.perf_counter() - t0, desc
 
 
 def run_reference(args):
@@ -206,17 +243,18 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args.config)
-    sample = OracleSample()
-    vals, desc = [], ""
+    sample = OracleSample(wl["op"])
+    vals, step_ms, desc = [], [], ""
     for i in range(args.warmup + args.steps):
         v, secs, desc = sample.time(1)
         if i >= args.warmup:
             vals.append(v)
+            step_ms.append(secs * 1e3)
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": wl["desc"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "step": "one bounded sample of the workload (see cpu_baseline)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -434,8 +472,8 @@ def run_libhp(args):
     if not args.no_e2e and wl["op"] not in ("lt", "between", "in", "sum", "rotsum", "join"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
     # ---- CPU baseline (rank 0, N = 1 only) ----
-    if not args.no_cpu and rank == 0 and world == 1 and wl["op"] not in ("rotsum", "join"):
-        v, secs, desc = OracleSample().time(8)
+    if not args.no_cpu and rank == 0 and world == 1:
+        v, secs, desc = OracleSample(wl["op"]).time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
     if rank == 0:
@@ -578,6 +616,10 @@ def run_batched(args):
     dec_i = ctx.decrypt(iout[:2]).reshape(-1)
     assert np.array_equal(dec_i[:N], (xi[:N] == yi[:N]).astype(np.uint32))
     value = total / (ms_packed / 1e3)
+    cpu = None
+    if not args.no_cpu:
+        v, secs, desc = OracleSample("batched").time(8)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "cpu_seconds": secs}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_packed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
@@ -592,6 +634,8 @@ def run_batched(args):
                 "error": "bit-exact (integer arithmetic; parity tests vs the oracle)"},
             "clocks": clk, "gpu_launches": launches.get("packed", 0) * args.steps,
             "gpu_launches_by_form": launches}
+    if cpu:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     ctx.close()
 
