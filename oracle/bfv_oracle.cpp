@@ -12,15 +12,17 @@
 //   EQ(ct_x, ct_y) = 1 - (ct_x - ct_y)^(p-1),  p - 1 = 2^16  =>  16 squarings.
 //
 // Every ciphertext operation is written as its plain integer definition
-// (Fan-Vercauteren 2012 textbook BFV; relinearisation with per-prime digits and
-// one special prime, Gentry-Halevi-Smart 2012):
+// (Fan-Vercauteren 2012 textbook BFV; relinearisation with digits over groups of
+// three data primes and one special prime, Gentry-Halevi-Smart 2012):
 //
 //   * coefficients are big integers in [0, Q) (Q = q_0 ... q_{L-1});
 //   * multiplication lifts every coefficient to (-Q/2, Q/2], forms the exact
 //     integer negacyclic products d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1,
 //     then maps d -> round(t d / Q) mod Q;
-//   * relinearisation: digit_i = [d2]_{q_i}, u = sum_i digit_i rk_i mod QP,
-//     (c0, c1) += round(u / P) mod Q.
+//   * relinearisation: digit_a = [d2]_{Q_a} with Q_a = q_3a q_3a+1 q_3a+2 (five
+//     digits for L = 15), u = sum_a digit_a rk_a mod QP, (c0, c1) += round(u / P)
+//     mod Q (the paper fixes only log QP = 881, Sec. 5.1; SEAL's own
+//     decomposition is internal to it).
 //
 // The exact integer polynomial products are computed by a multi-modular
 // negacyclic NTT over the oracle's OWN 61-bit primes followed by Garner CRT
