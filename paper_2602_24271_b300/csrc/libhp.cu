@@ -317,8 +317,10 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
         h->dprod, h->w3, h->status, h->tct, logN, b);
   }
   h->launches += 1;
-  // key switching: digits [d2]_{q_i} mod p_j (reduction fused into the first
-  // transform pass), key multiply-accumulate, inverse transform, mod-down
+  // key switching: the digits [d2]_{Q_a} (three data primes each, stored in
+  // mixed radix by the scale-and-round) recombined mod every target prime p_j
+  // in the first transform pass, key multiply-accumulate, inverse transform,
+  // mod-down
   ntt_fwd(h, h->ksin, (size_t)b * NDIG * NKS, MAP_KS, s, h->w3);
   {
     ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * NDIG * NKS * N);
