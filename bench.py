@@ -135,6 +135,9 @@ NTT_CLASSES = {0, 1, 2, 3}
 # register-only probes, 0.97 T butterflies/s and 1.06 T MAC/s, agrees)
 N_SM, MUL_LANES_PER_SM_CLK, MUL_PER_BUTTERFLY, MUL_PER_MAC = 148, 32, 9, 8
 MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-switch MAC
+# ciphertext multiplications with relinearisation per N units of each workload
+# (per ciphertext; per ciphertext and B row for join); rotations are not counted
+HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1022, "sum": 17, "rotsum": 0, "join": 18}
 
 
 KERNEL_SOURCES = {  # files whose text determines a kernel's code
@@ -466,7 +469,8 @@ def run_libhp(args):
                        % (n_ct * 2 * 15 * N * 8 * (2 if cy is not None else 1) / 1e9),
                        "parallelism": "replicas" if world == 1 else "dp%d (independent ciphertexts)" % world},
             "roofline": roof, "clocks": clk, "gpu_launches": launches,
-            "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None}
+            "kernel_shares": {hp.PROFILE_CLASSES[c]: shares[c] / tot for c in shares} if tot else None,
+            "hmult_per_s": value / N * HMULT_PER_CT[wl["op"]]}
 
     # ---- end to end through the public API with pinned host buffers ----
     if not args.no_e2e and wl["op"] not in ("lt", "between", "in", "sum", "rotsum", "join"):
@@ -633,7 +637,7 @@ def run_batched(args):
                 "per_instance_batched_over_plain": ms_plain / ms_per,
                 "error": "bit-exact (integer arithmetic; parity tests vs the oracle)"},
             "clocks": clk, "gpu_launches": launches.get("packed", 0) * args.steps,
-            "gpu_launches_by_form": launches}
+            "gpu_launches_by_form": launches, "hmult_per_s": n_pk * 16 / (ms_packed / 1e3)}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
