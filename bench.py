@@ -18,6 +18,7 @@ import glob
 import hashlib
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -239,6 +240,51 @@ class OracleSample:
                     " + %.3g rotations" % n_rot if n_rot else "",
                     "; not counted: %s (the rate is an upper bound)" % left_out if left_out else ""))
         return o.N / per_unit, time.perf_counter() - t0, desc
+
+
+def _oracle_worker(op, n_mul, barrier, results):
+    sample = OracleSample(op)
+    barrier.wait(timeout=120)  # every worker set up: the timed samples run concurrently
+    results.put(sample.time(n_mul))
+
+
+def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 8):
+    """The paper's multi-threaded form (Sec. 5.3: independent predicates
+    assigned to threads, measured up to 8 threads): W = min(8, host cores)
+    single-threaded oracle processes, started with spawn, set up (keys and one
+    ciphertext each), released together by a barrier, then each times the
+    cpu_baseline composition of one unit on its own ciphertext.  All W run at
+    the same time, so the aggregate rate is the sum of their rates."""
+    import multiprocessing as mp
+
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    w = max(1, min(max_workers, cores))
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(w), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(op, n_mul, barrier, results)) for _ in range(w)]
+    for pr in procs:
+        pr.start()
+    got, deadline = [], time.time() + 300
+    while len(got) < w:
+        try:
+            got.append(results.get(timeout=2))
+        except queue.Empty:
+            if time.time() > deadline or not any(pr.is_alive() for pr in procs):
+                break
+    for pr in procs:
+        pr.join(timeout=10)
+        if pr.is_alive():
+            pr.terminate()
+    if len(got) < w:
+        raise RuntimeError("%d of %d oracle worker processes reported" % (len(got), w))
+    value = sum(v for v, _, _ in got)
+    return {"value": value, "unit": UNIT, "cores": w, "kind": "oracle",
+            "sample": "%d concurrent single-threaded oracle processes (independent predicates on separate cores, "
+                      "as in the paper's multi-threaded runs), released together; value = sum of their rates; "
+                      "each: %s" % (w, got[0][2])}
 
 
 def run_reference(args):
@@ -480,6 +526,12 @@ def run_libhp(args):
         v, secs, desc = OracleSample(wl["op"]).time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
+        try:
+            mc = multicore_baseline(wl["op"])
+            mc["speedup_over_one_core_sample"] = mc["value"] / v
+        except Exception as e:  # the single-core baseline above stands on its own
+            mc = {"value": None, "error": str(e)[:200]}
+        line["cpu_baseline_multicore"] = mc
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
