@@ -43,7 +43,9 @@
  * description of the last failure on that handle.  On error the output
  * buffers are unspecified.
  *
- * Thread safety: a handle may be used by one host thread at a time.
+ * Thread safety: a handle may be used by one host thread at a time.  The
+ * library's process-wide tables (per-device constants, the autotune cache, the
+ * allocation-free scratch addresses) are guarded by a mutex.
  */
 #ifndef LIBHP_HP_H
 #define LIBHP_HP_H

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -582,12 +583,18 @@ static int build_tables(hp_handle* h) {
   return HP_OK;
 }
 
+// Process-wide tables shared by all handles (per-device constants, the
+// autotune cache, the allocation-free scratch addresses) are read and written
+// under this mutex, so handles may be created and tuned from several threads.
+static std::mutex g_tables_mu;
+
 // The constant block lives in __constant__ memory, one per device; handles on
 // the same device must agree on (q, P, t).
 static bool g_loaded[64];
 static Consts g_consts[64];
 
 static int load_consts(hp_handle* h) {
+  std::lock_guard<std::mutex> lock(g_tables_mu);
   if (h->device < 0 || h->device >= 64) HP_FAIL(h, HP_ERR_UNSUPPORTED, "device index out of range");
   if (g_loaded[h->device]) {
     if (memcmp(&g_consts[h->device], &h->C, sizeof(Consts)) != 0)
@@ -948,7 +955,7 @@ int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst,
 // Tile-size autotuner: times the EQ launch sequence for candidate tile sizes on
 // the handle's own staging buffers (the path is data-oblivious, so timings do
 // not depend on the data) and keeps the fastest per ciphertext.  Results are
-// cached per (ring degree, device) for the process.
+// cached per (ring degree, device, workspace tile) for the process.
 struct TuneKey {
   int logn, device;
   size_t maxtile, best;
@@ -958,12 +965,15 @@ static std::vector<TuneKey> g_tune;
 int hp_autotune(hp_handle* h, size_t* best_tile) {
   if (!h) return HP_ERR_ARG;
   if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
-  for (auto& k : g_tune)
-    if (k.logn == h->logn && k.device == h->device && k.maxtile == h->tile) {
-      h->run_tile = k.best;
-      if (best_tile) *best_tile = k.best;
-      return HP_OK;
-    }
+  {
+    std::lock_guard<std::mutex> lock(g_tables_mu);
+    for (auto& k : g_tune)
+      if (k.logn == h->logn && k.device == h->device && k.maxtile == h->tile) {
+        h->run_tile = k.best;
+        if (best_tile) *best_tile = k.best;
+        return HP_OK;
+      }
+  }
   const size_t cand[] = {1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64};
   cudaEvent_t e0, e1;
   CU(h, cudaEventCreate(&e0));
@@ -995,7 +1005,10 @@ int hp_autotune(hp_handle* h, size_t* best_tile) {
   cudaEventDestroy(e1);
   CU(h, hp_check_status(h) == HP_OK ? cudaSuccess : cudaErrorUnknown);
   h->run_tile = bt;
-  g_tune.push_back({h->logn, h->device, h->tile, bt});
+  {
+    std::lock_guard<std::mutex> lock(g_tables_mu);
+    g_tune.push_back({h->logn, h->device, h->tile, bt});
+  }
   if (best_tile) *best_tile = bt;
   return HP_OK;
 }
@@ -1635,6 +1648,7 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
 static uint64_t* g_noalloc_addr[64];  // device address of the array, per device (set up on first use)
 
 static int noalloc_scratch(hp_handle* h, uint64_t** out) {
+  std::lock_guard<std::mutex> lock(g_tables_mu);
   if (h->device < 0 || h->device >= (int)(sizeof(g_noalloc_addr) / sizeof(g_noalloc_addr[0])))
     HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: device ordinal %d beyond the 64 it keeps addresses for",
             h->device);
