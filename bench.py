@@ -177,7 +177,7 @@ def load_traffic(kernel: str, tile: int):
 # ---------------------------------------------------------------------------
 class OracleSample:
     """One ciphertext of the workload (N = 32768) on the CPU oracle, keys and
-    encryptions made once.  `time(op, n_mul)` times the oracle's primitives on it
+    encryptions made once.  `time(n_mul)` times the oracle's primitives on it
     single-threaded (difference, `n_mul` multiplications with relinearisation,
     "1 -", and one rotation with key switching where the workload rotates) and
     composes the time of one unit of the workload from the counts below.  The

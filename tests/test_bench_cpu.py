@@ -1,0 +1,63 @@
+"""Host-side pieces of bench.py (CPU only): the workload table, the stored
+ncu traffic lookup and the reference arm's JSON line, which times the oracle
+on a bounded sample and needs no GPU."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import bench
+
+OPS = ["ctct", "const", "batched", "in", "lt", "between", "sum", "rotsum", "join"]
+CONFIGS = ["plain", "const28", "batched", "lt", "between", "in", "sum", "rotsum", "join"]
+
+
+def test_every_config_has_a_composition_and_a_multiplication_count():
+    ops = {bench.workload(c)["op"] for c in CONFIGS}
+    assert ops == set(OPS)
+    for op in OPS:
+        assert op in bench.OracleSample.COUNTS
+        assert op == "batched" or op in bench.HMULT_PER_CT
+    # an EQ chain is 16 squarings (p - 1 = 2^16, Eq. 3); LT's schedule 511 products
+    assert bench.OracleSample.COUNTS["ctct"][1] == 16 == bench.HMULT_PER_CT["ctct"]
+    assert bench.OracleSample.COUNTS["lt"][1] == 511 == bench.HMULT_PER_CT["lt"]
+    assert bench.OracleSample.COUNTS["between"][1] == 2 * 511
+
+
+def test_stored_traffic_scales_with_the_tile_and_follows_the_sources():
+    path = os.path.join(bench.ROOT, "profiles", "ncu_counters.json")
+    d = json.load(open(path))
+    tile = d["tile_ct"]
+    for kernel, k in d["kernels"].items():
+        want = k["dram_bytes_per_launch_full"]
+        got = bench.load_traffic(kernel, tile)
+        if k["source_hash"] == bench.source_hash(kernel):
+            assert got == pytest.approx(want)
+            assert bench.load_traffic(kernel, 2 * tile) == pytest.approx(2 * want)
+        else:
+            assert got is None  # counters taken on other kernel sources are not reported
+    assert bench.load_traffic("k_no_such_kernel", tile) is None
+
+
+def test_reference_arm_prints_one_json_line():
+    env = dict(os.environ, RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["ms_per_step"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    env = dict(os.environ, RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
