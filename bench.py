@@ -248,13 +248,13 @@ def _oracle_worker(op, n_mul, barrier, results):
     results.put(sample.time(n_mul))
 
 
-def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 8):
+def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32):
     """The paper's multi-threaded form (Sec. 5.3: independent predicates
-    assigned to threads, measured up to 8 threads): W = min(8, host cores)
-    single-threaded oracle processes, started with spawn, set up (keys and one
-    ciphertext each), released together by a barrier, then each times the
-    cpu_baseline composition of one unit on its own ciphertext.  All W run at
-    the same time, so the aggregate rate is the sum of their rates."""
+    assigned to threads): W = min(32, host cores) single-threaded oracle
+    processes (about 0.45 GB of host memory each), started with spawn, set up
+    (keys and one ciphertext each), released together by a barrier, then each
+    times the cpu_baseline composition of one unit on its own ciphertext.  All
+    W run at the same time, so the aggregate rate is the sum of their rates."""
     import multiprocessing as mp
 
     try:
@@ -281,7 +281,7 @@ def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 8):
     if len(got) < w:
         raise RuntimeError("%d of %d oracle worker processes reported" % (len(got), w))
     value = sum(v for v, _, _ in got)
-    return {"value": value, "unit": UNIT, "cores": w, "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": w, "host_cores": cores, "kind": "oracle",
             "sample": "%d concurrent single-threaded oracle processes (independent predicates on separate cores, "
                       "as in the paper's multi-threaded runs), released together; value = sum of their rates; "
                       "each: %s" % (w, got[0][2])}
