@@ -37,19 +37,32 @@ _i8p = ctypes.POINTER(ctypes.c_int8)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 
 
+def _compile(path: str, flags, force: bool) -> str:
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", *flags, "-o", tmp, _SRC], check=True)
+    os.replace(tmp, path)
+    return path
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with g++ (no CUDA involved)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, ["-Wall"], force)
+
+
+def build_mutant(k: int, force: bool = False) -> str:
+    """A separate copy of the oracle with planted mistake number k (1..8, listed
+    at the top of bfv_oracle.cpp), for the tests that check that the pins catch
+    such mistakes.  Never loaded by anything but those tests."""
+    if not 1 <= k <= 8:
+        raise ValueError("no planted mistake %d" % k)
+    return _compile(os.path.join(_BUILD, "liboracle_mutant%d.so" % k), ["-DORC_MUTANT=%d" % k], force)
 
 
 _lib = None
+_libs = {}
 
 
 def galois_elements(logn: int):
@@ -60,11 +73,15 @@ def galois_elements(logn: int):
     return [pow(3, 1 << i, twoN) for i in range(logn - 2, -1, -1)] + [twoN - 1]
 
 
-def _load():
+def _load(path=None):
+    """The oracle library (built if needed), or the one at `path` (a planted-
+    mistake copy from build_mutant)."""
     global _lib
-    if _lib is not None:
+    if path is None and _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    if path is not None and path in _libs:
+        return _libs[path]
+    lib = ctypes.CDLL(build() if path is None else path)
     V = ctypes.c_void_p
     sig = {
         "orc_default_primes": (ctypes.c_int, [ctypes.c_int, _u64p, _u64p]),
@@ -105,7 +122,10 @@ def _load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
+    if path is None:
+        _lib = lib
+    else:
+        _libs[path] = lib
     return lib
 
 
@@ -165,10 +185,10 @@ class Oracle:
     """One BFV parameter set (ring degree 2^logn, data primes q, special prime P,
     plaintext modulus t).  Holds the relinearisation key after keygen()."""
 
-    def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT):
+    def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT, lib_path=None):
         if q is None:
             q, P = default_primes(L)
-        self.lib = _load()
+        self.lib = _load(lib_path)
         self.logn = logn
         self.N = 1 << logn
         self.q = [int(x) for x in q]

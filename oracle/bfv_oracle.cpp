@@ -29,6 +29,21 @@
 // reconstruction; a product is exact because the CRT modulus exceeds twice
 // the largest possible coefficient.  Big-integer arithmetic is a small
 // fixed-width sign-magnitude type written here.  Plain, slow, single-threaded.
+// Planted mistakes (mutation tests).  The normal build leaves ORC_MUTANT at 0
+// and none of them is compiled in.  tests/test_oracle_mutants.py builds separate
+// copies with -DORC_MUTANT=k, each containing one plausible mistake, and checks
+// that a pin of this oracle fails on that copy:
+//   1 round(t d / Q) truncated toward zero instead of rounded
+//   2 the cross term a1 b0 dropped from d1
+//   3 the mod-down remainder taken in [0, P) instead of centred
+//   4 the negacyclic twist left out (cyclic products)
+//   5 the sign of (a s + e) in the key-switching keys flipped
+//   6 slots read in natural instead of bit-reversed transform order
+//   7 key-switching digit a taken mod q_3a alone instead of mod Q_a
+//   8 one squaring too few in the EQ chain
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
 #include <cstdint>
 #include <cstring>
 #include <cstdlib>
@@ -465,12 +480,18 @@ struct NttPlan {
     }
   }
   void forward(uint64_t* a) const {
+#if ORC_MUTANT != 4
     for (int k = 0; k < n; ++k) a[k] = mulmod_shoup(a[k], tw[k], m);
+#endif
     cyclic(a, w);
   }
   void inverse(uint64_t* a) const {
     cyclic(a, iw);
+#if ORC_MUTANT == 4
+    for (int k = 0; k < n; ++k) a[k] = mulmod_shoup(a[k], itw[0], m);  // N^{-1} only
+#else
     for (int k = 0; k < n; ++k) a[k] = mulmod_shoup(a[k], itw[k], m);
+#endif
   }
 };
 
@@ -596,7 +617,11 @@ static Poly poly_mul_exact(const Ctx& c, const Poly& a, const Poly& b) {
 }
 // exact tensor of (a0, a1) and (b0, b1): d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1
 static std::vector<Poly> tensor_exact(const Ctx& c, const Poly& a0, const Poly& a1, const Poly& b0, const Poly& b1) {
+#if ORC_MUTANT == 2
+  return poly_sums_exact(c, {Terms{{&a0, &b0}}, Terms{{&a0, &b1}}, Terms{{&a1, &b1}}});
+#else
   return poly_sums_exact(c, {Terms{{&a0, &b0}}, Terms{{&a0, &b1}, {&a1, &b0}}, Terms{{&a1, &b1}}});
+#endif
 }
 
 // canonical representative in [0, M) of a signed integer, M = prod(ms)
@@ -619,7 +644,11 @@ static Big center_Q(const Ctx& c, const Big& x) {
 static Big round_t_over_Q(const Ctx& c, const Big& d) {
   Big a = d;
   a.neg = 0;
+#if ORC_MUTANT == 1
+  Big num = big_mul_u64(a, 2 * c.t);
+#else
   Big num = big_add(big_mul_u64(a, 2 * c.t), c.Q);  // 2 t |d| + Q
+#endif
   uint64_t r;
   Big h = mag_divmod_u64(num, 2, &r);               // floor(num / 2)
   Big w = mag_floordiv_primes(h, c.q);              // floor(num / (2Q))
@@ -663,11 +692,19 @@ static void ct_to_rns(const Ctx& c, const Ct& ct, uint64_t* a) {
 static void decode_poly(const Ctx& c, const uint64_t* m, uint32_t* slots) {
   std::vector<uint64_t> a(m, m + c.N);
   c.tplan.forward(a.data());
+#if ORC_MUTANT == 6
+  for (int j = 0; j < c.N; ++j) slots[j] = (uint32_t)a[j];
+#else
   for (int j = 0; j < c.N; ++j) slots[j] = (uint32_t)a[brv(j, c.logn)];
+#endif
 }
 static void encode_slots(const Ctx& c, const uint32_t* slots, uint64_t* m) {
   std::vector<uint64_t> a(c.N);
+#if ORC_MUTANT == 6
+  for (int j = 0; j < c.N; ++j) a[j] = slots[j] % c.t;
+#else
   for (int j = 0; j < c.N; ++j) a[brv(j, c.logn)] = slots[j] % c.t;
+#endif
   c.tplan.inverse(a.data());
   for (int j = 0; j < c.N; ++j) m[j] = a[j];
 }
@@ -712,7 +749,12 @@ static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d
   std::vector<uint64_t> res0((size_t)k * N), res1((size_t)k * N);
   std::vector<Big> digit((size_t)D * N);  // digit_a = [d2]_{Q_a}
   for (int a = 0; a < D; ++a)
+#if ORC_MUTANT == 7
+    for (int j = 0; j < N; ++j)
+      digit[(size_t)a * N + j] = mod_primes(d2[j], big_u64(c.grp[a][0]), std::vector<uint64_t>{c.grp[a][0]});
+#else
     for (int j = 0; j < N; ++j) digit[(size_t)a * N + j] = mod_primes(d2[j], c.Qa[a], c.grp[a]);
+#endif
   std::vector<uint64_t> Dg(N), acc0(N), acc1(N);
   for (int pi = 0; pi < k; ++pi) {
     uint64_t m = c.om[pi];
@@ -749,7 +791,12 @@ static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d
       Big u = crt.reconstruct_centered(&res[(size_t)j * k]);
       u = mod_QP(c, u);
       uint64_t rp = big_mod_u64(u, c.P);             // [u]_P, centred below
+#if ORC_MUTANT == 3
+      Big cen = big_u64(rp);
+      (void)Phalf;
+#else
       Big cen = rp > Phalf ? big_neg(big_u64(c.P - rp)) : big_u64(rp);
+#endif
       uint64_t rem;
       Big ks = mag_divmod_u64(big_sub(u, cen), c.P, &rem);  // (u - [u]_P) / P, exact
       if (rem != 0) fail("mod-down not exact");
@@ -844,7 +891,11 @@ static void make_ks_key(const Ctx& c, uint64_t seed, const Poly& s, const Poly& 
     }
     Poly as = poly_mul_exact(c, av, s);
     for (int k = 0; k < N; ++k) {
+#if ORC_MUTANT == 5
+      Big v = big_add(as[k], e[k]);
+#else
       Big v = big_neg(big_add(as[k], e[k]));
+#endif
       v = big_add(v, big_mul(Pg, src[k]));
       K.k0[a][k] = mod_QP(c, v);
       K.k1[a][k] = av[k];
@@ -1131,6 +1182,9 @@ int orc_eq(void* h, const uint64_t* x, const uint64_t* y, uint64_t const_val, in
   if (!c.have_rk) return -2;
   Ct d = ct_from_rns(c, x);
   d = y ? ct_sub(c, d, ct_from_rns(c, y)) : ct_sub_const(c, d, const_val);
+#if ORC_MUTANT == 8
+  --squarings;
+#endif
   for (int r = 0; r < squarings; ++r) d = ct_mul_relin(c, d, d);
   ct_to_rns(c, ct_one_minus(c, d), out);
   return 0;

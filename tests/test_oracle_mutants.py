@@ -1,0 +1,45 @@
+"""The oracle's pins have teeth (CPU only).
+
+Each case builds a separate copy of the oracle with one plausible mistake
+planted in it (bfv_oracle.cpp, ORC_MUTANT = k; the normal build has none) and
+runs a pin from test_oracle_pins.py on that copy: the pin must fail.  The pins
+compare the oracle with things other than itself -- Python big-integer brute
+force with a schoolbook product, direct evaluation of the encoding, the
+closed form of the predicate -- so a mistake in any of these steps shows up
+there and not only as a disagreement with the GPU."""
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+# (planted mistake, the pin that must catch it)
+CASES = [
+    (1, "round(t d / Q) truncated toward zero", pins.test_tensor_and_rounding_bruteforce),
+    (2, "cross term a1 b0 dropped from d1", pins.test_tensor_and_rounding_bruteforce),
+    (3, "mod-down remainder not centred", pins.test_relinearisation_bruteforce),
+    (4, "negacyclic twist left out", pins.test_encoding_closed_forms),
+    (4, "negacyclic twist left out", pins.test_tensor_and_rounding_bruteforce),
+    (5, "sign of (a s + e) in the key flipped", pins.test_keygen_relation_bruteforce),
+    (6, "slots in natural transform order", pins.test_encoding_closed_forms),
+    (7, "digit taken mod its first prime only", pins.test_relinearisation_bruteforce),
+    (8, "one squaring too few", pins.test_eq_const_closed_form),
+]
+
+
+def _oracle16(lib_path=None):
+    o = oracle.Oracle(4, lib_path=lib_path)  # the orc16 fixture's parameters and key seed
+    o.keygen(7)
+    return o
+
+
+@pytest.mark.parametrize("k, mistake, pin", CASES, ids=["%d-%s" % (k, p.__name__[5:]) for k, _, p in CASES])
+def test_pin_catches_planted_mistake(k, mistake, pin):
+    o = _oracle16(oracle.build_mutant(k))
+    with pytest.raises(AssertionError):
+        pin(o)
+
+
+def test_pins_pass_on_the_normal_build():
+    o = _oracle16()
+    for pin in {p for _, _, p in CASES}:
+        pin(o)
