@@ -41,6 +41,11 @@
 //   6 slots read in natural instead of bit-reversed transform order
 //   7 key-switching digit a taken mod q_3a alone instead of mod Q_a
 //   8 one squaring too few in the EQ chain
+//   9 LT coefficients taken from the even powers (b^(p-1-2m) for c_{2m+1})
+//  10 the automorphism's negacyclic sign dropped (X^N taken as +1)
+//  11 the rotate-and-add reduction without its row exchange
+//  12 BETWEEN combined as 1 - b + a instead of 1 - b - a
+//  13 LT's first giant step taken as w^128 instead of w^256
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
@@ -937,7 +942,11 @@ static Poly automorph(const Ctx& c, const Poly& a, uint64_t g, const Big* M) {
       out[e] = a[j];
     } else {
       const Big& v = a[j];
+#if ORC_MUTANT == 10
+      out[e - c.N] = v;
+#else
       out[e - c.N] = M ? (big_is_zero(v) ? v : big_sub(*M, v)) : big_neg(v);
+#endif
     }
   }
   return out;
@@ -1219,7 +1228,11 @@ static std::vector<uint32_t> lt_odd_coefficients(uint64_t p) {
   std::vector<uint64_t> acc(half, 0);
   for (uint64_t b = 1; b <= half; ++b) {
     const uint64_t b2inv = invmod(b * b % p, p);  // b^(p-2-2m) = b^(p-2) * (b^-2)^m
+#if ORC_MUTANT == 9
+    uint64_t v = 1;  // b^(p-1)
+#else
     uint64_t v = invmod(b, p);                    // b^(p-2)
+#endif
     for (uint64_t m = 0; m < half; ++m) {
       acc[m] += v;
       v = v * b2inv % p;
@@ -1294,7 +1307,11 @@ static Ct lt_eval(const Ctx& c, const Ct& z, const std::vector<uint32_t>& hc) {
   std::vector<Ct> B(BS), G(GS + 1);
   B[1] = w;
   for (int i = 2; i < BS; ++i) B[i] = (i % 2 == 0) ? ct_mul_relin(c, B[i / 2], B[i / 2]) : ct_mul_relin(c, B[i - 1], B[1]);
+#if ORC_MUTANT == 13
+  G[1] = B[128];
+#else
   G[1] = ct_mul_relin(c, B[128], B[128]);
+#endif
   for (int j = 2; j <= GS; ++j) G[j] = (j % 2 == 0) ? ct_mul_relin(c, G[j / 2], G[j / 2]) : ct_mul_relin(c, G[j - 1], G[1]);
   std::vector<const Ct*> ptrs;
   for (int i = 1; i < BS; ++i) ptrs.push_back(&B[i]);
@@ -1364,7 +1381,11 @@ int orc_between(void* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* 
   Ct X = ct_from_rns(c, x);
   Ct below = lt_eval(c, ct_sub_const(c, X, lo), hc);    // [x < lo]
   Ct above = lt_eval(c, ct_const_minus(c, X, hi), hc);  // [hi < x]
+#if ORC_MUTANT == 12
+  ct_to_rns(c, ct_add(c, ct_one_minus(c, above), below), out);
+#else
   ct_to_rns(c, ct_sub(c, ct_one_minus(c, above), below), out);  // (1 - b) - a
+#endif
   return 0;
 }
 
@@ -1469,6 +1490,9 @@ int orc_rotate_sum(void* h, const uint64_t* x, int row_steps, int swap, uint64_t
     if (!c.gk.count(g)) return -2;
     a = ct_add(c, a, ct_rotate(c, a, g));
   }
+#if ORC_MUTANT == 11
+  swap = 0;
+#endif
   if (swap) {
     if (!c.gk.count(twoN - 1)) return -2;
     a = ct_add(c, a, ct_rotate(c, a, twoN - 1));
