@@ -41,15 +41,17 @@ def test_stored_traffic_scales_with_the_tile_and_follows_the_sources():
     assert bench.load_traffic("k_no_such_kernel", tile) is None
 
 
-def test_reference_arm_prints_one_json_line():
+@pytest.mark.parametrize("config", ["plain", "rotsum"])  # multiplications; rotations with a Galois key
+def test_reference_arm_prints_one_json_line(config):
     env = dict(os.environ, RANK="0")
-    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, timeout=600, env=env)
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--config", config,
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["config"]["workload"] == bench.workload(config)["desc"]
     assert line["value"] > 0 and line["ms_per_step"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
