@@ -53,10 +53,10 @@ def build(force: bool = False) -> str:
 
 
 def build_mutant(k: int, force: bool = False) -> str:
-    """A separate copy of the oracle with planted mistake number k (1..13, listed
+    """A separate copy of the oracle with planted mistake number k (1..14, listed
     at the top of bfv_oracle.cpp), for the tests that check that the pins catch
     such mistakes.  Never loaded by anything but those tests."""
-    if not 1 <= k <= 13:
+    if not 1 <= k <= 14:
         raise ValueError("no planted mistake %d" % k)
     return _compile(os.path.join(_BUILD, "liboracle_mutant%d.so" % k), ["-DORC_MUTANT=%d" % k], force)
 

@@ -46,6 +46,7 @@
 //  11 the rotate-and-add reduction without its row exchange
 //  12 BETWEEN combined as 1 - b + a instead of 1 - b - a
 //  13 LT's first giant step taken as w^128 instead of w^256
+//  14 the noise budget without the factor 2 of its definition
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
@@ -1155,7 +1156,11 @@ int orc_decrypt(void* h, const int8_t* s, const uint64_t* ct_in, uint32_t* slots
     Big y = center_Q(c, mod_Q(c, big_mul_u64(x[k], c.t)));
     worst = std::max(worst, big_log2(y));
   }
+#if ORC_MUTANT == 14
+  if (noise_bits) *noise_bits = big_log2(c.Q) - worst;
+#else
   if (noise_bits) *noise_bits = big_log2(c.Q) - 1.0 - worst;
+#endif
   decode_poly(c, m.data(), slots_out);
   return 0;
 }

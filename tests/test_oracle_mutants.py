@@ -29,6 +29,7 @@ CASES = [
     (11, "reduction without the row exchange", pins.test_count_and_sum_closed_form_n16),
     (12, "BETWEEN as 1 - b + a", pins.test_between_closed_form_n16),
     (13, "first giant step w^128", pins.test_lt_closed_form_n16),
+    (14, "noise budget without its factor 2", pins.test_noise_budget_bruteforce),
 ]
 
 

@@ -217,6 +217,38 @@ def test_encrypt_relation_bruteforce(orc16):
     assert not np.array_equal(ct, ct2) and np.array_equal(o.decrypt(ct2), x)
 
 
+def _budget_bruteforce(o, ct):
+    """Invariant noise budget from its definition with Python integers:
+    log2(Q) - 1 - log2 max_k |[t (c0 + c1 s)_k]_Q| (centred), the phase taken
+    with a schoolbook negacyclic product."""
+    N, Q = o.N, math.prod(o.q)
+    c0, c1 = to_ints(ct[0], o.q), to_ints(ct[1], o.q)
+    ph = [(a + b) % Q for a, b in zip(c0, negacyclic_schoolbook(c1, [int(v) for v in o.s], N))]
+    y = [(T * v) % Q for v in ph]
+    worst = max(abs(v - Q if v > Q // 2 else v) for v in y)
+    return math.log2(Q) - 1 - math.log2(worst), worst
+
+
+def test_noise_budget_bruteforce(orc16):
+    """The decryption's noise budget equals its definition, for a fresh
+    ciphertext and after one product.  For a fresh ciphertext the closed form
+    bounds it: c0 + c1 s = Delta m - e gives [t (c0 + c1 s)]_Q = -(Q mod t) m - t e,
+    so |.| <= (Q mod t)(t - 1) + 21 t."""
+    o = orc16
+    Q = math.prod(o.q)
+    rng = np.random.default_rng(31)
+    x, y = rng.integers(0, T, o.N).astype(np.uint32), rng.integers(0, T, o.N).astype(np.uint32)
+    cx, cy = o.encrypt(x, 32, 0), o.encrypt(y, 32, 1)
+    _, nb = o.decrypt(cx, with_noise=True)
+    want, worst = _budget_bruteforce(o, cx)
+    assert abs(nb - want) < 1e-6
+    assert worst <= (Q % T) * (T - 1) + 21 * T
+    prod = o.mul_relin(cx, cy)
+    _, nb2 = o.decrypt(prod, with_noise=True)
+    assert abs(nb2 - _budget_bruteforce(o, prod)[0]) < 1e-6
+    assert nb2 < nb
+
+
 # --------------------------------------------------------------------------
 # textbook multiplication and relinearisation: brute force on N = 16
 # --------------------------------------------------------------------------
