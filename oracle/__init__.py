@@ -13,8 +13,10 @@ exposes; the arithmetic lives in the C++ file.
 
 Array conventions (numpy):
   ciphertext  uint64 [2][L][N]  residues mod q_0..q_{L-1}, coefficient domain
-  relin key   uint64 [D][2][L+1][N]  residues mod q_0..q_{L-1}, P; D = ceil(L / 3)
-              key-switching digits, each the residue mod a group of 3 data primes
+  relin key   uint64 [D][2][L+1][N]  residues mod q_0..q_{L-1}, P; D = ceil(L / dp)
+              key-switching digits, each the residue mod a group of dp data primes
+              (dp = 3 unless chosen otherwise); the per-prime key of the first
+              levels (fine_depth > 0) has D = L
   secret key  int8 [N] in {-1, 0, 1}
   slots       uint32 [N] values mod t
 """
@@ -53,10 +55,10 @@ def build(force: bool = False) -> str:
 
 
 def build_mutant(k: int, force: bool = False) -> str:
-    """A separate copy of the oracle with planted mistake number k (1..14, listed
+    """A separate copy of the oracle with planted mistake number k (1..15, listed
     at the top of bfv_oracle.cpp), for the tests that check that the pins catch
     such mistakes.  Never loaded by anything but those tests."""
-    if not 1 <= k <= 14:
+    if not 1 <= k <= 15:
         raise ValueError("no planted mistake %d" % k)
     return _compile(os.path.join(_BUILD, "liboracle_mutant%d.so" % k), ["-DORC_MUTANT=%d" % k], force)
 
@@ -117,6 +119,9 @@ def _load(path=None):
         "orc_rotate_sum": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, _u64p]),
         "orc_mul_plain": (ctypes.c_int, [V, _u64p, _u64p, _u64p]),
         "orc_between": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p]),
+        "orc_set_digits": (ctypes.c_int, [V, ctypes.c_int, ctypes.c_int]),
+        "orc_fine_key": (ctypes.c_int, [V, _u64p]),
+        "orc_mul_relin_depth": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p, ctypes.c_int, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -183,9 +188,15 @@ def ntt_inverse(logn: int, m: int, a) -> np.ndarray:
 
 class Oracle:
     """One BFV parameter set (ring degree 2^logn, data primes q, special prime P,
-    plaintext modulus t).  Holds the relinearisation key after keygen()."""
+    plaintext modulus t).  Holds the relinearisation key after keygen().
 
-    def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT, lib_path=None):
+    Key switching: the relinearisation and Galois keys have digits of `dp`
+    consecutive data primes (3 by default); products whose multiplicative depth
+    is at most `fine_depth` are relinearised with a second key of one prime per
+    digit instead (0 = never).  Depths count from fresh ciphertexts (depth 0)."""
+
+    def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT, lib_path=None,
+                 dp: int = 3, fine_depth: int = 0):
         if q is None:
             q, P = default_primes(L)
         self.lib = _load(lib_path)
@@ -197,9 +208,12 @@ class Oracle:
         self.t = int(t)
         qa = np.array(self.q, dtype=np.uint64)
         self.h = self.lib.orc_create(logn, self.L, _p(qa, ctypes.c_uint64), self.P, self.t)
-        self.D = self.lib.orc_num_digits(self.h)
         if not self.h:
             raise RuntimeError("orc_create failed")
+        if self.lib.orc_set_digits(self.h, dp, fine_depth) != 0:
+            raise ValueError("digit grouping must be 1..L data primes and fine_depth >= 0")
+        self.dp, self.fine_depth = dp, fine_depth
+        self.D = self.lib.orc_num_digits(self.h)
         self.s = None
         self.rk = None
 
@@ -296,10 +310,26 @@ class Oracle:
         self.lib.orc_one_minus(self.h, _p(X, ctypes.c_uint64), _p(out, ctypes.c_uint64))
         return out
 
-    def mul_relin(self, a, b):
+    def mul_relin(self, a, b, depth_a: int = 0, depth_b: int = 0):
+        """a * b relinearised; the operands lie at multiplicative depths depth_a and
+        depth_b (0 = fresh), the product at max(depth_a, depth_b) + 1, which selects
+        the relinearisation key."""
         A, B, out = _c(a, np.uint64), _c(b, np.uint64), self._ct_out()
-        if self.lib.orc_mul_relin(self.h, _p(A, ctypes.c_uint64), _p(B, ctypes.c_uint64), _p(out, ctypes.c_uint64)) != 0:
+        if depth_a == 0 and depth_b == 0:
+            rc = self.lib.orc_mul_relin(self.h, _p(A, ctypes.c_uint64), _p(B, ctypes.c_uint64), _p(out, ctypes.c_uint64))
+        else:
+            rc = self.lib.orc_mul_relin_depth(self.h, _p(A, ctypes.c_uint64), depth_a, _p(B, ctypes.c_uint64), depth_b,
+                                              _p(out, ctypes.c_uint64))
+        if rc != 0:
             raise RuntimeError("relinearisation key not set")
+        return out
+
+    def fine_key(self) -> np.ndarray:
+        """The per-prime relinearisation key (uint64 [L][2][L+1][N]) made by keygen()
+        when fine_depth > 0."""
+        out = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
+        if self.lib.orc_fine_key(self.h, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("no per-prime key (fine_depth = 0)")
         return out
 
     def eq(self, x, y=None, const_val: int = 0, squarings: int = 16):
@@ -420,7 +450,7 @@ class Oracle:
         return out
 
     def between(self, x, lo: int, hi: int):
-        """BETWEEN: 1 - LT(x, lo) - LT(hi, x) = [lo <= x <= hi] for constants lo <= hi."""
+        """BETWEEN: (1 - LT(x, lo)) (1 - LT(hi, x)) = [lo <= x <= hi] for constants lo <= hi."""
         X, out = _c(x, np.uint64), self._ct_out()
         rc = self.lib.orc_between(self.h, _p(X, ctypes.c_uint64), lo, hi, _p(out, ctypes.c_uint64))
         if rc != 0:

@@ -44,9 +44,10 @@
 //   9 LT coefficients taken from the even powers (b^(p-1-2m) for c_{2m+1})
 //  10 the automorphism's negacyclic sign dropped (X^N taken as +1)
 //  11 the rotate-and-add reduction without its row exchange
-//  12 BETWEEN combined as 1 - b + a instead of 1 - b - a
+//  12 BETWEEN's first factor taken as a instead of 1 - a
 //  13 LT's first giant step taken as w^128 instead of w^256
 //  14 the noise budget without the factor 2 of its definition
+//  15 the per-prime relinearisation key used only below the fine depth, not at it
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
@@ -513,16 +514,28 @@ static int brv(int x, int bits) {
 typedef std::vector<Big> Poly;  // N big-integer coefficients
 
 // A key-switching key from a secret s' to s: k_a = (-(a_a s + e_a) + P g_a s',
-// a_a) mod QP for the digits a < D (groups of DIGIT_PRIMES data primes, one
-// special prime), kept in big-integer form and transformed over the oracle
-// primes used for the exact products.
+// a_a) mod QP for the digits a < D, one special prime.  Digit a is the residue
+// modulo Q_a, the product of the a-th group of `dp` consecutive data primes (the
+// last group is shorter when dp does not divide L).  The key is kept in
+// big-integer form and transformed over the oracle primes used for the exact
+// products.
 struct KsKey {
+  int dp = 0, D = 0;                        // data primes per digit, digits
+  std::vector<std::vector<uint64_t>> grp;   // the primes of each digit
+  std::vector<Big> Qa;                      // their products
   std::vector<Poly> k0, k1;
   int nprimes = 0;
   std::vector<uint64_t> ntt;      // [i][comp][prime][N]
 };
 
-enum { DIGIT_PRIMES = 3 };  // data primes per key-switching digit
+// Key-switching digit groupings.  The relinearisation and Galois keys use
+// groups of c.dp data primes (3 unless set otherwise).  Products whose output
+// lies at multiplicative depth <= c.fine_depth are relinearised with a second
+// key of one prime per digit (the decomposition of SEAL): its key-switching
+// noise |digit| sqrt(N) / P is about 2^-110 of the three-prime key's, which
+// matters only while the product's own noise is still small, i.e. at the first
+// levels of a chain.
+enum { DIGIT_PRIMES_DEFAULT = 3, FINE_OBJ = 16 };  // fine key digits draw with object index 16 + i
 
 struct Ctx {
   int logn, N, L;
@@ -535,14 +548,13 @@ struct Ctx {
   std::vector<NttPlan> plans;     // one per oracle prime
   NttPlan tplan;                  // plaintext-modulus transform (batch encoding)
   std::vector<Crt> crt_prefix;    // crt over the first k oracle primes, k = 1..
-  // key-switching digits: consecutive groups of DIGIT_PRIMES data primes,
-  // digit a = [d]_{Q_a}, Q_a the product of group a's primes
-  int D = 0;
-  std::vector<std::vector<uint64_t>> grp;
-  std::vector<Big> Qa;
-  // relinearisation key and Galois keys (switching from s^2, resp. tau_g(s), to s)
-  bool have_rk = false;
-  KsKey rk;
+  // key-switching digit groupings (see KsKey): dp data primes per digit for the
+  // relinearisation and Galois keys; products at output depth <= fine_depth
+  // use the per-prime relinearisation key rk1
+  int dp = DIGIT_PRIMES_DEFAULT, fine_depth = 0;
+  // relinearisation keys and Galois keys (switching from s^2, resp. tau_g(s), to s)
+  bool have_rk = false, have_rk1 = false;
+  KsKey rk, rk1;
   std::map<uint64_t, KsKey> gk;   // by Galois element g
   std::vector<uint32_t> lt_h;     // LT polynomial's odd coefficients (computed on first use)
 };
@@ -664,7 +676,8 @@ static Big round_t_over_Q(const Ctx& c, const Big& d) {
 
 // ---- ciphertext <-> residue arrays (layout [2][L][N], canonical residues) ----
 struct Ct {
-  Poly c0, c1;  // coefficients in [0, Q)
+  Poly c0, c1;    // coefficients in [0, Q)
+  int depth = 0;  // multiplicative depth from fresh inputs (selects the relinearisation key)
 };
 static Poly poly_from_rns(const Ctx& c, const uint64_t* res /*[L][N]*/) {
   Poly p(c.N);
@@ -718,6 +731,7 @@ static void encode_slots(const Ctx& c, const uint32_t* slots, uint64_t* m) {
 // ---- scheme operations ----
 static Ct ct_sub(const Ctx& c, const Ct& x, const Ct& y) {
   Ct r;
+  r.depth = std::max(x.depth, y.depth);
   r.c0.resize(c.N);
   r.c1.resize(c.N);
   for (int j = 0; j < c.N; ++j) {
@@ -735,6 +749,7 @@ static Ct ct_sub_const(const Ctx& c, const Ct& x, uint64_t v) {
 // 1 - ct = (Delta - c0, -c1)
 static Ct ct_one_minus(const Ctx& c, const Ct& x) {
   Ct r;
+  r.depth = x.depth;
   r.c0.resize(c.N);
   r.c1.resize(c.N);
   for (int j = 0; j < c.N; ++j) {
@@ -747,19 +762,20 @@ static Ct ct_one_minus(const Ctx& c, const Ct& x) {
 
 // Key switching of (d0, d1, d2), coefficients in [0, Q), where d2 is to be
 // multiplied by the key's source secret: (d0, d1) + round(sum_a [d2]_{Q_a} k_a / P)
-// mod Q, digits a < D over groups of DIGIT_PRIMES data primes.  With the relinearisation key this is relinearisation (source s^2);
-// with a Galois key it completes an automorphism (source tau_g(s)).
+// mod Q, digits a < D over the key's groups of data primes.  With a
+// relinearisation key this is relinearisation (source s^2); with a Galois key
+// it completes an automorphism (source tau_g(s)).
 static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d1, const Poly& d2) {
-  int N = c.N, D = c.D, k = K.nprimes;
+  int N = c.N, D = K.D, k = K.nprimes;
   // u = sum_a digit_a * k_a  (exact integer negacyclic products, then mod QP)
   std::vector<uint64_t> res0((size_t)k * N), res1((size_t)k * N);
   std::vector<Big> digit((size_t)D * N);  // digit_a = [d2]_{Q_a}
   for (int a = 0; a < D; ++a)
 #if ORC_MUTANT == 7
     for (int j = 0; j < N; ++j)
-      digit[(size_t)a * N + j] = mod_primes(d2[j], big_u64(c.grp[a][0]), std::vector<uint64_t>{c.grp[a][0]});
+      digit[(size_t)a * N + j] = mod_primes(d2[j], big_u64(K.grp[a][0]), std::vector<uint64_t>{K.grp[a][0]});
 #else
-    for (int j = 0; j < N; ++j) digit[(size_t)a * N + j] = mod_primes(d2[j], c.Qa[a], c.grp[a]);
+    for (int j = 0; j < N; ++j) digit[(size_t)a * N + j] = mod_primes(d2[j], K.Qa[a], K.grp[a]);
 #endif
   std::vector<uint64_t> Dg(N), acc0(N), acc1(N);
   for (int pi = 0; pi < k; ++pi) {
@@ -812,12 +828,23 @@ static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d
   return out;
 }
 
-static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& d2) {
+// Relinearisation of a product at multiplicative depth `depth`: the per-prime
+// key when depth <= fine_depth, else the key of dp-prime digits.
+static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& d2, int depth) {
   if (!c.have_rk) fail("relinearisation key not set");
+#if ORC_MUTANT == 15
+  if (depth < c.fine_depth) {
+#else
+  if (depth <= c.fine_depth) {
+#endif
+    if (!c.have_rk1) fail("per-prime relinearisation key not set");
+    return key_switch(c, c.rk1, d0, d1, d2);
+  }
   return key_switch(c, c.rk, d0, d1, d2);
 }
 
-// textbook multiplication + relinearisation
+// textbook multiplication + relinearisation; the product lies one level below
+// the deeper operand
 static Ct ct_mul_relin(const Ctx& c, const Ct& a, const Ct& b) {
   int N = c.N;
   Poly a0(N), a1(N), b0(N), b1(N);
@@ -834,7 +861,9 @@ static Ct ct_mul_relin(const Ctx& c, const Ct& a, const Ct& b) {
     d1[j] = mod_Q(c, round_t_over_Q(c, d1[j]));
     d2[j] = mod_Q(c, round_t_over_Q(c, d2[j]));
   }
-  return relinearize(c, d0, d1, d2);
+  Ct r = relinearize(c, d0, d1, d2, std::max(a.depth, b.depth) + 1);
+  r.depth = std::max(a.depth, b.depth) + 1;
+  return r;
 }
 
 static Poly secret_poly(const Ctx& c, const int8_t* s) {
@@ -867,16 +896,31 @@ static Poly phase(const Ctx& c, const Ct& ct, const int8_t* s) {
 // uniform mod QP (residue j drawn with counter (k, j, obj_base | a, dom_a)),
 // e_a centred binomial (counter (k, 0, obj_base | a, dom_e)).
 // `out` (may be null): uint64 [D][2][L+1][N].
+// The digit groups of a key with dp data primes per digit: primes
+// q_{a dp} .. q_{min(L, (a+1) dp) - 1} form digit a.
+static void set_digit_groups(const Ctx& c, int dp, KsKey& K) {
+  K.dp = dp;
+  K.D = (c.L + dp - 1) / dp;
+  K.grp.assign(K.D, {});
+  K.Qa.assign(K.D, big_u64(1));
+  for (int a = 0; a < K.D; ++a)
+    for (int i = a * dp; i < std::min(c.L, (a + 1) * dp); ++i) {
+      K.grp[a].push_back(c.q[i]);
+      K.Qa[a] = big_mul_u64(K.Qa[a], c.q[i]);
+    }
+}
+
 static void make_ks_key(const Ctx& c, uint64_t seed, const Poly& s, const Poly& src, uint32_t dom_a, uint32_t dom_e,
-                        uint32_t obj_base, KsKey& K, uint64_t* out) {
-  int N = c.N, L = c.L, D = c.D;
+                        uint32_t obj_base, int dp, KsKey& K, uint64_t* out) {
+  set_digit_groups(c, dp, K);
+  int N = c.N, L = c.L, D = K.D;
   uint32_t w[4];
   K.k0.assign(D, Poly(N));
   K.k1.assign(D, Poly(N));
   std::vector<uint64_t> res(L + 1);
   for (int a = 0; a < D; ++a) {
     Big g = big_zero();
-    for (int i = a * DIGIT_PRIMES; i < std::min(L, (a + 1) * DIGIT_PRIMES); ++i) {
+    for (int i = a * dp; i < std::min(L, (a + 1) * dp); ++i) {
       uint64_t rr;
       Big qhat = mag_divmod_u64(c.Q, c.q[i], &rr);
       uint64_t qhat_inv = invmod(big_mod_u64(qhat, c.q[i]), c.q[i]);
@@ -916,7 +960,7 @@ static void make_ks_key(const Ctx& c, uint64_t seed, const Poly& s, const Poly& 
   }
   // transforms over the oracle primes: |u| < D N max(Q_a) QP
   int dbits = 0;
-  for (const Big& M : c.Qa) dbits = std::max(dbits, big_bits(M));
+  for (const Big& M : K.Qa) dbits = std::max(dbits, big_bits(M));
   int bound = dbits + big_bits(c.QP) + c.logn + (int)std::ceil(std::log2((double)D + 1)) + 1;
   int k = primes_needed(c, bound);
   K.nprimes = k;
@@ -956,6 +1000,7 @@ static Poly automorph(const Ctx& c, const Poly& a, uint64_t g, const Big* M) {
 // ct -> tau_g(ct), which decrypts under tau_g(s) to tau_g(m)
 static Ct ct_automorph(const Ctx& c, const Ct& x, uint64_t g) {
   Ct r;
+  r.depth = x.depth;
   r.c0 = automorph(c, x.c0, g, &c.Q);
   r.c1 = automorph(c, x.c1, g, &c.Q);
   return r;
@@ -968,7 +1013,9 @@ static Ct ct_rotate(const Ctx& c, const Ct& x, uint64_t g) {
   if (it == c.gk.end()) fail("Galois key not generated");
   Ct t = ct_automorph(c, x, g);
   Poly zero(c.N, big_zero());
-  return key_switch(c, it->second, t.c0, zero, t.c1);
+  Ct r = key_switch(c, it->second, t.c0, zero, t.c1);
+  r.depth = x.depth;
+  return r;
 }
 
 extern "C" {
@@ -1014,21 +1061,27 @@ void* orc_create(int logn, int L, const uint64_t* q, uint64_t P, uint64_t t) {
   for (size_t k = 1; k <= c->om.size(); ++k)
     c->crt_prefix[k - 1].init(std::vector<uint64_t>(c->om.begin(), c->om.begin() + k));
   c->tplan.init(logn, t);
-  c->D = (L + DIGIT_PRIMES - 1) / DIGIT_PRIMES;
-  c->grp.resize(c->D);
-  c->Qa.resize(c->D);
-  for (int a = 0; a < c->D; ++a) {
-    Big M = big_u64(1);
-    for (int i = a * DIGIT_PRIMES; i < std::min(L, (a + 1) * DIGIT_PRIMES); ++i) {
-      c->grp[a].push_back(c->q[i]);
-      M = big_mul_u64(M, c->q[i]);
-    }
-    c->Qa[a] = M;
-  }
   return c;
 }
 
-int orc_num_digits(void* h) { return ((Ctx*)h)->D; }
+// Digits of the relinearisation and Galois keys: ceil(L / dp).
+int orc_num_digits(void* h) {
+  Ctx* c = (Ctx*)h;
+  return (c->L + c->dp - 1) / c->dp;
+}
+
+// Key-switching digit groupings (before orc_keygen): dp data primes per digit
+// for the relinearisation and Galois keys (1 .. L), and the depth up to which
+// products are relinearised with the per-prime key instead (0 = never).
+int orc_set_digits(void* h, int dp, int fine_depth) {
+  Ctx* c = (Ctx*)h;
+  if (dp < 1 || dp > c->L || fine_depth < 0) return -1;
+  c->dp = dp;
+  c->fine_depth = fine_depth;
+  c->have_rk = c->have_rk1 = false;
+  c->gk.clear();
+  return 0;
+}
 
 void orc_destroy(void* h) { delete (Ctx*)h; }
 
@@ -1102,8 +1155,28 @@ int orc_keygen(void* h, uint64_t seed, int8_t* s_out, uint64_t* rk_out) {
     s_out[k] = (int8_t)sample_ternary(w);
   }
   Poly s = secret_poly(c, s_out);
-  make_ks_key(c, seed, s, poly_mul_exact(c, s, s), DOM_A_RK, DOM_E_RK, 0, c.rk, rk_out);
+  Poly s2 = poly_mul_exact(c, s, s);
+  make_ks_key(c, seed, s, s2, DOM_A_RK, DOM_E_RK, 0, c.dp, c.rk, rk_out);
   c.have_rk = true;
+  if (c.fine_depth > 0) {
+    make_ks_key(c, seed, s, s2, DOM_A_RK, DOM_E_RK, FINE_OBJ, 1, c.rk1, nullptr);
+    c.have_rk1 = true;
+  }
+  return 0;
+}
+
+// The per-prime relinearisation key made by orc_keygen when fine_depth > 0:
+// uint64 [L][2][L+1][N] (digit i = [d2]_{q_i}, drawn with object index 16 + i).
+int orc_fine_key(void* h, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk1) return -2;
+  for (int a = 0; a < c.rk1.D; ++a)
+    for (int comp = 0; comp < 2; ++comp)
+      for (int j = 0; j <= c.L; ++j)
+        for (int k = 0; k < c.N; ++k) {
+          const Big& v = comp ? c.rk1.k1[a][k] : c.rk1.k0[a][k];
+          out[((((size_t)a * 2 + comp) * (c.L + 1)) + j) * c.N + k] = big_mod_u64(v, c.qp[j]);
+        }
   return 0;
 }
 
@@ -1188,6 +1261,19 @@ int orc_mul_relin(void* h, const uint64_t* a, const uint64_t* b, uint64_t* out) 
   ct_to_rns(c, ct_mul_relin(c, ct_from_rns(c, a), ct_from_rns(c, b)), out);
   return 0;
 }
+// The same product for operands at multiplicative depths da and db (the
+// product's depth max(da, db) + 1 selects the relinearisation key), e.g. a
+// column (depth 0) times a predicate mask (SELECT, Eq. 5).
+int orc_mul_relin_depth(void* h, const uint64_t* a, int da, const uint64_t* b, int db, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk) return -2;
+  if (da < 0 || db < 0) return -1;
+  Ct A = ct_from_rns(c, a), B = ct_from_rns(c, b);
+  A.depth = da;
+  B.depth = db;
+  ct_to_rns(c, ct_mul_relin(c, A, B), out);
+  return 0;
+}
 
 // EQ: 1 - (x - y)^(2^squarings); y == NULL means x - const_val.
 // squarings = 16 gives the paper's predicate for p = 65537.
@@ -1253,6 +1339,7 @@ static std::vector<uint32_t> lt_odd_coefficients(uint64_t p) {
 // c * ct for an integer c in [0, t), coefficient-wise mod Q
 static Ct ct_scale(const Ctx& c, const Ct& a, uint64_t k) {
   Ct r;
+  r.depth = a.depth;
   r.c0.resize(c.N);
   r.c1.resize(c.N);
   for (int j = 0; j < c.N; ++j) {
@@ -1263,6 +1350,7 @@ static Ct ct_scale(const Ctx& c, const Ct& a, uint64_t k) {
 }
 static Ct ct_add(const Ctx& c, const Ct& a, const Ct& b) {
   Ct r;
+  r.depth = std::max(a.depth, b.depth);
   r.c0.resize(c.N);
   r.c1.resize(c.N);
   for (int j = 0; j < c.N; ++j) {
@@ -1298,26 +1386,43 @@ static Ct ct_linear(const Ctx& c, const std::vector<const Ct*>& cts, const std::
         buf[w] = (uint64_t)(acc[w] % c.q[i]);
       }
   Ct r = ct_from_rns(c, buf.data());
+  for (const Ct* x : cts) r.depth = std::max(r.depth, x->depth);
   return ct_add(c, r, ct_constant(c, coef0));
 }
 
-// The evaluation schedule of f(z) (both the oracle and the CUDA library follow it):
-//   w = z z;  B_1 = w;  B_i = B_{i/2}^2 (i even) or B_{i-1} B_1 (i odd), i < 256;
-//   G_1 = B_128^2 (= w^256);  G_j = G_{j/2}^2 (j even) or G_{j-1} G_1 (j odd), j <= 128;
-//   H_j = Delta h_{256 j} + sum_{i=1}^{255} h_{256 j + i} B_i   (j < 128);
-//   h = H_0 + sum_{j=1}^{127} H_j G_j;   out = z h - ((p-1)/2) G_128.
+// The evaluation schedule of f(z) (both the oracle and the CUDA library follow
+// it).  Every power is the product of its largest power-of-two part and the
+// rest, so the power e sits at depth ceil(log2 e) above its base:
+//   w = z z;  B_1 = w;  B_i = B_{i/2}^2 (i a power of 2) or B_{2^k} B_{i-2^k}
+//   (2^k < i < 2^(k+1)), i < 256;  depth(B_i) = 1 + ceil(log2 i) <= 9;
+//   G_1 = B_128^2 (= w^256, depth 9);  G_j likewise from G_{2^k} and G_{j-2^k},
+//   j <= 128;  depth(G_j) = 9 + ceil(log2 j) <= 16;
+//   H_j = Delta h_{256 j} + sum_{i=1}^{255} h_{256 j + i} B_i   (j < 128, depth 9);
+//   h = H_0 + sum_{j=1}^{127} H_j G_j (depth 17);   out = z h - ((p-1)/2) G_128 (depth 18).
+// 511 multiplications in all.
+static int top_pow2(int i) {  // largest power of two <= i (i >= 1)
+  int k = 1;
+  while (2 * k <= i) k *= 2;
+  return k;
+}
 static Ct lt_eval(const Ctx& c, const Ct& z, const std::vector<uint32_t>& hc) {
   const int BS = 256, GS = 128;
   Ct w = ct_mul_relin(c, z, z);
   std::vector<Ct> B(BS), G(GS + 1);
   B[1] = w;
-  for (int i = 2; i < BS; ++i) B[i] = (i % 2 == 0) ? ct_mul_relin(c, B[i / 2], B[i / 2]) : ct_mul_relin(c, B[i - 1], B[1]);
+  for (int i = 2; i < BS; ++i) {
+    const int k = top_pow2(i);
+    B[i] = (k == i) ? ct_mul_relin(c, B[i / 2], B[i / 2]) : ct_mul_relin(c, B[k], B[i - k]);
+  }
 #if ORC_MUTANT == 13
   G[1] = B[128];
 #else
   G[1] = ct_mul_relin(c, B[128], B[128]);
 #endif
-  for (int j = 2; j <= GS; ++j) G[j] = (j % 2 == 0) ? ct_mul_relin(c, G[j / 2], G[j / 2]) : ct_mul_relin(c, G[j - 1], G[1]);
+  for (int j = 2; j <= GS; ++j) {
+    const int k = top_pow2(j);
+    G[j] = (k == j) ? ct_mul_relin(c, G[j / 2], G[j / 2]) : ct_mul_relin(c, G[k], G[j - k]);
+  }
   std::vector<const Ct*> ptrs;
   for (int i = 1; i < BS; ++i) ptrs.push_back(&B[i]);
   Ct h;
@@ -1362,6 +1467,7 @@ int orc_linear(void* h, const uint64_t* cts, int n, const uint64_t* coef, uint64
 // v - x for a plaintext constant v: (Delta v - c0, -c1) mod Q
 static Ct ct_const_minus(const Ctx& c, const Ct& x, uint64_t v) {
   Ct r;
+  r.depth = x.depth;
   r.c0.resize(c.N);
   r.c1.resize(c.N);
   for (int j = 0; j < c.N; ++j) {
@@ -1372,12 +1478,11 @@ static Ct ct_const_minus(const Ctx& c, const Ct& x, uint64_t v) {
   return r;
 }
 
-// BETWEEN (Sec. 4.2.2): the combination of the two comparisons x >= lo and
-// x <= hi.  With a = LT(x, lo) = f(x - lo) and b = LT(hi, x) = f(hi - x), f the
+// BETWEEN (Sec. 4.2.2): the product of the two comparisons x >= lo and x <= hi.
+// With a = LT(x, lo) = f(x - lo) and b = LT(hi, x) = f(hi - x), f the
 // comparison polynomial of Eq. 4 (valid while x, lo, hi lie in [0, (p-1)/2]),
-// the product (1 - a)(1 - b) equals 1 - a - b for lo <= hi, because x < lo
-// and x > hi exclude each other; the difference form is evaluated, one level
-// shallower than the product.  Empty ranges (lo > hi) are rejected.
+// BETWEEN = (1 - a)(1 - b), one multiplication with relinearisation after the
+// two comparisons (depth 19).  Empty ranges (lo > hi) are rejected.
 int orc_between(void* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* out) {
   Ctx& c = *(Ctx*)h;
   if (!c.have_rk) return -2;
@@ -1387,9 +1492,9 @@ int orc_between(void* h, const uint64_t* x, uint64_t lo, uint64_t hi, uint64_t* 
   Ct below = lt_eval(c, ct_sub_const(c, X, lo), hc);    // [x < lo]
   Ct above = lt_eval(c, ct_const_minus(c, X, hi), hc);  // [hi < x]
 #if ORC_MUTANT == 12
-  ct_to_rns(c, ct_add(c, ct_one_minus(c, above), below), out);
+  ct_to_rns(c, ct_mul_relin(c, below, ct_one_minus(c, above)), out);
 #else
-  ct_to_rns(c, ct_sub(c, ct_one_minus(c, above), below), out);  // (1 - b) - a
+  ct_to_rns(c, ct_mul_relin(c, ct_one_minus(c, below), ct_one_minus(c, above)), out);  // (1 - a)(1 - b)
 #endif
   return 0;
 }
@@ -1443,7 +1548,7 @@ int orc_relin(void* h, const uint64_t* d3, uint64_t* out) {
   if (!c.have_rk) return -2;
   size_t s = (size_t)c.L * c.N;
   Poly d0 = poly_from_rns(c, d3), d1 = poly_from_rns(c, d3 + s), d2 = poly_from_rns(c, d3 + 2 * s);
-  ct_to_rns(c, relinearize(c, d0, d1, d2), out);
+  ct_to_rns(c, relinearize(c, d0, d1, d2, 1), out);  // a product of fresh ciphertexts
   return 0;
 }
 
@@ -1463,7 +1568,7 @@ int orc_galois_keygen(void* h, uint64_t seed, const int8_t* s_in, uint64_t g, ui
   if (g % 2 == 0 || g >= 2 * (uint64_t)c.N) return -1;
   Poly s = secret_poly(c, s_in);
   Poly sg = automorph(c, s, g, nullptr);
-  make_ks_key(c, seed, s, sg, DOM_A_GK, DOM_E_GK, (uint32_t)(g << 5), c.gk[g], gk_out);
+  make_ks_key(c, seed, s, sg, DOM_A_GK, DOM_E_GK, (uint32_t)(g << 5), c.dp, c.gk[g], gk_out);
   return 0;
 }
 

@@ -27,14 +27,17 @@ CASES = [
     (9, "LT coefficients from the even powers", pins.test_lt_polynomial_is_the_paper_sum),
     (10, "automorphism without the negacyclic sign", lambda o: pins.test_automorphism_permutes_slots(o, 5)),
     (11, "reduction without the row exchange", pins.test_count_and_sum_closed_form_n16),
-    (12, "BETWEEN as 1 - b + a", pins.test_between_closed_form_n16),
+    (12, "BETWEEN's first factor a instead of 1 - a", pins.test_between_closed_form_n16),
     (13, "first giant step w^128", pins.test_lt_closed_form_n16),
     (14, "noise budget without its factor 2", pins.test_noise_budget_bruteforce),
+    (15, "per-prime key only below the fine depth", lambda o: pins.check_fine_depth_selection(oracle.build_mutant(15))),
 ]
 
 
 def _name(pin):
-    return pin.__name__[5:] if pin.__name__.startswith("test_") else "automorphism_permutes_slots"
+    if pin.__name__.startswith("test_"):
+        return pin.__name__[5:]
+    return "fine_depth_selection" if "check_fine_depth_selection" in pin.__code__.co_names else "automorphism_permutes_slots"
 
 
 def _oracle16(lib_path=None):

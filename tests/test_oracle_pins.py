@@ -314,6 +314,92 @@ def test_relinearisation_bruteforce(orc16):
     assert to_ints(got[1], o.q) == out[1]
 
 
+def _relin_bruteforce(o, d3, rk, groups):
+    """(d0, d1) + round(sum_a [d2]_{Q_a} rk_a / P) mod Q with Python integers and a
+    schoolbook product; `groups`: the data-prime indices of each digit."""
+    N, P, Q = o.N, o.P, math.prod(o.q)
+    QP = Q * P
+    D = [to_ints(d3[k], o.q) for k in range(3)]
+    out = []
+    for c in range(2):
+        u = [0] * N
+        for a, grp in enumerate(groups):
+            Qa = math.prod(o.q[i] for i in grp)
+            dig = [v % Qa for v in D[2]]
+            u = [x + y for x, y in zip(u, negacyclic_schoolbook(dig, to_ints(rk[a][c], o.q + [P]), N))]
+        ks = []
+        for v in u:
+            v %= QP
+            r = v % P
+            r = r - P if r > (P - 1) // 2 else r
+            ks.append((v - r) // P)
+        out.append([(a + b) % Q for a, b in zip(D[c], ks)])
+    return out
+
+
+def _key_relation_ok(o, rk, groups, s2):
+    """rk_a0 + rk_a1 s = -e_a + P g_a s^2 mod QP with |e_a| <= 21, g_a = (Q/Q_a) [(Q/Q_a)^{-1}]_{Q_a}."""
+    N, P, Q = o.N, o.P, math.prod(o.q)
+    QP = Q * P
+    sl = [int(v) for v in o.s]
+    for a, grp in enumerate(groups):
+        Qa = math.prod(o.q[i] for i in grp)
+        g_a = (Q // Qa) * pow(Q // Qa, -1, Qa)
+        rk0, rk1 = to_ints(rk[a][0], o.q + [P]), to_ints(rk[a][1], o.q + [P])
+        lhs = [(x + y) % QP for x, y in zip(rk0, negacyclic_schoolbook(rk1, sl, N))]
+        err = [(v - P * g_a * w) % QP for v, w in zip(lhs, s2)]
+        if max(abs(e - QP if e > QP // 2 else e) for e in err) > 21:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("dp", [1, 2, 3])
+def test_digit_groupings_keys_and_relinearisation_bruteforce(dp):
+    """Key switching with digits of dp consecutive data primes (the last group
+    shorter when dp does not divide L = 15): the keys satisfy their defining
+    relation and relinearisation equals its integer definition, for each
+    grouping."""
+    o = oracle.Oracle(4, dp=dp)
+    o.keygen(7)
+    groups = [list(range(a * dp, min(o.L, (a + 1) * dp))) for a in range(o.D)]
+    assert o.D == -(-o.L // dp) and o.rk.shape[0] == o.D
+    sl = [int(v) for v in o.s]
+    assert _key_relation_ok(o, o.rk, groups, negacyclic_schoolbook(sl, sl, o.N))
+    rng = np.random.default_rng(60 + dp)
+    d3 = np.stack([np.stack([rng.integers(0, qi, o.N, dtype=np.uint64) for qi in o.q]) for _ in range(3)])
+    got = o.relin(d3)
+    want = _relin_bruteforce(o, d3, o.rk, groups)
+    assert to_ints(got[0], o.q) == want[0] and to_ints(got[1], o.q) == want[1]
+
+
+def test_fine_depth_selects_the_per_prime_key_bruteforce():
+    """With fine_depth F = 1 the oracle keeps a second relinearisation key of one
+    prime per digit (its own relation holds) and relinearises a product of fresh
+    ciphertexts (depth 1) with it, a product at depth 2 with the three-prime
+    key: each equals tensor-and-round followed by the integer key switching of
+    its key, by brute force."""
+    check_fine_depth_selection()
+
+
+def check_fine_depth_selection(lib_path=None):
+    o = oracle.Oracle(4, fine_depth=1, lib_path=lib_path)
+    o.keygen(7)
+    fine = o.fine_key()
+    sl = [int(v) for v in o.s]
+    s2 = negacyclic_schoolbook(sl, sl, o.N)
+    per_prime = [[i] for i in range(o.L)]
+    three = [[3 * a, 3 * a + 1, 3 * a + 2] for a in range(5)]
+    assert _key_relation_ok(o, fine, per_prime, s2)
+    rng = np.random.default_rng(61)
+    a = o.encrypt(rng.integers(0, T, o.N).astype(np.uint32), seed=3, ct_index=0)
+    b = o.encrypt(rng.integers(0, T, o.N).astype(np.uint32), seed=3, ct_index=1)
+    d3 = o.tensor_round(a, b)
+    for depth_a, key, groups in [(0, fine, per_prime), (1, o.rk, three)]:
+        got = o.mul_relin(a, b, depth_a=depth_a)
+        want = _relin_bruteforce(o, d3, key, groups)
+        assert to_ints(got[0], o.q) == want[0] and to_ints(got[1], o.q) == want[1], depth_a
+
+
 def test_homomorphic_product_closed_form(orc16):
     o = orc16
     rng = np.random.default_rng(8)
@@ -639,9 +725,9 @@ def test_join_closed_form_n16(orc16):
 
 def test_between_closed_form_n16(orc16):
     """BETWEEN (Sec. 4.2.2) decrypts to [lo <= x <= hi] on 15-bit inputs,
-    including both bounds and lo = hi.  The difference form 1 - LT(x, lo) -
-    LT(hi, x) equals the product (1 - LT(x, lo)) (1 - LT(hi, x)) slot by slot,
-    checked here after decryption; an empty range (lo > hi) is rejected."""
+    including both bounds and lo = hi, and equals the product (1 - LT(x, lo))
+    (1 - LT(hi, x)) of the two comparisons slot by slot, checked here after
+    decryption; an empty range (lo > hi) is rejected."""
     o = orc16
     rng = np.random.default_rng(40)
     x = rng.integers(0, (T - 1) // 2 + 1, o.N).astype(np.uint32)
