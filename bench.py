@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched-vs-plain comparison")
+    ap.add_argument("--no-extras", action="store_true", help="default line: skip the 2^28-slot and LT extras")
     ap.add_argument("--ncu-region", action="store_true",
                     help="after warm-up, run one extra step between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -53,9 +55,9 @@ def parse():
 
 def workload(cfg: str):
     if cfg == "between":
-        return dict(n_ct=64, op="between", desc="x BETWEEN 1000 AND 20000 (Sec. 4.2.2: 1 - LT(x, lo) - LT(hi, x)): "
+        return dict(n_ct=64, op="between", desc="x BETWEEN 1000 AND 20000 (Sec. 4.2.2: (1 - LT(x, lo)) (1 - LT(hi, x))): "
                     "2^21 slots = 64 BFV ciphertexts, x in [0, 2^15], N=32768, L=15, p=65537; two LT evaluations "
-                    "(1022 multiplications) per ciphertext, bit-exact")
+                    "and their product (1023 multiplications) per ciphertext, bit-exact")
     if cfg == "join":
         return dict(n_ct=64, op="join", n_rows=16, desc="equi-join A.key = B.key (Sec. 4.2.2, Extract + Broadcast): "
                     "A = 2^21 rows (64 BFV ciphertexts), 16 B rows with 2 attributes; 1024 EQ chains, 2048 products, "
@@ -138,7 +140,11 @@ N_SM, MUL_LANES_PER_SM_CLK, MUL_PER_BUTTERFLY, MUL_PER_MAC = 148, 32, 9, 8
 MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-switch MAC
 # ciphertext multiplications with relinearisation per N units of each workload
 # (per ciphertext; per ciphertext and B row for join); rotations are not counted
-HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1022, "sum": 17, "rotsum": 0, "join": 18}
+HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "sum": 17, "rotsum": 0, "join": 18}
+# Shoup products of the three-prime digit recombination per ciphertext and squaring,
+# in units of N: per digit (5) and target prime (16), two products, one for the
+# digit's second prime, none for its first: 5 (14 x 2 + 1) = 145
+DIGIT_PRODUCTS_PER_HMULT = 145
 
 
 KERNEL_SOURCES = {  # files whose text determines a kernel's code
@@ -195,7 +201,7 @@ class OracleSample:
         "batched": (1, 16, 1, 0, ""),
         "in": (1, 16, 1, 0, "the additions of the IN sum"),
         "lt": (1, 511, 0, 0, "the 128 inner sums of 255 scalar products and the additions"),
-        "between": (3, 1022, 1, 0, "the 2 x 128 inner sums of 255 scalar products and the additions"),
+        "between": (3, 1023, 2, 0, "the 2 x 128 inner sums of 255 scalar products and the additions"),
         "sum": (1, 17, 1, 15 / 2048, "the additions"),
         "rotsum": (0, 0, 0, 15, "the additions"),
         "join": (1, 18, 1, 45 / 64, "the plaintext products of Extract and the additions"),
@@ -395,10 +401,10 @@ def run_libhp(args):
     # one profiled warm-up step over every kernel class: shares and the dominant kernel
     ctx.profile((1 << len(hp.PROFILE_CLASSES)) - 1)
     step()
-    shares = {}
+    shares, works = {}, {}
     for c, name in enumerate(hp.PROFILE_CLASSES):
         ms, n, w = ctx.profile_read(c)
-        shares[c] = ms
+        shares[c], works[c] = ms, w
     ctx.profile(0)
     dom = max(shares, key=shares.get)
     tot = sum(shares.values())
@@ -506,6 +512,17 @@ def run_libhp(args):
     roof["probe_butterfly_per_s"] = hp.probe_peak(0)
     roof["probe_mac_per_s"] = hp.probe_peak(1)
     roof["traffic"] = load_traffic(kernel, ctx_tile(ctx))
+    # whole path: the step's algorithmic butterflies (every transform), digit
+    # recombination products (counted at the butterfly rate) and key-switching
+    # multiply-accumulates at the derived ALU ceilings, against the step time;
+    # the base conversions run on the tensor cores and are not counted
+    butterflies = sum(works[c] for c in NTT_CLASSES)
+    digit_products = DIGIT_PRODUCTS_PER_HMULT * N * n_ct * HMULT_PER_CT[wl["op"]] * wl.get("n_const", 1)
+    ks_macs = works.get(8, 0.0)
+    t_ideal = (butterflies + digit_products) / (mul_rate / MUL_PER_BUTTERFLY) + ks_macs / (mul_rate / MUL_PER_MAC)
+    roof["path_frac"] = t_ideal / (ms_per_step / 1e3)
+    roof["path_work_per_step"] = {"butterflies": butterflies, "digit_products": digit_products, "ks_macs": ks_macs,
+                                  "ideal_ms": t_ideal * 1e3}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -521,6 +538,17 @@ def run_libhp(args):
     # ---- end to end through the public API with pinned host buffers ----
     if not args.no_e2e and wl["op"] not in ("lt", "between", "in", "sum", "rotsum", "join"):
         line["e2e"] = e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist)
+    # ---- the headline line also carries config 3 (batched vs plain) and extras ----
+    if wl["op"] == "ctct" and world == 1 and not (args.no_batched and args.no_extras) and not args.n_ct:
+        del cx, cy, out
+        torch.cuda.empty_cache()
+        if not args.no_batched:
+            r = batched_measure(ctx, 1, 1, stream)
+            r["plain_elements_per_s"] = value
+            r["packed_batched_over_plain"] = r["packed_batched_elements_per_s"] / value
+            line["batched_vs_plain"] = r
+        if not args.no_extras:
+            line["extras"] = extras_measure(ctx, stream)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:
         v, secs, desc = OracleSample(wl["op"]).time(8)
@@ -541,6 +569,68 @@ def run_libhp(args):
 
 def ctx_tile(ctx):
     return ctx.tile()
+
+
+def extras_measure(ctx, stream):
+    """Two more workloads on the same handle, one timed pass each after one
+    warm-up pass: config 4 (EQ against a constant over 2^28 slots = 8192
+    ciphertexts, the closed form checked on three of them) and LT (Eq. 4) over 16
+    ciphertext pairs at N = 32768 (the closed form checked on every slot)."""
+    import numpy as np
+    import torch
+
+    from paper_2602_24271_b300 import hp
+    from paper_2602_24271_b300.inputs import eq_pair_columns
+
+    N = ctx.N
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # config 4: 2^28 slots against a constant (x drawn per chunk of 128 ciphertexts)
+    n28, cval = 8192, 4242
+    x28 = ctx.ct_empty(n28)
+    probe = {}
+    for c0 in range(0, n28, 128):
+        xs, _ = eq_pair_columns(128 * N, seed=SEED_DATA + 1000 + c0)
+        xs[::7] = cval
+        x28[c0:c0 + 128] = ctx.encrypt(xs.reshape(128, N), seed=SEED_DATA + 3, ct_index0=c0)
+        for c in (0, n28 // 2, n28 - 1):
+            if c0 <= c < c0 + 128:
+                probe[c] = xs[(c - c0) * N:(c - c0 + 1) * N]
+    o28 = ctx.ct_empty(n28)
+    ms = timed(lambda: ctx.run(hp.HP_EQ_CT_CONST, x28, None, cval, out=o28, stream=stream))
+    dec = ctx.decrypt(o28[list(probe)])
+    for k, c in enumerate(probe):
+        assert np.array_equal(dec[k], (probe[c] == cval).astype(np.uint32)), "const28 result wrong"
+    out["const28"] = {"workload": "EQ(x, c): 2^28 slots = 8192 ciphertexts vs a broadcast constant, N=32768",
+                      "value": n28 * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1,
+                      "check": "closed form on ciphertexts 0, 4096, 8191"}
+    del x28, o28
+    torch.cuda.empty_cache()
+    # LT over 16 ciphertext pairs, closed form on every slot
+    nl = 16
+    xl, yl = eq_pair_columns(nl * N, seed=SEED_DATA + 7, value_bits=15)
+    cxl = ctx.encrypt(xl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=0)
+    cyl = ctx.encrypt(yl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=nl)
+    ol = ctx.ct_empty(nl)
+    ms = timed(lambda: ctx.run(hp.HP_LT, cxl, cyl, 0, out=ol, stream=stream))
+    assert np.array_equal(ctx.decrypt(ol).reshape(-1), (xl < yl).astype(np.uint32)), "LT result wrong"
+    out["lt"] = {"workload": "LT(x, y) (Eq. 4): 16 ciphertext pairs = 2^19 slots, x, y in [0, 2^15], N=32768, "
+                 "511 multiplications per ciphertext (depth 18)", "value": nl * N / (ms / 1e3), "unit": UNIT,
+                 "ms_per_step": ms, "steps": 1, "warmup": 1, "check": "closed form [x < y] on every slot",
+                 "hmult_per_s": nl * 511 / (ms / 1e3)}
+    del cxl, cyl, ol
+    torch.cuda.empty_cache()
+    return out
 
 
 def e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist):
@@ -573,21 +663,18 @@ def e2e_measure(ctx, cx, cy, const_val, n_ct, N, args, world, dist):
             "seconds_per_step": secs, "path": "hp_run with pinned host buffers (library stages tiles through HBM)"}
 
 
-def run_batched(args):
-    """Config 3: uneven instances through hp_run_batched (slot-packed and one
-    ciphertext group per instance) against plain hp_run calls per instance.
-    elements = slots of the instances (the real rows compared)."""
+def batched_measure(ctx, steps: int, warm: int, stream, per_instance: bool = True):
+    """Config 3: 4096 uneven instances (sizes log-uniform in [2^8, 2^16] slots,
+    dictionary IDs) through hp_run_batched, slot-packed into shared ciphertexts
+    and (per_instance) with one group of ciphertexts per instance, against plain
+    hp_run calls per instance.  elements = slots of the instances (the rows
+    compared).  Checks the closed form on sampled instances of each form."""
     import numpy as np
     import torch
 
     from paper_2602_24271_b300 import hp
     from paper_2602_24271_b300.inputs import dictionary_column, log_uniform_sizes
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    wl = workload("batched")
-    ctx = hp.Context(LOGN, max_tile_ct=args.tile)
-    ctx.keygen(SEED_KEY)
-    tile = ctx.autotune()
     N = ctx.N
     sizes = log_uniform_sizes(4096, seed=2, lo_log2=8, hi_log2=16)
     total = int(sizes.sum())
@@ -606,6 +693,19 @@ def run_batched(args):
             out[c0:c1] = ctx.encrypt(slots[c0 * N:c1 * N].reshape(-1, N), seed=SEED_DATA, ct_index0=idx0 + c0)
         return out
 
+    def timed(fn, n_steps, n_warm):
+        for _ in range(n_warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n_steps
+
+    launches = {}
     # (a) slot-packed: instances back to back in one global slot space
     packed, off = [], 0
     for n in sizes:
@@ -616,80 +716,90 @@ def run_batched(args):
     xs, ys = columns(n_pk * N)
     px, py = encrypt_all(xs, n_pk, 0), encrypt_all(ys, n_pk, n_pk)
     pout = ctx.ct_empty(n_pk)
-    # (b) one group of ciphertexts per instance
-    per, c = [], 0
-    for n in sizes:
-        k = (int(n) + N - 1) // N
-        per.append((c, k, 0, int(n), 0, 0))
-        c += k
-    n_pi = c
-    xi, yi = columns(n_pi * N)
-    ix, iy = encrypt_all(xi, n_pi, 0), encrypt_all(yi, n_pi, n_pi)
-    iout = ctx.ct_empty(n_pi)
-    stream = torch.cuda.current_stream()
-
-    def timed(fn, steps, warm):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
-
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    launches = {}
 
     def f_packed():
         ctx.run_batched(hp.HP_EQ_CT_CT, packed, px, py, out=pout, stream=stream)
         launches["packed"] = ctx.launch_count()
 
-    def f_per():
-        ctx.run_batched(hp.HP_EQ_CT_CT, per, ix, iy, out=iout, stream=stream)
-        launches["per"] = ctx.launch_count()
-
-    def f_plain():
-        n = 0
-        for (c0, k, _, _, _, _) in per:
-            ctx.run(hp.HP_EQ_CT_CT, ix[c0:c0 + k], iy[c0:c0 + k], 0, out=iout[c0:c0 + k], stream=stream)
-            n += ctx.launch_count()
-        launches["plain"] = n
-
-    ms_packed = timed(f_packed, args.steps, args.warmup)
-    ms_per = timed(f_per, 1, 1)
-    ms_plain = timed(f_plain, 1, 0)
-    clk = clocks.stop()
-    ctx.check_status()
-    # closed form on sampled instances of each form
+    ms_packed = timed(f_packed, steps, warm)
     dec_p = ctx.decrypt(pout[:4]).reshape(-1)
     for (ct0, k, so, n, _, _) in packed[:8]:
         g0 = ct0 * N + so
         if g0 + n <= 4 * N:
             assert np.array_equal(dec_p[g0:g0 + n], (xs[g0:g0 + n] == ys[g0:g0 + n]).astype(np.uint32))
-    dec_i = ctx.decrypt(iout[:2]).reshape(-1)
-    assert np.array_equal(dec_i[:N], (xi[:N] == yi[:N]).astype(np.uint32))
-    value = total / (ms_packed / 1e3)
+    res = {"instances": 4096, "instance_slots": total, "ciphertexts_packed": n_pk,
+           "packed_batched_elements_per_s": total / (ms_packed / 1e3), "packed_ms_per_pass": ms_packed}
+    del px, py, pout
+    if per_instance:
+        # (b) one group of ciphertexts per instance; (c) plain hp_run per instance
+        per, c = [], 0
+        for n in sizes:
+            k = (int(n) + N - 1) // N
+            per.append((c, k, 0, int(n), 0, 0))
+            c += k
+        n_pi = c
+        xi, yi = columns(n_pi * N)
+        ix, iy = encrypt_all(xi, n_pi, 0), encrypt_all(yi, n_pi, n_pi)
+        iout = ctx.ct_empty(n_pi)
+
+        def f_per():
+            ctx.run_batched(hp.HP_EQ_CT_CT, per, ix, iy, out=iout, stream=stream)
+            launches["per"] = ctx.launch_count()
+
+        def f_plain():
+            n = 0
+            for (c0, k, _, _, _, _) in per:
+                ctx.run(hp.HP_EQ_CT_CT, ix[c0:c0 + k], iy[c0:c0 + k], 0, out=iout[c0:c0 + k], stream=stream)
+                n += ctx.launch_count()
+            launches["plain"] = n
+
+        ms_per = timed(f_per, 1, 1)
+        ms_plain = timed(f_plain, 1, 0)
+        dec_i = ctx.decrypt(iout[:2]).reshape(-1)
+        assert np.array_equal(dec_i[:N], (xi[:N] == yi[:N]).astype(np.uint32))
+        res.update({"ciphertexts_per_instance": n_pi,
+                    "per_instance_batched_elements_per_s": total / (ms_per / 1e3),
+                    "plain_per_instance_calls_elements_per_s": total / (ms_plain / 1e3),
+                    "packed_over_plain_per_instance_calls": ms_plain / ms_packed,
+                    "per_instance_batched_over_plain_per_instance_calls": ms_plain / ms_per})
+        del ix, iy, iout
+    res["error"] = "bit-exact (integer arithmetic; parity tests vs the oracle)"
+    res["launches_by_form"] = dict(launches)
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(args):
+    """Config 3 on its own line: the packed batched form is the value."""
+    import torch
+
+    from paper_2602_24271_b300 import hp
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = workload("batched")
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile)
+    ctx.keygen(SEED_KEY)
+    tile = ctx.autotune()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    r = batched_measure(ctx, args.steps, args.warmup, stream)
+    clk = clocks.stop()
+    ctx.check_status()
+    value = r["packed_batched_elements_per_s"]
     cpu = None
     if not args.no_cpu:
         v, secs, desc = OracleSample("batched").time(8)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "cpu_seconds": secs}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_packed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
-            "config": {"workload": wl["desc"], "instances": 4096, "instance_slots": total, "ciphertexts_packed": n_pk,
-                       "ciphertexts_per_instance": n_pi, "tile_ct": tile, "l2": "inputs larger than L2"},
-            "batched_vs_plain": {
-                "packed_batched_elements_per_s": value,
-                "per_instance_batched_elements_per_s": total / (ms_per / 1e3),
-                "plain_per_instance_calls_elements_per_s": total / (ms_plain / 1e3),
-                "packed_over_plain": ms_plain / ms_packed,
-                "per_instance_batched_over_plain": ms_plain / ms_per,
-                "error": "bit-exact (integer arithmetic; parity tests vs the oracle)"},
-            "clocks": clk, "gpu_launches": launches.get("packed", 0) * args.steps,
-            "gpu_launches_by_form": launches, "hmult_per_s": n_pk * 16 / (ms_packed / 1e3)}
+            "ms_per_step": r["packed_ms_per_pass"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "instances": r["instances"], "instance_slots": r["instance_slots"],
+                       "ciphertexts_packed": r["ciphertexts_packed"],
+                       "ciphertexts_per_instance": r["ciphertexts_per_instance"], "tile_ct": tile,
+                       "l2": "inputs larger than L2"},
+            "batched_vs_plain": r, "clocks": clk,
+            "gpu_launches": r["launches_by_form"].get("packed", 0) * args.steps,
+            "hmult_per_s": r["ciphertexts_packed"] * 16 / (r["packed_ms_per_pass"] / 1e3)}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

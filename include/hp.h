@@ -76,6 +76,10 @@ typedef struct {
   uint64_t P;         /* special prime */
   uint64_t t;         /* plaintext modulus, must be 65537 */
   uint32_t max_depth; /* multiplicative depth the caller needs (16 for EQ, 17 with SELECT) */
+  uint32_t ks_fine_depth; /* products at multiplicative depth <= this are relinearised with a
+                             per-prime key (15 digits [d2]_{q_i}, SEAL's decomposition); deeper
+                             ones with the three-prime key.  0 = three-prime digits throughout;
+                             >= the deepest product = per-prime throughout.  See hp_budget_estimate. */
 } hp_params;
 
 /* Operations of hp_run / hp_run_batched. */
@@ -107,6 +111,19 @@ int hp_create(const hp_params* params, const uint64_t* relin_key, size_t max_til
  * The handle keeps its own transformed copy; the caller keeps ownership of
  * `relin_key_dev`.  Synchronous with respect to the host. */
 int hp_set_relin_key(hp_handle* h, const uint64_t* relin_key_dev);
+
+/* The per-prime relinearisation key of a handle created with ks_fine_depth > 0
+ * (HP_ERR_STATE otherwise): digit i = [d2]_{q_i} (i < L), key
+ * rk_i = (-(a_i s + e_i) + P g_i s^2, a_i) mod QP with g_i = (Q/q_i) [(Q/q_i)^{-1}]_{q_i};
+ * layout [L][2][L+1][N] (residues mod q_0..q_{L-1}, P; coefficient domain).
+ *   hp_set_relin_key_fine: install a key made elsewhere (device memory);
+ *   hp_keygen_fine: make it from the secret sk (device int8 [N]) and `seed`
+ *     (Philox counter (k, j, 16 + i, 5) for a_i, (k, 0, 16 + i, 4) for e_i) and
+ *     install it; rk_fine_out (device, optional) receives it.  hp_keygen calls
+ *     it itself for such handles.
+ * Both synchronous. */
+int hp_set_relin_key_fine(hp_handle* h, const uint64_t* rk_fine_dev);
+int hp_keygen_fine(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_fine_out, void* stream);
 
 /* Evaluate `op` on n_ct ciphertexts.
  *   HP_EQ_CT_CT    out[i] = EQ(x[i], y[i])
@@ -253,6 +270,46 @@ int hp_extract_broadcast(hp_handle* h, const uint64_t* column, size_t n_ct, size
 int hp_join(hp_handle* h, const uint64_t* a_key, size_t n_a, const uint64_t* b_key, const uint64_t* b_attr,
             size_t n_attr, size_t n_rows, uint64_t* out, void* stream);
 
+/* ---- noise budget (Sec. 4.3: the planner keeps every query within the depth
+ * the parameters allow) -------------------------------------------------------
+ * hp_budget_estimate: a static, conservative estimate of the invariant-noise
+ * budget in bits (log2(Q / (2 |v|)); decryption is exact while it is positive)
+ * left in the result of `op` for the parameters `params` (log_n, q, P, t,
+ * ks_fine_depth; no GPU needed):
+ *   HP_BUDGET_EQ / _SELECT / _SQUARE / _LT / _BETWEEN   the operation on fresh inputs
+ *   HP_BUDGET_PRODUCT      a fresh column times an operand of budget in_bits
+ *                          lying at multiplicative depth in_depth (hp_select_mask)
+ *   HP_BUDGET_ROTATE_SUM   the rotate-and-add reduction of an operand of budget
+ *                          in_bits (COUNT / SUM over all N slots)
+ * The model: fresh budget log Q - log t - log N - 8, log t + log N + 1 bits per
+ * level, capped after each product by the key-switching noise of the key used;
+ * LT pays 8 more bits for its giant-step sum.  It lies below the oracle's
+ * measured budgets.  Every operation of this library refuses to run
+ * (HP_ERR_DEPTH) when its estimate is below HP_BUDGET_MARGIN bits. */
+#define HP_BUDGET_MARGIN 10.0
+typedef enum {
+  HP_BUDGET_EQ = 0,
+  HP_BUDGET_SELECT = 1,
+  HP_BUDGET_SQUARE = 2,
+  HP_BUDGET_LT = 3,
+  HP_BUDGET_BETWEEN = 4,
+  HP_BUDGET_PRODUCT = 5,
+  HP_BUDGET_ROTATE_SUM = 6
+} hp_budget_op;
+int hp_budget_estimate(const hp_params* params, int op, uint32_t in_depth, double in_bits, double* out_bits);
+
+/* SELECT (Eq. 5, Sec. 4.2.2) with any predicate mask: out[c] = col[c] * mask[c]
+ * for n_ct device ciphertexts, one multiplication with relinearisation.  The
+ * mask is an EQ, LT or BETWEEN result (or a product of such: AND), lying at
+ * multiplicative depth mask_depth (16 for EQ, 18 for LT, 19 for BETWEEN) with
+ * estimated budget mask_bits (hp_budget_estimate of the operation that made
+ * it); the column is fresh.  The product lies at depth mask_depth + 1, which
+ * selects the relinearisation key as for every product.  HP_ERR_DEPTH when
+ * the estimated budget after the product is below HP_BUDGET_MARGIN.  out may
+ * alias col or mask.  Stream-ordered; tiles of the handle's tile size. */
+int hp_select_mask(hp_handle* h, const uint64_t* col, const uint64_t* mask, size_t n_ct, uint32_t mask_depth,
+                   double mask_bits, uint64_t* out, void* stream);
+
 /* Adjoint of hp_run.  The predicate is an exact integer map over Z_Q with no
  * derivative, so this always returns HP_ERR_UNSUPPORTED. */
 int hp_backward(hp_handle* h, int op, const uint64_t* grad_out, uint64_t* grad_x, size_t n_ct, void* stream);
@@ -318,6 +375,9 @@ int hp_check_status(hp_handle* h);
  *   - the handle's device must be current (HP_ERR_ARG otherwise);
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     after a device reset (cudaDeviceReset) the next call on that device
+ *     finds a new context and looks the address up again, so make it, too,
+ *     before any capture;
  *   - all calls share the one array and it keeps the last call's contents;
  *     nothing in it needs to start at zero.  Calls whose GPU work overlaps
  *     (different streams, or several host threads) race on it: order them.
@@ -360,7 +420,10 @@ int hp_probe_tc_timeout(uint32_t polls);
 /* Register-only peak probe on the current device (no handle needed):
  * kind 0 = the 64-bit Shoup butterfly of the NTT kernels (butterflies/s),
  * kind 1 = the 64x64->128-bit multiply-accumulate of the base conversions and
- * key switching (MACs/s).  Launches 8 blocks of 256 threads per SM. */
+ * key switching (MACs/s), kind 2 = the same Shoup butterfly on 32-bit words
+ * for a 30-bit prime (butterflies/s; no kernel of the library uses it: it
+ * measures what a narrower residue word would buy).  Launches 8 blocks of 256
+ * threads per SM. */
 int hp_probe_peak(int kind, double* per_second);
 
 #ifdef __cplusplus

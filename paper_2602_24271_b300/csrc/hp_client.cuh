@@ -52,14 +52,16 @@ __global__ void k_secret_automorph(const int8_t* s, int8_t* out, uint32_t g, int
   }
 }
 
-// Key-switching key (relinearisation: source s^2, domains A_RK / E_RK, object
-// i; Galois element g: source tau_g(s), domains A_GK / E_GK, object (g << 5) | i),
-// part 1: a_{i,j,k} (uniform mod p_j) into both the output rk[i][1][j][k] and a
-// work copy A[i][j][k].
-__global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN, uint32_t dom, uint32_t obj_base) {
+// Key-switching key with nd digits of dp data primes each (relinearisation:
+// source s^2, domains A_RK / E_RK, object i for the three-prime key and
+// FINE_OBJ + i for the per-prime key; Galois element g: source tau_g(s),
+// domains A_GK / E_GK, object (g << 5) | i), part 1: a_{i,j,k} (uniform mod p_j)
+// into both the output rk[i][1][j][k] and a work copy A[i][j][k].
+__global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN, uint32_t dom, uint32_t obj_base,
+                              int nd) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)NDIG * NKS * N) return;
+  if (gid >= (size_t)nd * NKS * N) return;
   int k = (int)(gid & (N - 1));
   size_t ij = gid >> logN;
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
@@ -72,10 +74,10 @@ __global__ void k_rk_sample_a(uint64_t* rk, uint64_t* A, uint64_t seed, int logN
 // part 2: rk[i][0][j][k] = -(a s + e) + [q_j in digit i] [P]_{q_j} src  mod p_j, with
 // AS = a s and S2 = the source secret in coefficient domain (canonical).
 __global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2, uint64_t seed, int logN,
-                            uint32_t dom, uint32_t obj_base) {
+                            uint32_t dom, uint32_t obj_base, int nd, int dp) {
   const int N = 1 << logN;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)NDIG * NKS * N) return;
+  if (gid >= (size_t)nd * NKS * N) return;
   int k = (int)(gid & (N - 1));
   size_t ij = gid >> logN;
   int j = (int)(ij % NKS), i = (int)(ij / NKS);
@@ -84,7 +86,7 @@ __global__ void k_rk_finish(uint64_t* rk, const uint64_t* AS, const uint64_t* S2
   int e = draw_cbd21(philox((uint32_t)k, 0u, obj_base | (uint32_t)i, dom, seed));
   uint64_t em = e < 0 ? p - (uint64_t)(-e) : (uint64_t)e;
   uint64_t v = sub_mod(0, add_mod(AS[gid], em, p), p);
-  if (j < L && j / DIGIT_PRIMES == i) {  // g_i = 1 mod the digit's primes, 0 mod the others and P
+  if (j < L && j / dp == i) {  // g_i = 1 mod the digit's primes, 0 mod the others and P
     uint64_t s2 = S2[(size_t)j * N + k];
     uint64_t t = (uint64_t)(((unsigned __int128)s2 * cK.Pmodq[j]) % p);
     v = add_mod(v, t, p);

@@ -18,9 +18,14 @@ constexpr int ID_P = L + K;        // 31
 constexpr int ID_T = L + K + 1;    // 32
 constexpr int NPRIME = L + K + 2;  // 33
 constexpr int NKS = L + 1;         // key-switching targets: q_0..q_{L-1}, P
-constexpr int DIGIT_PRIMES = 3;    // data primes per key-switching digit
+constexpr int DIGIT_PRIMES = 3;    // data primes per key-switching digit (relinearisation, rotations)
 constexpr int NDIG = L / DIGIT_PRIMES;  // digits: digit a = [d]_{q_3a q_3a+1 q_3a+2}
 static_assert(L % DIGIT_PRIMES == 0, "digits are whole groups of data primes");
+// The per-prime relinearisation key (digit i = [d]_{q_i}) used for products at
+// output depth <= the handle's ks_fine_depth; its digits draw Philox with
+// object index FINE_OBJ + i.
+constexpr int NDIG_FINE = L;
+constexpr uint32_t FINE_OBJ = 16;
 constexpr int LOGN_MIN = 12, LOGN_MAX = 15;
 
 // Constants for the exact RNS base conversions, relinearisation and the
@@ -88,16 +93,25 @@ uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);
 uint64_t h_invmod(uint64_t a, uint64_t m);
 uint64_t h_shoup(uint64_t w, uint64_t p);
 
-// Tables of the tensor-core base conversions (8-bit limbs, f16 operands).
-//   B1 [128][128]: row 8k+b (k < K, b < 7), column 8i+a (i < L, a < 7):
-//                  limb b of [2^(8a) (Q/q_i)]_{b_k}; other entries 0.
-//   B2 [128][128]: row 8i+b (i < L, b < 7), column 8k+a (k < K, a < 7):
-//                  limb b of [2^(8a) (B/b_k)]_{q_i}; other entries 0.
-// Both as f16 bit patterns in the no-swizzle K-major core-matrix layout.
-//   T1 [16][16]:   [-v Q]_{b_k} for v < 16 (k < K)
-//   T2 [17][16]:   [-v B]_{q_i} for v <= K (i < L; column 15 unused)
+// Tables of the tensor-core base conversions (8-bit limbs, f16 operands), all
+// [128][128] f16 bit patterns in the no-swizzle K-major core-matrix layout:
+//   B1L (lift):   row 8k+b (k < K, b < 7), column 8i+a (i < L, a < 7):
+//                 limb b of [2^(8a) (Q/q_i)]_{b_k};
+//   B1S (scale-and-round): the same entries times [Q^{-1} (B/b_k)^{-1}]_{b_k}, so
+//                 that the product is the B residue already multiplied by it;
+//   both also:    row 8l+7 (l < 8), column 8i+a: limb l of floor(2^(64+8a) / q_i),
+//                 whose column sums give sum_i y_i / q_i in 64-bit fixed point;
+//   B2:           row 8i+b (i < L, b < 7), column 8k+a (k < K, a < 7):
+//                 limb b of [2^(8a) (B/b_k)]_{q_i}; row 120+l: limb l of
+//                 floor(2^(64+8a) / b_k) (the fixed-point sum of y_k / b_k).
+// Correction tables (uint64):
+//   T1 [16][16]:  [-v Q]_{b_k} for v < 16 (k < K);  T1S: the same times [Q^{-1} (B/b_k)^{-1}]_{b_k}
+//   T2 [17][16]:  [-v B]_{q_i} for v <= K (i < L; column 15 unused)
 constexpr int TC_ROWS = 128, TC_K = 128, TC_T1 = 16 * 16, TC_T2 = 17 * 16;
-void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, uint64_t* T2);
+constexpr int TC_OPER = TC_ROWS * TC_K;                       // f16 elements of one operand
+constexpr int TCT_B1L = 0, TCT_B1S = TC_OPER, TCT_B2 = 2 * TC_OPER, TCT_OPS = 3 * TC_OPER;  // in f16 elements
+constexpr int TCT_T1 = 0, TCT_T1S = TC_T1, TCT_T2 = 2 * TC_T1, TCT_TABS = 2 * TC_T1 + TC_T2;  // in words
+void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs);
 
 // LT polynomial's odd coefficients (32768 words), see hp_host.cpp.
 int lt_coefficients(uint32_t* out);
@@ -108,5 +122,16 @@ int lt_coefficients(uint32_t* out);
 // log N + 2 bits per squaring, the key-switching noise bounding the budget
 // after the first), below the oracle's measured budgets.  Used by hp_create.
 int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t);
+
+// Static estimate of the invariant-noise budget (bits) left in the result of
+// one of the operations below on fresh inputs (BUDGET_PRODUCT: a fresh column
+// times an operand of budget in_bits at depth in_depth; BUDGET_ROTATE_SUM: the
+// rotate-and-add reduction of an operand of budget in_bits).  Operations refuse
+// to run when it is below BUDGET_MARGIN.  Values match hp_budget_op in hp.h.
+enum { BUDGET_EQ = 0, BUDGET_SELECT = 1, BUDGET_SQUARE = 2, BUDGET_LT = 3, BUDGET_BETWEEN = 4, BUDGET_PRODUCT = 5,
+       BUDGET_ROTATE_SUM = 6 };
+constexpr double BUDGET_MARGIN = 10.0;
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int fine_depth, int op,
+                       int in_depth, double in_bits);
 
 }  // namespace hp

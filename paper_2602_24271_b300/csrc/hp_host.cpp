@@ -297,27 +297,53 @@ static uint16_t f16_of_int(uint32_t v) {
 }
 static int tc_cm_host(int r, int k) { return ((r >> 3) * (TC_K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
-void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, uint64_t* T2) {
+// limb l (8 bits) of floor(2^(64 + 8a) / m), the fixed-point weight of limb a
+// of a residue mod m in sum_i y_i / m_i (m > 2^54, a < 7: the value is < 2^58)
+static uint32_t fix_limb(uint64_t m, int a, int l) {
+  const u128 c = ((u128)1 << (64 + 8 * a)) / m;
+  return (uint32_t)(c >> (8 * l)) & 255u;
+}
+
+void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs) {
   const uint64_t* q = C.p;
   const uint64_t* b = C.p + L;
-  memset(B1, 0, sizeof(uint16_t) * TC_ROWS * TC_K);
-  memset(B2, 0, sizeof(uint16_t) * TC_ROWS * TC_K);
+  uint16_t* B1L = ops + TCT_B1L;
+  uint16_t* B1S = ops + TCT_B1S;
+  uint16_t* B2 = ops + TCT_B2;
+  memset(ops, 0, sizeof(uint16_t) * TCT_OPS);
   for (int k = 0; k < K; ++k)
     for (int i = 0; i < L; ++i) {
-      uint64_t c = prod_mod(q, L, i, b[k]);  // [Q/q_i]_{b_k}
-      for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, b[k]))
-        for (int l = 0; l < 7; ++l) B1[tc_cm_host(8 * k + l, 8 * i + a)] = f16_of_int((uint32_t)(c >> (8 * l)) & 255);
+      uint64_t c = prod_mod(q, L, i, b[k]);          // [Q/q_i]_{b_k}
+      uint64_t cs = h_mulmod(c, C.QBinv[k], b[k]);  // times [Q^{-1} (B/b_k)^{-1}]_{b_k}
+      for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, b[k]), cs = h_mulmod(cs, 256, b[k]))
+        for (int l = 0; l < 7; ++l) {
+          B1L[tc_cm_host(8 * k + l, 8 * i + a)] = f16_of_int((uint32_t)(c >> (8 * l)) & 255);
+          B1S[tc_cm_host(8 * k + l, 8 * i + a)] = f16_of_int((uint32_t)(cs >> (8 * l)) & 255);
+        }
     }
+  for (int l = 0; l < 8; ++l)  // the fixed-point sum of y_i / q_i in column 8l + 7
+    for (int i = 0; i < L; ++i)
+      for (int a = 0; a < 7; ++a) {
+        B1L[tc_cm_host(8 * l + 7, 8 * i + a)] = f16_of_int(fix_limb(q[i], a, l));
+        B1S[tc_cm_host(8 * l + 7, 8 * i + a)] = f16_of_int(fix_limb(q[i], a, l));
+      }
   for (int i = 0; i < L; ++i)
     for (int k = 0; k < K; ++k) {
       uint64_t c = prod_mod(b, K, k, q[i]);  // [B/b_k]_{q_i}
       for (int a = 0; a < 7; ++a, c = h_mulmod(c, 256, q[i]))
         for (int l = 0; l < 7; ++l) B2[tc_cm_host(8 * i + l, 8 * k + a)] = f16_of_int((uint32_t)(c >> (8 * l)) & 255);
     }
+  for (int l = 0; l < 8; ++l)  // the fixed-point sum of y_k / b_k in columns 120 .. 127
+    for (int k = 0; k < K; ++k)
+      for (int a = 0; a < 7; ++a) B2[tc_cm_host(8 * L + l, 8 * k + a)] = f16_of_int(fix_limb(b[k], a, l));
+  uint64_t* T1 = tabs + TCT_T1;
+  uint64_t* T1S = tabs + TCT_T1S;
+  uint64_t* T2 = tabs + TCT_T2;
   for (int v = 0; v < 16; ++v)
     for (int k = 0; k < 16; ++k) {
       const uint64_t Qb = prod_mod(q, L, -1, b[k]);
       T1[v * 16 + k] = (b[k] - h_mulmod((uint64_t)v, Qb, b[k])) % b[k];
+      T1S[v * 16 + k] = h_mulmod(T1[v * 16 + k], C.QBinv[k], b[k]);
     }
   for (int v = 0; v < 17; ++v)
     for (int i = 0; i < 16; ++i) {
@@ -328,6 +354,72 @@ void build_tc_tables(const Consts& C, uint16_t* B1, uint16_t* B2, uint64_t* T1, 
       const uint64_t Bq = prod_mod(b, K, -1, q[i]);
       T2[v * 16 + i] = (q[i] - h_mulmod((uint64_t)v, Bq, q[i])) % q[i];
     }
+}
+
+// ---- invariant-noise budget model --------------------------------------------
+// Budgets in bits, log2(Q / (2 |v|)) for the invariant noise v.  The model:
+//   fresh          log Q - log t - log N - 8 (a fresh encryption, |e| <= 21)
+//   per level      log t + log N + 1 (a product multiplies the noise by about t N)
+//   key switching  a product relinearised with digits of g data primes adds
+//                  noise |digit| sqrt(N) 2^6 / P, so its budget is at most
+//                  (log Q - log t) - (log |digit| + log N / 2 + 6 - log P)
+// B(d) = min(B(d-1) - per level, key-switching bound of the key used at depth d):
+// the three-prime key's bound (about 686 bits at N = 32768) is what costs the
+// first levels' budget when they use it; the per-prime key's lies above the
+// fresh budget.  Every constant sits on the conservative side of the oracle's
+// measured budgets (per level 27.6 bits measured at N = 4096, 30.3 at N = 32768).
+struct NoiseModel {
+  double fresh, per_level, ks3, ks1;
+};
+static NoiseModel noise_model(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {
+  double lq = 0, l3 = 0, l1 = 0;
+  for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
+  for (int a = 0; a * DIGIT_PRIMES < nq; ++a) {
+    double g = 0;
+    for (int i = a * DIGIT_PRIMES; i < nq && i < (a + 1) * DIGIT_PRIMES; ++i) g += log2((double)q[i]);
+    l3 = l3 > g ? l3 : g;
+  }
+  for (int i = 0; i < nq; ++i) l1 = l1 > log2((double)q[i]) ? l1 : log2((double)q[i]);
+  const double lt = log2((double)t), lp = log2((double)P);
+  NoiseModel m;
+  m.fresh = lq - lt - log_n - 8.0;
+  m.per_level = lt + log_n + 1.0;
+  m.ks3 = (lq - lt) - (l3 + 0.5 * log_n + 6.0 - lp);
+  m.ks1 = (lq - lt) - (l1 + 0.5 * log_n + 6.0 - lp);
+  return m;
+}
+// budget after a chain of products whose d-th lies at depth d (d = 1 .. depth)
+static double chain_budget(const NoiseModel& m, int depth, int fine_depth) {
+  double b = m.fresh;
+  for (int d = 1; d <= depth; ++d) {
+    const double floor_d = d <= fine_depth ? m.ks1 : m.ks3;
+    b = std::min(b - m.per_level, floor_d);
+  }
+  return b;
+}
+
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int fine_depth, int op,
+                       int in_depth, double in_bits) {
+  const NoiseModel m = noise_model(log_n, q, nq, P, t);
+  // a product of a fresh operand with one of budget `bits` lying at depth `d`
+  auto product = [&](double bits, int d) {
+    const double floor_d = d <= fine_depth ? m.ks1 : m.ks3;
+    return std::min(std::min(bits, m.fresh) - m.per_level, floor_d);
+  };
+  // LT: the giant-step sum adds 128 products of depth <= 17 (7 bits), the
+  // scalar combinations before them scale the baby-step noise by < 2^24, which
+  // stays below the giant powers' (at least 7 levels deeper)
+  const double lt = chain_budget(m, 18, fine_depth) - 8.0;
+  switch (op) {
+    case BUDGET_EQ: return chain_budget(m, 16, fine_depth);
+    case BUDGET_SELECT: return product(chain_budget(m, 16, fine_depth), 17);
+    case BUDGET_SQUARE: return chain_budget(m, 1, fine_depth);
+    case BUDGET_LT: return lt;
+    case BUDGET_BETWEEN: return product(lt, 19) - 1.0;  // two LT results, each at budget lt
+    case BUDGET_PRODUCT: return product(in_bits, in_depth + 1);
+    case BUDGET_ROTATE_SUM: return std::min(in_bits - log_n - 1.0, m.ks3);  // N slots summed
+    default: return -1e9;
+  }
 }
 
 int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {

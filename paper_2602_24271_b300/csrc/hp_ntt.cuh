@@ -60,15 +60,20 @@ struct NttTabs {
   // twiddle of the last inverse stage), each with its Shoup companion
   const uint64_t* scale;
 };
-// c = N^{-1}; t N^{-1} 2^64; N^{-1} 2^64; N^{-1} P^{-1} (data primes, mod-down)
-enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3, NSCALE = 4 };
+// c = N^{-1}; t N^{-1} 2^64; N^{-1} 2^64; N^{-1} P^{-1} (data primes, mod-down);
+// t N^{-1} 2^64 times the first factor of each base conversion of the
+// tensor-core scale-and-round ([(Q/q_i)^{-1}]_{q_i}, [Q^{-1} (B/b_k)^{-1}]_{b_k})
+enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3, SCALE_T_NINV_R_CONV = 4, NSCALE = 5 };
 
 // Optional fused load of the forward column pass: polynomial (b, g, j) of the
 // key-switching batch is digit g of ciphertext b reduced modulo target prime
-// j.  The digit is stored in mixed radix as (r0, t1, t2) in w3[b][2][3g .. 3g+2]
-// and recombined as r0 + [q_3g]_{p_j} t1 + [q_3g q_3g+1]_{p_j} t2 mod p_j.
+// j.  Three-prime digits (dp = 3) are stored in mixed radix as (r0, t1, t2) in
+// w3[b][2][3g .. 3g+2] and recombined as r0 + [q_3g]_{p_j} t1 + [q_3g q_3g+1]_{p_j} t2
+// mod p_j; a per-prime digit (dp = 1) is the residue w3[b][2][g] < q_g, which
+// one conditional subtraction reduces modulo any target (q_g < 2 p_j).
 struct DigitSrc {
   const uint64_t* w3;  // nullptr: the pass transforms `data` in place
+  int dp;              // data primes per digit: 3 or 1
 };
 
 // ---- modular helpers for the transform ------------------------------------------
@@ -243,7 +248,12 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restri
   const ulonglong2* tw = T.tw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
   uint64_t x[16];
-  if (dig.w3) {  // key-switching digits: poly = (b * NDIG + g) * NKS + j
+  if (dig.w3 && dig.dp == 1) {  // per-prime digits: poly = (b * L + g) * NKS + j
+    const int b = poly / (NDIG_FINE * NKS), g = (poly / NKS) % NDIG_FINE;
+    const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g) * N;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = csub(src[(size_t)(rb + u * RB) * C + k0 + k], p);
+  } else if (dig.w3) {  // three-prime digits: poly = (b * NDIG + g) * NKS + j
     const int b = poly / (NDIG * NKS), g = (poly / NKS) % NDIG, j = poly % NKS;
     const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g * DIGIT_PRIMES) * N;
     const uint64_t c1 = cK.dig1[g][j], c1s = cK.dig1_s[g][j], c2 = cK.dig2[g][j], c2s = cK.dig2_s[g][j];
@@ -344,7 +354,7 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t* __restri
 //   d0 = a0 a0 2^-64, d1 = 2 a0 a1 2^-64 (reduced to [0, 2p)), d2 = a1 a1 2^-64.
 // ext: [nct][2][NQB][N] after the column pass; dprod: [nct][3][NQB][N].
 template <int LOGR, int LOGC>
-__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_rows_sq(const uint64_t* __restrict__ ext,
+__global__ void __launch_bounds__(NTT_THREADS, 6) k_ntt_fwd_rows_sq(const uint64_t* __restrict__ ext,
                                                                  uint64_t* __restrict__ dprod, NttTabs T) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int ROWS = NTT_TILE >> LOGC, TPR = C / 16, B2 = LOGC - 4, PADC = C + C / 16;

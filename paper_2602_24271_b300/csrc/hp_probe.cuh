@@ -36,6 +36,37 @@ __global__ void __launch_bounds__(256) k_probe_butterfly(uint64_t* sink, int ite
   if (acc == 0x123456789ull) sink[0] = acc;  // keeps the chains live
 }
 
+// The same forward butterfly on 32-bit words for a prime p < 2^30 (a narrower
+// residue word than the library's 55-bit primes): Shoup's product W Y - q p with
+// q = floor(Y W' / 2^32), W' = floor(W 2^32 / p), is three 32-bit multiplies
+// (low W Y, high Y W', low q p) and lies in [0, 2p); the lazy range grows by 2p
+// per stage as in the 64-bit form.  Measures what a 32-bit residue basis would
+// buy per multiplier slot; no kernel of the library uses it.
+__global__ void __launch_bounds__(256) k_probe_butterfly32(uint64_t* sink, int iters, uint32_t p, uint32_t w,
+                                                           uint32_t wp) {
+  uint32_t X[PROBE_CHAINS], Y[PROBE_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PROBE_CHAINS; ++c) {
+    X[c] = (threadIdx.x * 7919u + c * 104729u + blockIdx.x) % p;
+    Y[c] = (threadIdx.x * 15485863u + c * 32452843u) % p;
+  }
+  const uint32_t p2 = 2 * p;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) {
+      const uint32_t x = X[c];  // wraps mod 2^32 over many rounds: only the instruction stream matters here
+      const uint32_t q = __umulhi(Y[c], wp);
+      const uint32_t v = Y[c] * w - q * p;
+      X[c] = x + v;
+      Y[c] = x - v + p2;
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < PROBE_CHAINS; ++c) acc ^= X[c] ^ Y[c];
+  if (acc == 0x12345679u) sink[0] = acc;  // keeps the chains live
+}
+
 // The base conversions' multiply-accumulate: 56-bit operands in 28-bit limbs,
 // three 64-bit accumulators (four 32x32+64 multiply-adds per MAC).
 __global__ void __launch_bounds__(256) k_probe_mac(uint64_t* sink, int iters, uint64_t p, uint64_t pinv) {

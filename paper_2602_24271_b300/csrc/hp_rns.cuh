@@ -202,9 +202,11 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
 HPD int ks_id(int j) { return j < L ? j : ID_P; }
 
 // One thread per (target j, n), looping over the tile's ciphertexts so that
-// each key word is read once per launch.  rk: [NDIG][2][NKS][N], NTT domain,
-// Montgomery form (canonical); digits in [0, 8p): sums < 5 8 p^2 < p 2^64.
-// ksin: [nct][NDIG][NKS][N]; ksout: [nct][2][NKS][N] in [0, 2p).
+// each key word is read once per launch.  rk: [ND][2][NKS][N], NTT domain,
+// Montgomery form (canonical); digits in [0, 8p): sums < ND 8 p^2 < p 2^64
+// for ND <= 15.  ksin: [nct][ND][NKS][N]; ksout: [nct][2][NKS][N] in [0, 2p).
+// ND = NDIG (three-prime digits) or NDIG_FINE (per-prime digits).
+template <int ND>
 __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restrict__ ksin, const uint64_t* __restrict__ rk,
                                                        uint64_t* __restrict__ ksout, int logN, int nct) {
   const int N = 1 << logN;
@@ -214,9 +216,9 @@ __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restric
   const int j = (int)(gid >> logN);
   const int id = ks_id(j);
   const uint64_t p = cK.p[id], pinv = cK.pinv[id];
-  uint64_t k0[NDIG], k1[NDIG];
+  uint64_t k0[ND], k1[ND];
 #pragma unroll
-  for (int i = 0; i < NDIG; ++i) {
+  for (int i = 0; i < ND; ++i) {
     k0[i] = rk[((size_t)(i * 2 + 0) * NKS + j) * N + n];
     k1[i] = rk[((size_t)(i * 2 + 1) * NKS + j) * N + n];
   }
@@ -225,8 +227,8 @@ __global__ void __launch_bounds__(EW_THREADS) k_ks_mac(const uint64_t* __restric
     acc_zero(a0);
     acc_zero(a1);
 #pragma unroll
-    for (int i = 0; i < NDIG; ++i) {
-      const uint64_t d = ksin[(((size_t)b * NDIG + i) * NKS + j) * N + n];
+    for (int i = 0; i < ND; ++i) {
+      const uint64_t d = ksin[(((size_t)b * ND + i) * NKS + j) * N + n];
       acc_mac(a0, d, k0[i]);
       acc_mac(a1, d, k1[i]);
     }

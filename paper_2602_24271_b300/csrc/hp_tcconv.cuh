@@ -10,10 +10,25 @@
 // (tcgen05.mma, M = 128 coefficients, N = 128 = 16 primes x 8 limb columns,
 // K = 128 = 16 residues x 8 columns, the eighth zero) then gives, per
 // coefficient and prime, the seven limb sums D_l = sum y^(a) c^(l)
-// < 112 * 255^2 < 2^23: exact in the f32 accumulator.  The value sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime
-// on the CUDA cores.  Everything else (the exact centring decisions, the
-// subtraction, the mixed-radix digits) is the same arithmetic as k_scale_round,
-// so the outputs are bit-identical.
+// < 112 * 255^2 < 2^23: exact in the f32 accumulator.  The value
+// sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime on the CUDA cores.
+//
+// The eighth column of each prime's block is free, and the centring sums go
+// there: column 8l + 7 (l < 8) of the Q -> B product holds
+// E_l = sum_{i,a} y_i^(a) [floor(2^(64+8a) / q_i)]^(l), limb l of the fixed-point
+// weight of y_i^(a) in S = sum_i y_i / q_i, so that sum_l E_l 2^(8l) lies within
+// 15 * 7 * 255 < 2^15 below S 2^64 (each weight truncated by less than 1); the
+// B -> Q product holds the same for sum_k y_k / b_k in columns 120 .. 127.  The
+// rounding decisions v = floor(S + 1/2) are read from there, and an undecided
+// window (probability about 2^-49) falls back to the exact mixed-radix
+// comparison, as in k_lift.
+//
+// The inputs come from the inverse transform with its output scale extended
+// (SCALE_T_NINV_R_CONV): the Q residues arrive as y_i = [t d (Q/q_i)^{-1}]_{q_i}
+// and the B residues as [t d Q^{-1} (B/b_k)^{-1}]_{b_k}; the Q -> B operand and
+// its correction table carry the factor [Q^{-1} (B/b_k)^{-1}]_{b_k} too, so
+// y_k of w = (t d - r) / Q in B is one modular subtraction.  The outputs are
+// bit-identical to k_scale_round's.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -24,10 +39,18 @@ namespace hp {
 
 constexpr int SRT_GROUPS = 4;                    // tiles of 128 coefficients in flight per CTA
 constexpr int SRT_THREADS = 128 * SRT_GROUPS;    // one thread per coefficient
-constexpr int SRT_OPER = TC_ROWS * TC_K;         // f16 elements of one operand tile
+constexpr int SRT_OPER = TC_OPER;                // f16 elements of one operand tile
 constexpr size_t SRT_SMEM = (size_t)(2 + SRT_GROUPS) * SRT_OPER * 2 + (TC_T1 + TC_T2) * 8 + SRT_GROUPS * 8 + 32;
+constexpr uint64_t FIX_WINDOW = 1ull << 15;       // the fixed-point sums' window (units of 2^-64)
 
 HPD void named_sync(int id, int count) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
+
+// 32 TMEM lanes x 1 column
+HPD uint32_t tc_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+  return r;
+}
 
 // 32 TMEM lanes x 8 consecutive 32-bit columns
 HPD void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -80,6 +103,30 @@ HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
 // value of an exact integer below 2^23 held in an f32 accumulator word
 HPD uint32_t acc_int(uint32_t bits) { return __float_as_uint(__uint_as_float(bits) + 8388608.0f) & 0x7FFFFFu; }
 
+// The fixed-point sum sum_l E_l 2^(8l) (< 2^80) of eight accumulator words
+// holding exact integers E_l < 2^23, as a Fix (64 low bits, the rest above).
+HPD Fix fix_from_limbs(const uint32_t* e) {
+  Fix F = {0, 0};
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    const uint64_t v = acc_int(e[l]);
+    const uint64_t lo = v << (8 * l);
+    const uint32_t hi = l == 0 ? 0u : (uint32_t)(v >> (64 - 8 * l));
+    F.lo += lo;
+    F.hi += hi + (F.lo < lo ? 1u : 0u);
+  }
+  return F;
+}
+
+// Exact centring decision v of the Q -> B conversion when the fixed-point
+// window does not decide it: the residues [t d]_{q_i} = y_i [Q/q_i]_{q_i} are
+// rebuilt from the y_i in memory (stride N) and compared with (Q-1)/2.
+__device__ __noinline__ int lift_v_y_mem(const uint64_t* y, size_t stride, uint32_t Fhi) {
+  uint64_t r[L];
+  for (int i = 0; i < L; ++i) r[i] = mul_shoup(y[(size_t)i * stride], cK.qhat[i], cK.qhat_s[i], cK.p[i]);
+  return (int)Fhi + greater_than_half(r, 1);
+}
+
 // sum_l D_l 2^(8l) + corr mod p, for the limb sums D_0..D_6 of one prime;
 // c32 = [2^32]_p (Shoup pair).  The low part is < 2^48 < p, the high part
 // times 2^32 reduces to [0, 2p), corr < p: the total is below 4p.
@@ -94,26 +141,29 @@ HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t
 
 // Persistent: SRT_GROUPS groups of four warps, each taking tiles of 128
 // consecutive coefficients (one per thread) of the nct x 3 coefficient
-// polynomials.  tables = B1 | B2 | T1 | T2 (see build_tc_tables).
+// polynomials.  ops / tabs: the operand and correction tables of
+// build_tc_tables (B1S, B2; T1S, T2).  With `mixed` d2 is written as
+// three-prime key-switching digits in mixed radix; otherwise as plain residues
+// (the per-prime digits).
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_scale_round_tc(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3, int* __restrict__ status,
-                     const uint16_t* __restrict__ tables, int logN, int nct) {
+                     const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int mixed) {
   extern __shared__ __align__(1024) uint8_t srt_smem[];
-  uint16_t* B1s = (uint16_t*)srt_smem;
-  uint16_t* B2s = B1s + SRT_OPER;
-  uint16_t* As = B2s + SRT_OPER;  // SRT_GROUPS tiles
-  uint64_t* T1s = (uint64_t*)(As + SRT_GROUPS * SRT_OPER);
+  uint16_t* B1s = (uint16_t*)srt_smem;  // B1S
+  uint16_t* B2s = B1s + SRT_OPER;       // B2
+  uint16_t* As = B2s + SRT_OPER;        // SRT_GROUPS tiles
+  uint64_t* T1s = (uint64_t*)(As + SRT_GROUPS * SRT_OPER);  // T1S
   uint64_t* T2s = T1s + TC_T1;
   uint64_t* mbar = T2s + TC_T2;
   uint32_t* tslot = (uint32_t*)(mbar + SRT_GROUPS);
   uint32_t* okf = tslot + 1;  // per group: the last MMA batch completed
   const int N = 1 << logN, t = threadIdx.x, warp = t >> 5, g = warp >> 2, m = t & 127;
   {  // constant operands and tables, once per CTA
-    const uint4* src = (const uint4*)tables;
+    const uint4* src = (const uint4*)(ops + TCT_B1S);  // B1S and B2 are adjacent
     uint4* dst = (uint4*)srt_smem;
     for (int e = t; e < 2 * SRT_OPER / 8; e += SRT_THREADS) dst[e] = src[e];
-    const uint64_t* tsrc = (const uint64_t*)(tables + 2 * SRT_OPER);
-    for (int e = t; e < TC_T1 + TC_T2; e += SRT_THREADS) T1s[e] = tsrc[e];
+    for (int e = t; e < TC_T1; e += SRT_THREADS) T1s[e] = tabs[TCT_T1S + e];
+    for (int e = t; e < TC_T2; e += SRT_THREADS) T2s[e] = tabs[TCT_T2 + e];
   }
   if (t < SRT_GROUPS) mbar_init(mbar + t, 1);
   fence_async_smem();
@@ -133,18 +183,15 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     const int n = (int)(gid & (N - 1));
     const size_t bj = gid >> logN;
     const uint64_t* d = dprod + bj * NQB * N + n;
-    // ---- r = [t d]_Q: y_i and the centring decision v (as k_scale_round) ----
-    uint64_t y[L];
-    Fix F = {0, 0};
+    // ---- r = [t d]_Q to B: y_i = [t d (Q/q_i)^{-1}]_{q_i} straight from the transform ----
+    {
+      uint64_t y[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) {
-      y[i] = mul_shoup(d[(size_t)i * N], cK.qhatinv[i], cK.qhatinv_s[i], cK.p[i]);
-      fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
+      for (int i = 0; i < L; ++i) y[i] = d[(size_t)i * N];
+      put_limb_row<L>(A, m, y);
     }
-    const int v = lift_v_mem(F, d, N);
-    put_limb_row<L>(A, m, y);
     fence_async_smem();
-    uint64_t dB[K];  // residues mod B, loaded while the MMA runs
+    uint64_t dB[K];  // [t d Q^{-1} (B/b_k)^{-1}]_{b_k}, loaded while the MMA runs
 #pragma unroll
     for (int k = 0; k < K; ++k) dB[k] = d[(size_t)(L + k) * N];
     named_sync(1 + g, 128);
@@ -164,9 +211,19 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     }
     phase ^= 1;
     tc_fence_after();
-    // ---- r in B, w = (t d - r) Q^{-1} in B, the centring decision vb ----
+    // the centring decision v = floor(S + 1/2), S = sum_i y_i / q_i, from columns 8l + 7
+    int v;
+    {
+      uint32_t e[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) e[l] = tc_ld1(tmem + 8 * l + 7);
+      tc_wait_ld();
+      const Fix F = fix_from_limbs(e);
+      v = fix_round(F, FIX_WINDOW);
+      if (v < 0) v = lift_v_y_mem(d, N, F.hi);
+    }
+    // ---- y_k of w = (t d - r) Q^{-1} in B: one subtraction per prime ----
     uint64_t yb[K];
-    Fix G = {0, 0};
 #pragma unroll
     for (int kb = 0; kb < K / 4; ++kb) {  // four primes (32 columns) per TMEM load
       uint32_t r32[32];
@@ -176,16 +233,8 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
       for (int kk = 0; kk < 4; ++kk) {
         const int k = kb * 4 + kk;
         const uint64_t b = cK.p[L + k];
-        const uint64_t r = limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]);
-        const uint64_t z = sub_mod(dB[k], r, b);
-        yb[k] = mul_shoup(z, cK.QBinv[k], cK.QBinv_s[k], b);
-        fix_add(G, fix_term(yb[k], cK.omb_hi[k], cK.omb_lo[k]));
+        yb[k] = sub_mod(dB[k], limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]), b);
       }
-    }
-    int vb = fix_round(G, 2 * K);
-    if (vb < 0) {  // cannot happen for |w| < B / 2^24; recorded for the host
-      atomicOr(status, ST_BQ_WINDOW);
-      vb = (int)G.hi;
     }
     tc_fence_before();
     named_sync(1 + g, 128);  // every lane has read D; the first MMA finished with A
@@ -208,6 +257,19 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     }
     phase ^= 1;
     tc_fence_after();
+    // the centring decision vb of the B -> Q conversion, from columns 120 .. 127
+    int vb;
+    {
+      uint32_t e[8];
+      tc_ld8(tmem + 8 * L, e);
+      tc_wait_ld();
+      const Fix G = fix_from_limbs(e);
+      vb = fix_round(G, FIX_WINDOW);
+      if (vb < 0) {  // cannot happen for |w| < B / 2^24; recorded for the host
+        atomicOr(status, ST_BQ_WINDOW);
+        vb = (int)G.hi;
+      }
+    }
     // ---- w mod q_i (B -> Q), stored; d2 as key-switching digits ----
     uint64_t* o = w3 + bj * L * N + n;
     uint64_t out[L];
@@ -222,7 +284,7 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
         if (i < L) out[i] = limb_sum_mod(r32 + 8 * ii, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
       }
     }
-    if ((bj % 3) == 2) {  // d2 as key-switching digits
+    if (mixed && (bj % 3) == 2) {  // d2 as three-prime key-switching digits
 #pragma unroll
       for (int gq = 0; gq < NDIG; ++gq) {
         uint64_t r3[DIGIT_PRIMES] = {out[3 * gq], out[3 * gq + 1], out[3 * gq + 2]};
@@ -243,28 +305,34 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
 
 // ---- exact centred lift Q -> B (k_lift) with the conversion on the tensor cores ----
 // Same first-lift modes and residue outputs as k_lift; the auxiliary residues
-// come from one f16 MMA per 128-coefficient tile with the operand B1 (the Q ->
-// B conversion of the scale-and-round) and the correction table T1.
+// come from one f16 MMA per 128-coefficient tile with the operand B1L (the plain
+// Q -> B conversion) and the correction table T1, the centring decision from the
+// same MMA's fixed-point columns.
 constexpr size_t LFT_SMEM = (size_t)(1 + SRT_GROUPS) * SRT_OPER * 2 + TC_T1 * 8 + SRT_GROUPS * 8 + 32;
 
 // the input residues of coefficient `m` of a lift tile (and the subtrahend's, for LIFT_SUB_CT)
-HPD void lift_tile_load(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, int mode, size_t tile,
-                        int m, int logN, uint64_t (&xv)[L], uint64_t (&sv)[L]) {
+template <bool SUBCT>
+HPD void lift_tile_load(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, size_t tile, int m, int logN,
+                        uint64_t (&xv)[L], uint64_t (&sv)[SUBCT ? L : 1]) {
   const int N = 1 << logN;
   const size_t gid = (tile << 7) + m, bc = gid >> logN;
   const size_t off = bc * L * N + (gid & (N - 1));
 #pragma unroll
   for (int i = 0; i < L; ++i) xv[i] = src[off + (size_t)i * N];
-  if (mode == LIFT_SUB_CT) {
+  if (SUBCT) {
 #pragma unroll
     for (int i = 0; i < L; ++i) sv[i] = sub[off + (size_t)i * N];
   }
 }
 
+// SUBCT: mode LIFT_SUB_CT (a second ciphertext is read per coefficient); the
+// other modes read at most one plaintext word, so their prefetch holds half the
+// registers.
+template <bool SUBCT>
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_lift_tc(const uint64_t* __restrict__ src, const uint64_t* __restrict__ sub, uint64_t const_val, int mode,
-              uint64_t* __restrict__ ext, int* __restrict__ status, const uint16_t* __restrict__ tables, int logN,
-              int nct) {
+              uint64_t* __restrict__ ext, int* __restrict__ status, const uint16_t* __restrict__ ops,
+              const uint64_t* __restrict__ tabs, int logN, int nct) {
   extern __shared__ __align__(1024) uint8_t lft_smem[];
   uint16_t* B1s = (uint16_t*)lft_smem;
   uint16_t* As = B1s + SRT_OPER;
@@ -274,11 +342,10 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
   uint32_t* okf = tslot + 1;
   const int N = 1 << logN, t = threadIdx.x, warp = t >> 5, g = warp >> 2, m = t & 127;
   {
-    const uint4* bsrc = (const uint4*)tables;
+    const uint4* bsrc = (const uint4*)(ops + TCT_B1L);
     uint4* dst = (uint4*)lft_smem;
     for (int e = t; e < SRT_OPER / 8; e += SRT_THREADS) dst[e] = bsrc[e];
-    const uint64_t* tsrc = (const uint64_t*)(tables + 2 * SRT_OPER);
-    for (int e = t; e < TC_T1; e += SRT_THREADS) T1s[e] = tsrc[e];
+    for (int e = t; e < TC_T1; e += SRT_THREADS) T1s[e] = tabs[TCT_T1 + e];
   }
   if (t < SRT_GROUPS) mbar_init(mbar + t, 1);
   fence_async_smem();
@@ -293,9 +360,9 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
   const uint32_t a_addr = smem_u32(A), b1_addr = smem_u32(B1s);
   const size_t ntiles = ((size_t)nct * 2) << (logN - 7), stride = (size_t)gridDim.x * SRT_GROUPS;
   uint32_t phase = 0;
-  uint64_t xv[L], sv[L];  // this tile's inputs; the next tile's are loaded during the MMA
+  uint64_t xv[L], sv[SUBCT ? L : 1];  // this tile's inputs; the next tile's are loaded during the MMA
   size_t tile = (size_t)blockIdx.x * SRT_GROUPS + g;
-  if (tile < ntiles) lift_tile_load(src, sub, mode, tile, m, logN, xv, sv);
+  if (tile < ntiles) lift_tile_load<SUBCT>(src, sub, tile, m, logN, xv, sv);
   for (; tile < ntiles; tile += stride) {
     const size_t gid = (tile << 7) + m;
     const int n = (int)(gid & (N - 1));
@@ -303,13 +370,12 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     const int comp = (int)(bc & 1);
     uint64_t* o = ext + bc * NQB * N + n;
     uint64_t y[L];
-    Fix F = {0, 0};
 #pragma unroll
     for (int i = 0; i < L; ++i) {
       const uint64_t p = cK.p[i];
       uint64_t v = xv[i];
-      if (mode == LIFT_SUB_CT) {
-        v = sub_mod(v, sv[i], p);
+      if (SUBCT) {
+        v = sub_mod(v, sv[SUBCT ? i : 0], p);
       } else if (mode == LIFT_SUB_CONST && comp == 0 && n == 0) {
         v = sub_mod(v, mul_shoup(const_val, cK.delta[i], cK.delta_s[i], p), p);
       } else if (mode == LIFT_SUB_PT && comp == 0) {
@@ -319,12 +385,10 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
       }
       o[(size_t)i * N] = v;
       y[i] = mul_shoup(v, cK.qhatinv[i], cK.qhatinv_s[i], p);
-      fix_add(F, fix_term(y[i], cK.om_hi[i], cK.om_lo[i]));
     }
-    const int v = lift_v_mem(F, o, N);  // the exact path re-reads the residues written above
     put_limb_row<L>(A, m, y);
     fence_async_smem();
-    if (tile + stride < ntiles) lift_tile_load(src, sub, mode, tile + stride, m, logN, xv, sv);
+    if (tile + stride < ntiles) lift_tile_load<SUBCT>(src, sub, tile + stride, m, logN, xv, sv);
     named_sync(1 + g, 128);
     if (m == 0) {
       tc_fence_after();
@@ -342,6 +406,16 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     }
     phase ^= 1;
     tc_fence_after();
+    int v;  // floor(S + 1/2), S = sum_i y_i / q_i, from the fixed-point columns 8l + 7
+    {
+      uint32_t e[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) e[l] = tc_ld1(tmem + 8 * l + 7);
+      tc_wait_ld();
+      const Fix F = fix_from_limbs(e);
+      v = fix_round(F, FIX_WINDOW);
+      if (v < 0) v = (int)F.hi + greater_than_half(o, N);  // exact: the residues written above
+    }
 #pragma unroll
     for (int kb = 0; kb < 4; ++kb) {  // four primes (32 columns) per TMEM load
       uint32_t r32[32];

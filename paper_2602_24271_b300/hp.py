@@ -34,6 +34,16 @@ HP_SELECT = 2
 HP_SQUARE = 3
 HP_LT = 4
 
+# hp_budget_op: operations of the static noise-budget estimate
+HP_BUDGET_EQ = 0
+HP_BUDGET_SELECT = 1
+HP_BUDGET_SQUARE = 2
+HP_BUDGET_LT = 3
+HP_BUDGET_BETWEEN = 4
+HP_BUDGET_PRODUCT = 5
+HP_BUDGET_ROTATE_SUM = 6
+HP_BUDGET_MARGIN = 10.0
+
 L = 15
 T = 65537
 
@@ -44,6 +54,7 @@ EXPORTED = [
     "hp_square_noalloc", "hp_autotune", "hp_lt_coefficients", "hp_eq_fanout",
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
     "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm", "hp_probe_tc_timeout", "hp_between",
+    "hp_set_relin_key_fine", "hp_keygen_fine", "hp_budget_estimate", "hp_select_mask",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -70,6 +81,7 @@ class hp_params(ctypes.Structure):
         ("P", ctypes.c_uint64),
         ("t", ctypes.c_uint64),
         ("max_depth", ctypes.c_uint32),
+        ("ks_fine_depth", ctypes.c_uint32),
     ]
 
 
@@ -131,6 +143,11 @@ def load():
         "hp_between": (ctypes.c_int, [H, P64, SZ, ctypes.c_uint64, ctypes.c_uint64, P64, V]),
         "hp_extract_broadcast": (ctypes.c_int, [H, P64, SZ, SZ, SZ, P64, V]),
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
+        "hp_set_relin_key_fine": (ctypes.c_int, [H, P64]),
+        "hp_keygen_fine": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
+        "hp_budget_estimate": (ctypes.c_int, [ctypes.POINTER(hp_params), ctypes.c_int, ctypes.c_uint32,
+                                              ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "hp_select_mask": (ctypes.c_int, [H, P64, P64, SZ, ctypes.c_uint32, ctypes.c_double, P64, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -175,7 +192,8 @@ def _stream(stream) -> int:
 class Context:
     """One libhp handle: parameters, tables, relinearisation key, workspace."""
 
-    def __init__(self, log_n: int, max_tile_ct: int = 0, max_depth: int = 17, q=None, P=None, t=T):
+    def __init__(self, log_n: int, max_tile_ct: int = 0, max_depth: int = 17, q=None, P=None, t=T,
+                 ks_fine_depth: int = 0):
         import torch  # device memory and streams only
 
         self.torch = torch
@@ -186,7 +204,8 @@ class Context:
         self.D = self.L // DIGIT_PRIMES  # key-switching digits
         self.q, self.P, self.t = list(q), int(P), int(t)
         self._q = (ctypes.c_uint64 * len(q))(*q)
-        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth)
+        self.ks_fine_depth = ks_fine_depth
+        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth, ks_fine_depth)
         h = ctypes.c_void_p()
         _check(self.lib.hp_create(ctypes.byref(prm), None, max_tile_ct, ctypes.byref(h)))
         self.h = h
@@ -219,6 +238,17 @@ class Context:
 
     def set_relin_key(self, rk):
         _check(self.lib.hp_set_relin_key(self.h, _ptr(rk)), self.h)
+
+    def keygen_fine(self, seed: int, sk=None, stream=None):
+        """The per-prime relinearisation key ([L, 2, L+1, N]) from the secret, installed."""
+        torch = self.torch
+        sk = self.sk if sk is None else sk
+        rk = torch.empty((self.L, 2, self.L + 1, self.N), dtype=torch.int64, device="cuda")
+        _check(self.lib.hp_keygen_fine(self.h, seed, _ptr(sk), _ptr(rk), _stream(stream)), self.h)
+        return rk
+
+    def set_relin_key_fine(self, rk):
+        _check(self.lib.hp_set_relin_key_fine(self.h, _ptr(rk)), self.h)
 
     def encrypt(self, slots, seed: int, ct_index0: int = 0, sk=None, stream=None):
         torch = self.torch
@@ -268,6 +298,19 @@ class Context:
             out = self.ct_empty(n)
         _check(self.lib.hp_between(self.h, _ptr(x), n, lo, hi, _ptr(out), _stream(stream)), self.h)
         return out
+
+    def select_mask(self, col, mask, mask_depth: int, mask_bits: float, out=None, stream=None):
+        """SELECT (Eq. 5) with any mask: col * mask, relinearised; the mask lies at
+        depth mask_depth with estimated budget mask_bits (see budget_estimate)."""
+        n = col.shape[0]
+        if out is None:
+            out = self.ct_empty(n)
+        _check(self.lib.hp_select_mask(self.h, _ptr(col), _ptr(mask), n, mask_depth, float(mask_bits), _ptr(out),
+                                       _stream(stream)), self.h)
+        return out
+
+    def params(self, max_depth: int = 17) -> hp_params:
+        return hp_params(self.log_n, self.L, self._q, self.P, self.t, max_depth, self.ks_fine_depth)
 
     def eq_fanout(self, x, consts, masks=True, in_set=True, stream=None):
         """GROUP BY masks EQ(x, c_k) ([n_const, n_ct, 2, L, N]) and/or IN(x, consts)
@@ -393,8 +436,17 @@ def lt_coefficients() -> np.ndarray:
     return out
 
 
+def budget_estimate(params: hp_params, op: int, in_depth: int = 0, in_bits: float = 0.0) -> float:
+    """The library's static noise-budget estimate (bits) for `op` (HP_BUDGET_*);
+    host computation, no GPU."""
+    v = ctypes.c_double()
+    _check(load().hp_budget_estimate(ctypes.byref(params), op, in_depth, float(in_bits), ctypes.byref(v)))
+    return v.value
+
+
 def probe_peak(kind: int) -> float:
-    """Register-only peak rate on the current device: 0 = butterflies/s, 1 = MACs/s."""
+    """Register-only peak rate on the current device: 0 = butterflies/s, 1 = MACs/s, 2 = 32-bit-word
+    butterflies/s (a 30-bit prime)."""
     v = ctypes.c_double()
     _check(load().hp_probe_peak(kind, ctypes.byref(v)))
     return v.value

@@ -1,8 +1,9 @@
 """Writes tests/golden/between_n4096.txt: the SHA-256 of the ciphertext the
-oracle computes for BETWEEN (Sec. 4.2.2) on the GPU test's inputs, so that the
-GPU test compares bit for bit without re-running the oracle's two LT
-evaluations (about ten minutes of CPU at N = 4096).  Calls only oracle/ and the
-seeded input recipe of tests/test_gpu_between.py.
+oracle computes for BETWEEN (Sec. 4.2.2: the product (1 - LT(x, lo)) (1 - LT(hi, x))
+of the two comparisons) on the GPU test's inputs, so that the GPU test compares
+bit for bit without re-running the oracle's two LT evaluations (about ten
+minutes of CPU at N = 4096).  Calls only oracle/ and the seeded input recipe of
+tests/test_gpu_between.py.
 
     python tests/golden/make_between_digest.py
 """

@@ -23,7 +23,8 @@ def test_every_config_has_a_composition_and_a_multiplication_count():
     # an EQ chain is 16 squarings (p - 1 = 2^16, Eq. 3); LT's schedule 511 products
     assert bench.OracleSample.COUNTS["ctct"][1] == 16 == bench.HMULT_PER_CT["ctct"]
     assert bench.OracleSample.COUNTS["lt"][1] == 511 == bench.HMULT_PER_CT["lt"]
-    assert bench.OracleSample.COUNTS["between"][1] == 2 * 511
+    # BETWEEN: two LT evaluations and their product (Sec. 4.2.2)
+    assert bench.OracleSample.COUNTS["between"][1] == 2 * 511 + 1 == bench.HMULT_PER_CT["between"]
 
 
 def test_stored_traffic_scales_with_the_tile_and_follows_the_sources():

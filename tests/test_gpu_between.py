@@ -1,7 +1,7 @@
 """BETWEEN (Sec. 4.2.2) on the GPU: [lo <= x <= hi] on every slot of 4
 ciphertexts (one tile of 3 and a ragged tail of 1) with the bounds, values just
 outside them, 0 and (p-1)/2 in the inputs; the tail's ciphertext bit for bit
-against the oracle's combination 1 - LT(x, lo) - LT(hi, x) of its two LT
+against the oracle's product (1 - LT(x, lo)) (1 - LT(hi, x)) of its two LT
 evaluations (through the SHA-256 the oracle wrote into
 tests/golden/between_n4096.txt, see make_between_digest.py); bound errors and
 the empty range lo > hi."""

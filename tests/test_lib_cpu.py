@@ -126,3 +126,4 @@ def test_galois_elements_match_oracle(lib):
     g = (ctypes.c_uint64 * 2)()
     assert lib.hp_galois_elements(2, g) == hp.HP_ERR_ARG
     assert lib.hp_galois_elements(12, None) == hp.HP_ERR_ARG
+

@@ -45,6 +45,14 @@ def test_noalloc_square_matches_hp_run_twice():
     torch.cuda.synchronize()
     assert np.array_equal(hp.to_u64(got2), hp.to_u64(ref2))
     assert not np.array_equal(hp.to_u64(got1), hp.to_u64(got2))
+    # the squaring is 13 launches: lift, tensor, scale-and-round, key-switch
+    # multiply-accumulate and mod-down, plus four two-pass transforms
+    assert ctx.launch_count() == 13
+    # in place (ct_out aliasing ct_in), again bit for bit against hp_run
+    inplace = cts[0:1].clone()
+    _noalloc(ctx, inplace[0], inplace[0])
+    torch.cuda.synchronize()
+    assert np.array_equal(hp.to_u64(inplace), hp.to_u64(ref1))
     ctx.check_status()
     ctx.close()
 
