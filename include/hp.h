@@ -16,8 +16,10 @@
  *                   round(t d / Q) mod Q; key switching (relinearisation,
  *                   rotations) with D = L / 3 digits [d2]_{q_3a q_3a+1 q_3a+2},
  *                   each the residue modulo a group of three data primes, and
- *                   the special prime P.  Results are bit-exact against that
- *                   integer definition.
+ *                   the special prime P; products at multiplicative depth up
+ *                   to the handle's ks_fine_depth are relinearised with L
+ *                   per-prime digits [d2]_{q_i} instead.  Results are bit-exact
+ *                   against that integer definition.
  *
  * Memory layouts (all words uint64, residues canonical in [0, prime)):
  *   ciphertext      [2][L][N]        (c0, c1) residues mod q_0..q_{L-1},
@@ -134,7 +136,9 @@ int hp_keygen_fine(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_f
  *                  when x - y lies in [-(p-1)/2, (p-1)/2] (inputs below 2^15 + 1);
  *                  the polynomial f(z) = z h(z^2) - ((p-1)/2) z^(p-1) of Eq. 4
  *                  is evaluated by baby steps (255 powers of z^2) and giant
- *                  steps (128 powers of z^512): 511 multiplications, depth 18.
+ *                  steps (128 powers of z^512), each power the product of its
+ *                  largest power-of-two part and the rest: 511
+ *                  multiplications, depth 18.
  *                  Device memory only; the first call allocates its workspace
  *                  (about 3.1 GB per ciphertext of the LT tile, tile <= 8 at
  *                  N = 32768).
@@ -161,7 +165,10 @@ typedef struct {
 /* Evaluate `op` (HP_EQ_CT_CT or HP_EQ_CT_CONST) for n_inst instances of
  * uneven size in one pass over the union of their ciphertexts: tiles of
  * ciphertexts, each replayed from a CUDA graph of the whole 16-squaring launch
- * sequence (captured once per tile shape and kept in the handle).  `inst` is
+ * sequence (captured once per tile shape and kept in the handle) whose first
+ * and last kernels are pointed at the tile's own ciphertexts before each
+ * launch, so the ciphertexts are read and written in place (ct_out may alias
+ * ct_x).  `inst` is
  * host memory; ct_x / ct_y / ct_out are device arrays of n_ct_total
  * ciphertexts.  Instance i covers global slots [ct_offset N + slot_offset,
  * + n_slots) inside its ciphertexts ct_offset .. ct_offset + n_ct - 1.  For
@@ -173,23 +180,23 @@ int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst,
                    const uint64_t* ct_y, uint64_t* ct_out, size_t n_ct_total, void* stream);
 
 /* Time the EQ launch sequence for candidate tile sizes (up to the handle's
- * workspace tile) and make the fastest per ciphertext the tile used by hp_run
- * and hp_run_batched; *best_tile (optional) receives it.  Runs on the
+ * workspace tile; per candidate the fastest of three passes after a warm-up
+ * pass) and make the largest tile within 1 % of the fastest per ciphertext the
+ * tile used by hp_run and hp_run_batched; *best_tile (optional) receives it.  Runs on the
  * handle's own staging buffers (the computation is data-oblivious, so the
  * timing does not depend on the data); cached per (ring degree, device, max
  * tile) for the process.  Synchronous. */
 int hp_autotune(hp_handle* h, size_t* best_tile);
 
 /* BETWEEN (Sec. 4.2.2): out[c] = [lo <= x <= hi] slot-wise for plaintext bounds
- * lo <= hi.  The paper's product of the two comparisons, (1 - LT(x, lo))
- * (1 - LT(hi, x)), equals 1 - LT(x, lo) - LT(hi, x) because x < lo and x > hi
- * exclude each other; that form is computed: two LT evaluations (511
- * multiplications each, the Eq. 4 polynomial on x - lo and hi - x, see HP_LT)
- * and no product, so BETWEEN has LT's depth (the product's extra level is more
- * than the noise budget leaves at N = 32768).  Exact when x, lo, hi lie in
- * [0, (t-1)/2]; bounds outside that range or lo > hi give HP_ERR_ARG.  x, out:
- * n_ct device ciphertexts; tiles of up to 8 ciphertexts share the LT
- * workspace.  Needs t = 65537 and the relinearisation key. */
+ * lo <= hi, as the paper's product of the two comparisons,
+ * (1 - LT(x, lo)) (1 - LT(hi, x)): two LT evaluations (511 multiplications
+ * each, the Eq. 4 polynomial on x - lo and hi - x, see HP_LT) and one product,
+ * depth 19.  Exact when x, lo, hi lie in [0, (t-1)/2]; bounds outside that
+ * range or lo > hi give HP_ERR_ARG.  x, out: n_ct device ciphertexts; tiles of
+ * up to 8 ciphertexts share the LT workspace.  Needs t = 65537 and the
+ * relinearisation key.  The result goes on to hp_select_mask with
+ * mask_depth 19 and the budget hp_budget_estimate(HP_BUDGET_BETWEEN) gives. */
 int hp_between(hp_handle* h, const uint64_t* ct_x, size_t n_ct, uint64_t lo, uint64_t hi, uint64_t* ct_out,
                void* stream);
 
