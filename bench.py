@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--config", default="plain", choices=["plain", "const28", "batched", "lt", "between", "in", "sum", "rotsum", "join"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
+    ap.add_argument("--ks-digit-primes", type=int, default=0, choices=[0, 3, 5],
+                    help="data primes per key-switching digit (0: the workload's default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched-vs-plain comparison")
@@ -141,10 +143,21 @@ MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-
 # ciphertext multiplications with relinearisation per N units of each workload
 # (per ciphertext; per ciphertext and B row for join); rotations are not counted
 HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "sum": 17, "rotsum": 0, "join": 18}
-# Shoup products of the three-prime digit recombination per ciphertext and squaring,
-# in units of N: per digit (5) and target prime (16), two products, one for the
-# digit's second prime, none for its first: 5 (14 x 2 + 1) = 145
-DIGIT_PRODUCTS_PER_HMULT = 145
+# Shoup products of the digit recombination per ciphertext and multiplication, in
+# units of N, for digits of G primes: per digit (15 / G) and target prime (16),
+# G - 1 products, or o for the digit's own prime at offset o:
+# G = 3: 5 (13 x 2 + 0 + 1 + 2) = 145; G = 5: 3 (11 x 4 + 0 + 1 + 2 + 3 + 4) = 162
+DIGIT_PRODUCTS_PER_HMULT = {3: 145, 5: 162}
+# key-switching digit grouping per workload (data primes per digit): five-prime
+# digits (3 digits) for the EQ workloads, whose depth-16 chain keeps about 114 bits
+# of noise budget with them at N = 32768; three-prime digits (5) for the others
+# (LT and BETWEEN would not fit with five-prime digits)
+DEFAULT_DIGIT_PRIMES = {"ctct": 5, "const": 5, "batched": 5, "in": 3, "sum": 3, "rotsum": 3, "join": 3, "lt": 3,
+                        "between": 3}
+
+
+def digit_primes(args, op):
+    return args.ks_digit_primes or DEFAULT_DIGIT_PRIMES[op]
 
 
 KERNEL_SOURCES = {  # files whose text determines a kernel's code
@@ -207,12 +220,12 @@ class OracleSample:
         "join": (1, 18, 1, 45 / 64, "the plaintext products of Extract and the additions"),
     }
 
-    def __init__(self, op: str = "ctct"):
+    def __init__(self, op: str = "ctct", dp: int = 3):
         import oracle
         from paper_2602_24271_b300.inputs import eq_pair_columns
 
         self.op = op
-        self.o = oracle.Oracle(LOGN)
+        self.o = oracle.Oracle(LOGN, dp=dp)
         self.o.keygen(SEED_KEY)
         x, y = eq_pair_columns(self.o.N, seed=SEED_DATA)
         self.cx, self.cy = self.o.encrypt(x, 7, 0), self.o.encrypt(y, 7, 1)
@@ -239,22 +252,22 @@ class OracleSample:
             t_rot = time.perf_counter() - t3
         t_sub, t_mul, t_1m = t1 - t0, (t2 - t1) / max(1, n_mul), t3 - t2
         per_unit = n_sub * t_sub + n_m * t_mul + n_1m * t_1m + n_rot * t_rot
-        desc = ("1 ciphertext at N=32768 (32768 slots) on the oracle, single-threaded: a difference, %d "
-                "multiplication(s) with relinearisation, '1 -'%s timed; one unit of the workload composed as "
-                "%d difference(s) + %d multiplications + %d x '1 -'%s%s" % (
-                    n_mul, " and one rotation" if self.g is not None else "", n_sub, n_m, n_1m,
+        desc = ("1 ciphertext at N=32768 (32768 slots) on the oracle, single-threaded, key-switching digits of %d "
+                "primes: a difference, %d multiplication(s) with relinearisation, '1 -'%s timed; one unit of the "
+                "workload composed as %d difference(s) + %d multiplications + %d x '1 -'%s%s" % (
+                    o.dp, n_mul, " and one rotation" if self.g is not None else "", n_sub, n_m, n_1m,
                     " + %.3g rotations" % n_rot if n_rot else "",
                     "; not counted: %s (the rate is an upper bound)" % left_out if left_out else ""))
         return o.N / per_unit, time.perf_counter() - t0, desc
 
 
-def _oracle_worker(op, n_mul, barrier, results):
-    sample = OracleSample(op)
+def _oracle_worker(op, n_mul, barrier, results, dp):
+    sample = OracleSample(op, dp)
     barrier.wait(timeout=120)  # every worker set up: the timed samples run concurrently
     results.put(sample.time(n_mul))
 
 
-def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32):
+def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32, dp: int = 3):
     """The paper's multi-threaded form (Sec. 5.3: independent predicates
     assigned to threads): W = min(32, host cores) single-threaded oracle
     processes (about 0.45 GB of host memory each), started with spawn, set up
@@ -270,7 +283,7 @@ def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32):
     w = max(1, min(max_workers, cores))
     ctx = mp.get_context("spawn")
     barrier, results = ctx.Barrier(w), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(op, n_mul, barrier, results)) for _ in range(w)]
+    procs = [ctx.Process(target=_oracle_worker, args=(op, n_mul, barrier, results, dp)) for _ in range(w)]
     for pr in procs:
         pr.start()
     got, deadline = [], time.time() + 300
@@ -298,7 +311,7 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args.config)
-    sample = OracleSample(wl["op"])
+    sample = OracleSample(wl["op"], digit_primes(args, wl["op"]))
     vals, step_ms, desc = [], [], ""
     for i in range(args.warmup + args.steps):
         v, secs, desc = sample.time(1)
@@ -336,7 +349,7 @@ def run_libhp(args):
 
     wl = workload(args.config)
     n_ct = args.n_ct or wl["n_ct"]
-    ctx = hp.Context(LOGN, max_tile_ct=args.tile)
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, wl["op"]))
     ctx.keygen(SEED_KEY)
     if not args.ncu_region:
         ctx.autotune()
@@ -517,7 +530,7 @@ def run_libhp(args):
     # multiply-accumulates at the derived ALU ceilings, against the step time;
     # the base conversions run on the tensor cores and are not counted
     butterflies = sum(works[c] for c in NTT_CLASSES)
-    digit_products = DIGIT_PRODUCTS_PER_HMULT * N * n_ct * HMULT_PER_CT[wl["op"]] * wl.get("n_const", 1)
+    digit_products = DIGIT_PRODUCTS_PER_HMULT[ctx.ks_digit_primes] * N * n_ct * HMULT_PER_CT[wl["op"]] * wl.get("n_const", 1)
     ks_macs = works.get(8, 0.0)
     t_ideal = (butterflies + digit_products) / (mul_rate / MUL_PER_BUTTERFLY) + ks_macs / (mul_rate / MUL_PER_MAC)
     roof["path_frac"] = t_ideal / (ms_per_step / 1e3)
@@ -528,7 +541,8 @@ def run_libhp(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n_ct_per_gpu": n_ct, "slots_per_gpu": n_ct * N,
-                       "tile_ct": ctx_tile(ctx), "l2": "inputs larger than L2 (%.1f GB of ciphertexts read per step)"
+                       "tile_ct": ctx_tile(ctx), "ks_digit_primes": ctx.ks_digit_primes,
+                       "l2": "inputs larger than L2 (%.1f GB of ciphertexts read per step)"
                        % (n_ct * 2 * 15 * N * 8 * (2 if cy is not None else 1) / 1e9),
                        "parallelism": "replicas" if world == 1 else "dp%d (independent ciphertexts)" % world},
             "roofline": roof, "clocks": clk, "gpu_launches": launches,
@@ -551,11 +565,11 @@ def run_libhp(args):
             line["extras"] = extras_measure(ctx, stream)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:
-        v, secs, desc = OracleSample(wl["op"]).time(8)
+        v, secs, desc = OracleSample(wl["op"], ctx.ks_digit_primes).time(8)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
         try:
-            mc = multicore_baseline(wl["op"])
+            mc = multicore_baseline(wl["op"], dp=ctx.ks_digit_primes)
             mc["speedup_over_one_core_sample"] = mc["value"] / v
         except Exception as e:  # the single-core baseline above stands on its own
             mc = {"value": None, "error": str(e)[:200]}
@@ -616,19 +630,26 @@ def extras_measure(ctx, stream):
                       "check": "closed form on ciphertexts 0, 4096, 8191"}
     del x28, o28
     torch.cuda.empty_cache()
-    # LT over 16 ciphertext pairs, closed form on every slot
+    # LT over 16 ciphertext pairs, closed form on every slot; its depth-18 chain
+    # keeps three-prime key-switching digits
+    lctx = ctx
+    if ctx.ks_digit_primes != 3:
+        lctx = hp.Context(LOGN, max_tile_ct=ctx_tile(ctx), ks_digit_primes=3)
+        lctx.keygen(SEED_KEY)
     nl = 16
     xl, yl = eq_pair_columns(nl * N, seed=SEED_DATA + 7, value_bits=15)
-    cxl = ctx.encrypt(xl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=0)
-    cyl = ctx.encrypt(yl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=nl)
-    ol = ctx.ct_empty(nl)
-    ms = timed(lambda: ctx.run(hp.HP_LT, cxl, cyl, 0, out=ol, stream=stream))
-    assert np.array_equal(ctx.decrypt(ol).reshape(-1), (xl < yl).astype(np.uint32)), "LT result wrong"
+    cxl = lctx.encrypt(xl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=0)
+    cyl = lctx.encrypt(yl.reshape(nl, N), seed=SEED_DATA + 4, ct_index0=nl)
+    ol = lctx.ct_empty(nl)
+    ms = timed(lambda: lctx.run(hp.HP_LT, cxl, cyl, 0, out=ol, stream=stream))
+    assert np.array_equal(lctx.decrypt(ol).reshape(-1), (xl < yl).astype(np.uint32)), "LT result wrong"
     out["lt"] = {"workload": "LT(x, y) (Eq. 4): 16 ciphertext pairs = 2^19 slots, x, y in [0, 2^15], N=32768, "
                  "511 multiplications per ciphertext (depth 18)", "value": nl * N / (ms / 1e3), "unit": UNIT,
                  "ms_per_step": ms, "steps": 1, "warmup": 1, "check": "closed form [x < y] on every slot",
-                 "hmult_per_s": nl * 511 / (ms / 1e3)}
+                 "hmult_per_s": nl * 511 / (ms / 1e3), "ks_digit_primes": lctx.ks_digit_primes}
     del cxl, cyl, ol
+    if lctx is not ctx:
+        lctx.close()
     torch.cuda.empty_cache()
     return out
 
@@ -777,7 +798,7 @@ def run_batched(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     wl = workload("batched")
-    ctx = hp.Context(LOGN, max_tile_ct=args.tile)
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, "batched"))
     ctx.keygen(SEED_KEY)
     tile = ctx.autotune()
     stream = torch.cuda.current_stream()
@@ -788,7 +809,7 @@ def run_batched(args):
     value = r["packed_batched_elements_per_s"]
     cpu = None
     if not args.no_cpu:
-        v, secs, desc = OracleSample("batched").time(8)
+        v, secs, desc = OracleSample("batched", ctx.ks_digit_primes).time(8)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "cpu_seconds": secs}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["packed_ms_per_pass"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

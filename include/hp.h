@@ -25,7 +25,7 @@
  *   ciphertext      [2][L][N]        (c0, c1) residues mod q_0..q_{L-1},
  *                                    coefficient domain; n ciphertexts are
  *                                    contiguous: [n][2][L][N]
- *   relin key       [D][2][L+1][N]   rk_a = (rk_a0, rk_a1) for digit a < D = 5,
+ *   relin key       [D][2][L+1][N]   rk_a = (rk_a0, rk_a1) for digit a < D = L / ks_digit_primes,
  *                                    residues mod q_0..q_{L-1}, P; coefficient
  *                                    domain
  *   secret key      int8 [N]         coefficients in {-1, 0, 1}
@@ -82,6 +82,10 @@ typedef struct {
                              per-prime key (15 digits [d2]_{q_i}, SEAL's decomposition); deeper
                              ones with the three-prime key.  0 = three-prime digits throughout;
                              >= the deepest product = per-prime throughout.  See hp_budget_estimate. */
+  uint32_t ks_digit_primes; /* data primes per digit of the relinearisation and Galois keys: 3 (the
+                               default, also for 0; D = 5 digits) or 5 (D = 3 digits: 48 instead of
+                               80 key-switching transforms per product, for more key-switching noise:
+                               EQ then leaves about 114 bits of budget at N = 32768, against 224) */
 } hp_params;
 
 /* Operations of hp_run / hp_run_batched. */

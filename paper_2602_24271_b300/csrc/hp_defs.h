@@ -18,9 +18,13 @@ constexpr int ID_P = L + K;        // 31
 constexpr int ID_T = L + K + 1;    // 32
 constexpr int NPRIME = L + K + 2;  // 33
 constexpr int NKS = L + 1;         // key-switching targets: q_0..q_{L-1}, P
-constexpr int DIGIT_PRIMES = 3;    // data primes per key-switching digit (relinearisation, rotations)
-constexpr int NDIG = L / DIGIT_PRIMES;  // digits: digit a = [d]_{q_3a q_3a+1 q_3a+2}
+constexpr int DIGIT_PRIMES = 3;    // default data primes per key-switching digit (relinearisation, rotations)
+constexpr int NDIG = L / DIGIT_PRIMES;  // its digits: digit a = [d]_{q_3a q_3a+1 q_3a+2}
 static_assert(L % DIGIT_PRIMES == 0, "digits are whole groups of data primes");
+// The other grouping a handle may choose (ks_digit_primes = 5): three digits
+// [d]_{q_5a ... q_5a+4}, fewer key-switching transforms for more key-switching noise.
+constexpr int DIGIT_PRIMES5 = 5, NDIG5 = L / DIGIT_PRIMES5;
+static_assert(L % DIGIT_PRIMES5 == 0, "digits are whole groups of data primes");
 // The per-prime relinearisation key (digit i = [d]_{q_i}) used for products at
 // output depth <= the handle's ks_fine_depth; its digits draw Philox with
 // object index FINE_OBJ + i.
@@ -65,14 +69,11 @@ struct Consts {
   uint64_t negQt;                         // [-Q 2^64]_t
   uint64_t Qinv_t;                        // [Q^{-1}]_t
   uint64_t Pmodq[L];                      // [P]_{q_i}   (key generation)
-  // key-switching digits in mixed radix: digit a = r0 + q_3a t1 + q_3a q_3a+1 t2
-  // with r0 = [d]_{q_3a}, t1 = (r1 - r0) q_3a^{-1} mod q_3a+1,
-  // t2 = ((r2 - r0) q_3a^{-1} - t1) q_3a+1^{-1} mod q_3a+2 (Garner)
-  uint64_t g01[NDIG], g01_s[NDIG];  // [q_3a^{-1}]_{q_3a+1}
-  uint64_t g02[NDIG], g02_s[NDIG];  // [q_3a^{-1}]_{q_3a+2}
-  uint64_t g12[NDIG], g12_s[NDIG];  // [q_3a+1^{-1}]_{q_3a+2}
-  uint64_t dig1[NDIG][NKS], dig1_s[NDIG][NKS];  // [q_3a]_{p_j}
-  uint64_t dig2[NDIG][NKS], dig2_s[NDIG][NKS];  // [q_3a q_3a+1]_{p_j}
+  // key-switching digits of g primes in mixed radix (Garner, with the inverses
+  // mrc_inv): digit a = t_0 + q_ga t_1 + q_ga q_ga+1 t_2 + ... with t_0 = [d]_{q_ga};
+  // their recombination modulo a target prime p_j uses [q_ga ... q_ga+m-1]_{p_j}:
+  uint64_t digm3[2][NDIG][NKS], digm3_s[2][NDIG][NKS];    // g = 3, m = 1, 2 (index m - 1)
+  uint64_t digm5[4][NDIG5][NKS], digm5_s[4][NDIG5][NKS];  // g = 5, m = 1 .. 4
   uint64_t r32b[K], r32b_s[K];                  // [2^32]_{b_k}
 };
 
@@ -131,7 +132,7 @@ int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t
 enum { BUDGET_EQ = 0, BUDGET_SELECT = 1, BUDGET_SQUARE = 2, BUDGET_LT = 3, BUDGET_BETWEEN = 4, BUDGET_PRODUCT = 5,
        BUDGET_ROTATE_SUM = 6 };
 constexpr double BUDGET_MARGIN = 10.0;
-double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int fine_depth, int op,
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth, int op,
                        int in_depth, double in_bits);
 
 }  // namespace hp

@@ -217,20 +217,24 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
     C->r32b[k] = (uint64_t)(((unsigned __int128)1 << 32) % b[k]);
     C->r32b_s[k] = h_shoup(C->r32b[k], b[k]);
   }
-  for (int a = 0; a < NDIG; ++a) {
-    const uint64_t q0 = q[3 * a], q1 = q[3 * a + 1], q2 = q[3 * a + 2];
-    C->g01[a] = h_invmod(q0 % q1, q1);
-    C->g01_s[a] = h_shoup(C->g01[a], q1);
-    C->g02[a] = h_invmod(q0 % q2, q2);
-    C->g02_s[a] = h_shoup(C->g02[a], q2);
-    C->g12[a] = h_invmod(q1 % q2, q2);
-    C->g12_s[a] = h_shoup(C->g12[a], q2);
-    for (int j = 0; j < NKS; ++j) {
-      const uint64_t pj = j < L ? q[j] : P;
-      C->dig1[a][j] = q0 % pj;
-      C->dig1_s[a][j] = h_shoup(C->dig1[a][j], pj);
-      C->dig2[a][j] = h_mulmod(q0 % pj, q1 % pj, pj);
-      C->dig2_s[a][j] = h_shoup(C->dig2[a][j], pj);
+  // mixed-radix recombination constants [q_ga ... q_ga+m-1]_{p_j} for both groupings
+  for (int j = 0; j < NKS; ++j) {
+    const uint64_t pj = j < L ? q[j] : P;
+    for (int a = 0; a < NDIG; ++a) {
+      uint64_t c = 1;
+      for (int m = 1; m < DIGIT_PRIMES; ++m) {
+        c = h_mulmod(c, q[DIGIT_PRIMES * a + m - 1] % pj, pj);
+        C->digm3[m - 1][a][j] = c;
+        C->digm3_s[m - 1][a][j] = h_shoup(c, pj);
+      }
+    }
+    for (int a = 0; a < NDIG5; ++a) {
+      uint64_t c = 1;
+      for (int m = 1; m < DIGIT_PRIMES5; ++m) {
+        c = h_mulmod(c, q[DIGIT_PRIMES5 * a + m - 1] % pj, pj);
+        C->digm5[m - 1][a][j] = c;
+        C->digm5_s[m - 1][a][j] = h_shoup(c, pj);
+      }
     }
   }
   C->negQt = to_mont((t - Qt) % t, t);
@@ -364,19 +368,19 @@ void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs) {
 //                  noise |digit| sqrt(N) 2^6 / P, so its budget is at most
 //                  (log Q - log t) - (log |digit| + log N / 2 + 6 - log P)
 // B(d) = min(B(d-1) - per level, key-switching bound of the key used at depth d):
-// the three-prime key's bound (about 686 bits at N = 32768) is what costs the
-// first levels' budget when they use it; the per-prime key's lies above the
-// fresh budget.  Every constant sits on the conservative side of the oracle's
+// the three-prime key's bound (about 686 bits at N = 32768; the five-prime
+// key's about 576) is what costs the first levels' budget when they use it;
+// the per-prime key's lies above the fresh budget.  Every constant sits on the conservative side of the oracle's
 // measured budgets (per level 27.6 bits measured at N = 4096, 30.3 at N = 32768).
 struct NoiseModel {
-  double fresh, per_level, ks3, ks1;
+  double fresh, per_level, ks3, ks1;  // ks3: the cap of the handle's main grouping (3 or 5 primes)
 };
-static NoiseModel noise_model(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t) {
+static NoiseModel noise_model(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp) {
   double lq = 0, l3 = 0, l1 = 0;
   for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
-  for (int a = 0; a * DIGIT_PRIMES < nq; ++a) {
+  for (int a = 0; a * dp < nq; ++a) {
     double g = 0;
-    for (int i = a * DIGIT_PRIMES; i < nq && i < (a + 1) * DIGIT_PRIMES; ++i) g += log2((double)q[i]);
+    for (int i = a * dp; i < nq && i < (a + 1) * dp; ++i) g += log2((double)q[i]);
     l3 = l3 > g ? l3 : g;
   }
   for (int i = 0; i < nq; ++i) l1 = l1 > log2((double)q[i]) ? l1 : log2((double)q[i]);
@@ -398,9 +402,9 @@ static double chain_budget(const NoiseModel& m, int depth, int fine_depth) {
   return b;
 }
 
-double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int fine_depth, int op,
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth, int op,
                        int in_depth, double in_bits) {
-  const NoiseModel m = noise_model(log_n, q, nq, P, t);
+  const NoiseModel m = noise_model(log_n, q, nq, P, t, dp);
   // a product of a fresh operand with one of budget `bits` lying at depth `d`
   auto product = [&](double bits, int d) {
     const double floor_d = d <= fine_depth ? m.ks1 : m.ks3;

@@ -67,13 +67,15 @@ enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3
 
 // Optional fused load of the forward column pass: polynomial (b, g, j) of the
 // key-switching batch is digit g of ciphertext b reduced modulo target prime
-// j.  Three-prime digits (dp = 3) are stored in mixed radix as (r0, t1, t2) in
-// w3[b][2][3g .. 3g+2] and recombined as r0 + [q_3g]_{p_j} t1 + [q_3g q_3g+1]_{p_j} t2
-// mod p_j; a per-prime digit (dp = 1) is the residue w3[b][2][g] < q_g, which
-// one conditional subtraction reduces modulo any target (q_g < 2 p_j).
+// j.  A digit of G = dp primes (3 or 5) is stored in mixed radix as
+// (t_0, ..., t_{G-1}) in w3[b][2][Gg .. Gg+G-1] and recombined as
+// t_0 + sum_{m >= 1} [q_Gg ... q_Gg+m-1]_{p_j} t_m mod p_j (the terms whose
+// constant contains p_j itself vanish); a per-prime digit (dp = 1) is the
+// residue w3[b][2][g] < q_g, which one conditional subtraction reduces modulo
+// any target (q_g < 2 p_j).
 struct DigitSrc {
   const uint64_t* w3;  // nullptr: the pass transforms `data` in place
-  int dp;              // data primes per digit: 3 or 1
+  int dp;              // data primes per digit: 1, 3 or 5
 };
 
 // ---- modular helpers for the transform ------------------------------------------
@@ -101,6 +103,60 @@ HPD uint64_t red64to8(uint64_t x, uint64_t p) {
   x = csub(x, 32 * p);
   x = csub(x, 16 * p);
   return csub(x, 8 * p);
+}
+
+// Digit (t_0, ..., t_{G-1}) modulo target p for the 16 rows rb + u RB of one
+// column (offset col), with the NT terms m = 1 .. NT:
+// t_0 < 2p (primes within a factor 2) plus NT Shoup products in [0, 4p), so the
+// sum lies below (2 + 4 NT) p and conditional subtractions of 16p .. p (those
+// below the bound) bring it to [0, p).
+template <int NT, int G, int LOGR, int LOGC>
+HPD void digit_terms(uint64_t (&x)[16], const uint64_t* __restrict__ src, int rb, int col, const uint64_t (&c)[G - 1],
+                     const uint64_t (&cs)[G - 1], const PForm& f) {
+  constexpr int N = 1 << (LOGR + LOGC), C = 1 << LOGC, RB = 1 << (LOGR - 4);
+  const uint64_t p = f.p;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const size_t off = (size_t)(rb + u * RB) * C + col;
+    uint64_t v = src[off];
+#pragma unroll
+    for (int m = 1; m <= NT; ++m) v += mul_shoup4(src[(size_t)m * N + off], c[m - 1], cs[m - 1], f);
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1)
+      if (k < 2 + 4 * NT) v = csub(v, k * p);
+    x[u] = v;
+  }
+}
+
+// Polynomial (b, g, j) of a key-switching batch of G-prime digits: digit g of
+// ciphertext b reduced modulo target prime j.  For a target outside the digit's
+// group every term counts; at offset o inside it the terms m > o vanish (their
+// constant is a multiple of p_j), and at o = 0 the value is t_0 itself, already
+// canonical.
+template <int G, int LOGR, int LOGC>
+HPD void load_digit(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly, int rb, int col, const PForm& f) {
+  constexpr int N = 1 << (LOGR + LOGC), C = 1 << LOGC, RB = 1 << (LOGR - 4), ND = L / G;
+  const int b = poly / (ND * NKS), g = (poly / NKS) % ND, j = poly % NKS;
+  const uint64_t* src = w3 + ((size_t)(b * 3 + 2) * L + g * G) * N;
+  const int o = j - G * g;  // offset of the target inside the digit's group
+  if (o == 0) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + col];
+    return;
+  }
+  uint64_t c[G - 1], cs[G - 1];
+#pragma unroll
+  for (int m = 1; m < G; ++m) {
+    c[m - 1] = G == 3 ? cK.digm3[m - 1][g][j] : cK.digm5[m - 1][g][j];
+    cs[m - 1] = G == 3 ? cK.digm3_s[m - 1][g][j] : cK.digm5_s[m - 1][g][j];
+  }
+  const int nt = (o > 0 && o < G) ? o : G - 1;
+  if (nt == G - 1) return digit_terms<G - 1, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+  if (nt == 1) return digit_terms<1, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+  if constexpr (G > 3) {
+    if (nt == 2) return digit_terms<2, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    if (nt == 3) return digit_terms<3, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+  }
 }
 
 // ---- register blocks --------------------------------------------------------
@@ -234,9 +290,11 @@ HPD void inv_block_scaled(uint64_t (&x)[1 << A], uint32_t base, int logN, const 
 // ---- forward, columns (stages 0 .. LOGR-1) -------------------------------------
 // Block: COLS = 2048 / R adjacent columns.  Step A: thread (k, rb) holds rows
 // rb + 16-stride (stages 0..3); step B: groups of 2^(LOGR-4) consecutive rows.
-template <int LOGR, int LOGC>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
-                                                              DigitSrc dig) {
+// DG selects the input: 0 the polynomials of `data` (in place), 1, 3 or 5 a
+// key-switching batch built from dig.w3 in digits of that many data primes.
+template <int LOGR, int LOGC, int DG>
+__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+                                                                 DigitSrc dig) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
   __shared__ uint64_t s[NTT_TILE];
@@ -248,35 +306,13 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(uint64_t* __restri
   const ulonglong2* tw = T.tw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
   uint64_t x[16];
-  if (dig.w3 && dig.dp == 1) {  // per-prime digits: poly = (b * L + g) * NKS + j
+  if constexpr (DG == 1) {  // per-prime digits: poly = (b * L + g) * NKS + j
     const int b = poly / (NDIG_FINE * NKS), g = (poly / NKS) % NDIG_FINE;
     const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g) * N;
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = csub(src[(size_t)(rb + u * RB) * C + k0 + k], p);
-  } else if (dig.w3) {  // three-prime digits: poly = (b * NDIG + g) * NKS + j
-    const int b = poly / (NDIG * NKS), g = (poly / NKS) % NDIG, j = poly % NKS;
-    const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g * DIGIT_PRIMES) * N;
-    const uint64_t c1 = cK.dig1[g][j], c1s = cK.dig1_s[g][j], c2 = cK.dig2[g][j], c2s = cK.dig2_s[g][j];
-    if (j == DIGIT_PRIMES * g) {  // the digit's own first prime: the value is r0 (canonical)
-#pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + k0 + k];
-    } else if (j == DIGIT_PRIMES * g + 1) {  // [q_3g q_3g+1] = 0 here: no t2 term
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
-        const uint64_t v = csub(src[off] + mul_shoup4(src[N + off], c1, c1s, f), 4 * p);  // < 6p, then < 4p
-        x[u] = csub(csub(v, 2 * p), p);
-      }
-    } else {
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const size_t off = (size_t)(rb + u * RB) * C + k0 + k;
-        // r0 < 2p (primes within a factor 2) and two products in [0, 4p): sum < 10p
-        uint64_t v = src[off] + mul_shoup4(src[N + off], c1, c1s, f) + mul_shoup4(src[2 * N + off], c2, c2s, f);
-        v = csub(csub(v, 8 * p), 4 * p);
-        x[u] = csub(csub(v, 2 * p), p);
-      }
-    }
+  } else if constexpr (DG > 1) {  // digits of DG primes: poly = (b * (L / DG) + g) * NKS + j
+    load_digit<DG, LOGR, LOGC>(x, dig.w3, poly, rb, k0 + k, f);
   } else {
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = a[(size_t)(rb + u * RB) * C + k0 + k];
@@ -479,8 +515,10 @@ struct ModDown {
   int one_minus;
   int pstride, poff;
 };
+// Bounds: 8 blocks per SM (64 registers, 12 B of spills) for the plain pass, 7
+// for the mod-down form (72 registers; 8 would spill 104 B).
 template <int LOGR, int LOGC, bool MD>
-__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+__global__ void __launch_bounds__(NTT_THREADS, MD ? 7 : 8) k_ntt_inv_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
                                                               int scale_mode, ModDown md) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);

@@ -114,18 +114,24 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_gen(const uint64_t* __res
   dprod[((b * 3 + 2) * NQB + pi) * N + n] = mont_mul_lazy(a1, b1, p, pinv);
 }
 
-// Key-switching digit g of a coefficient from its residues r = (r0, r1, r2) mod
-// the group's primes (q0, q1, q2) = (q_3g, q_3g+1, q_3g+2): the digit [d]_{q0 q1 q2}
-// = r0 + q0 t1 + q0 q1 t2 is kept as its mixed-radix form (r0, t1, t2) with
-// t1 = (r1 - r0) q0^{-1} mod q1 and t2 = ((r2 - r0) q0^{-1} - t1) q1^{-1} mod q2
-// (Garner).  Data primes lie within a factor 2 of each other, so one conditional
-// subtraction reduces a residue of one prime modulo another.
-HPD void digit_mixed_radix(uint64_t (&r)[DIGIT_PRIMES], int g) {
-  const uint64_t q1 = cK.p[DIGIT_PRIMES * g + 1], q2 = cK.p[DIGIT_PRIMES * g + 2];
-  const uint64_t t1 = mul_shoup(sub_mod(r[1], csub(r[0], q1), q1), cK.g01[g], cK.g01_s[g], q1);
-  const uint64_t u = mul_shoup(sub_mod(r[2], csub(r[0], q2), q2), cK.g02[g], cK.g02_s[g], q2);
-  r[2] = mul_shoup(sub_mod(u, csub(t1, q2), q2), cK.g12[g], cK.g12_s[g], q2);
-  r[1] = t1;
+// A key-switching digit of G primes from a coefficient's residues r[m] mod
+// q_{base+m} (m < G): the digit [d]_{q_base ... q_base+G-1} = t_0 + q_base t_1 +
+// q_base q_base+1 t_2 + ... is kept as its mixed-radix form (t_0, ..., t_{G-1}),
+// t_0 = r_0 and t_m = (((r_m - t_0) q_base^{-1} - t_1) q_base+1^{-1} - ...) q_base+m-1^{-1}
+// mod q_base+m (Garner).  Data primes lie within a factor 2 of each other, so one
+// conditional subtraction reduces a residue of one prime modulo another.
+template <int G>
+HPD void digit_mixed_radix(uint64_t (&r)[G], int base) {
+#pragma unroll
+  for (int m = 1; m < G; ++m) {
+    const int im = base + m;
+    const uint64_t qm = cK.p[im];
+    uint64_t v = r[m];
+#pragma unroll
+    for (int k = 0; k < m; ++k)
+      v = mul_shoup(sub_mod(v, csub(r[k], qm), qm), cK.mrc_inv[base + k][im], cK.mrc_inv_s[base + k][im], qm);
+    r[m] = v;
+  }
 }
 
 // One thread per (b, j in {0,1,2}, n).  dprod holds t d (coefficient domain,
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_scale_round(const uint64_t* __re
       acc3_mac(a, (uint32_t)vb, 0, cK.negBQ_l[i], cK.negBQ_h[i]);
       r[e] = redc(acc3_fold(a), p, cK.pinv[i]);
     }
-    if (digits) digit_mixed_radix(r, g);
+    if (digits) digit_mixed_radix<DIGIT_PRIMES>(r, g * DIGIT_PRIMES);
 #pragma unroll
     for (int e = 0; e < DIGIT_PRIMES; ++e) o[(size_t)(g * DIGIT_PRIMES + e) * N] = r[e];
   }
@@ -365,26 +371,29 @@ __global__ void k_ct_group_sum(const uint64_t* x, size_t n_ct, size_t group, uin
 
 // Galois automorphism tau_g (rotation of the slots), gathered per output
 // coefficient: tau_g(a)_n = a_j with j = n g^{-1} mod 2N when j < N, else
-// -a_{j - N}.  One thread per (b, digit g, n), covering the digit's primes;
+// -a_{j - N}.  One thread per (b, digit g, n), covering the digit's G primes;
 // writes the key-switching input
 //   w3[b][0] = (acc ? c0 : 0) + tau_g(c0),  w3[b][1] = acc ? c1 : 0,
-//   w3[b][2] = tau_g(c1) as key-switching digits (switched from tau_g(s) to s),
+//   w3[b][2] = tau_g(c1) as key-switching digits of G primes (switched from
+//   tau_g(s) to s),
 // so the mod-down that follows yields ct + rotate(ct) (acc) or rotate(ct).
+template <int G>
 __global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict__ w3, uint32_t ginv, int acc,
                             int logN, int nct) {
+  constexpr int ND = L / G;
   const int N = 1 << logN;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)nct * NDIG * N) return;
+  if (gid >= (size_t)nct * ND * N) return;
   const int n = (int)(gid & (N - 1));
   const size_t bg = gid >> logN;
-  const int g = (int)(bg % NDIG);
-  const size_t b = bg / NDIG;
+  const int g = (int)(bg % ND);
+  const size_t b = bg / ND;
   const uint32_t j = (uint32_t)(((uint64_t)n * ginv) & (2 * (uint64_t)N - 1));
   const uint32_t src = j < (uint32_t)N ? j : j - N;
-  uint64_t r[DIGIT_PRIMES];
+  uint64_t r[G];
 #pragma unroll
-  for (int e = 0; e < DIGIT_PRIMES; ++e) {
-    const int i = g * DIGIT_PRIMES + e;
+  for (int e = 0; e < G; ++e) {
+    const int i = g * G + e;
     const uint64_t q = cK.p[i];
     const uint64_t* x0 = x + ((b * 2 + 0) * L + i) * N;
     const uint64_t* x1 = x + ((b * 2 + 1) * L + i) * N;
@@ -398,9 +407,9 @@ __global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict
     o[(size_t)L * N] = acc ? x1[n] : 0;
     r[e] = t1;
   }
-  digit_mixed_radix(r, g);
+  digit_mixed_radix<G>(r, g * G);
 #pragma unroll
-  for (int e = 0; e < DIGIT_PRIMES; ++e) w3[((b * 3 + 2) * L + g * DIGIT_PRIMES + e) * N + n] = r[e];
+  for (int e = 0; e < G; ++e) w3[((b * 3 + 2) * L + g * G + e) * N + n] = r[e];
 }
 
 // ---- Extract (JOIN, Sec. 4.2.2): product with a plaintext unit vector --------------

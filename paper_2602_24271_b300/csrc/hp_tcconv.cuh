@@ -142,12 +142,12 @@ HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t
 // Persistent: SRT_GROUPS groups of four warps, each taking tiles of 128
 // consecutive coefficients (one per thread) of the nct x 3 coefficient
 // polynomials.  ops / tabs: the operand and correction tables of
-// build_tc_tables (B1S, B2; T1S, T2).  With `mixed` d2 is written as
-// three-prime key-switching digits in mixed radix; otherwise as plain residues
-// (the per-prime digits).
+// build_tc_tables (B1S, B2; T1S, T2).  d2 is written as key-switching digits
+// of dp primes in mixed radix (dp = 3 or 5), or as plain residues (dp = 1: the
+// per-prime digits).
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_scale_round_tc(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3, int* __restrict__ status,
-                     const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int mixed) {
+                     const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int dp) {
   extern __shared__ __align__(1024) uint8_t srt_smem[];
   uint16_t* B1s = (uint16_t*)srt_smem;  // B1S
   uint16_t* B2s = B1s + SRT_OPER;       // B2
@@ -284,13 +284,25 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
         if (i < L) out[i] = limb_sum_mod(r32 + 8 * ii, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
       }
     }
-    if (mixed && (bj % 3) == 2) {  // d2 as three-prime key-switching digits
+    if ((bj % 3) == 2 && dp == DIGIT_PRIMES) {  // d2 as three-prime key-switching digits
 #pragma unroll
       for (int gq = 0; gq < NDIG; ++gq) {
-        uint64_t r3[DIGIT_PRIMES] = {out[3 * gq], out[3 * gq + 1], out[3 * gq + 2]};
-        digit_mixed_radix(r3, gq);
-        out[3 * gq + 1] = r3[1];
-        out[3 * gq + 2] = r3[2];
+        uint64_t r3[DIGIT_PRIMES];
+#pragma unroll
+        for (int e = 0; e < DIGIT_PRIMES; ++e) r3[e] = out[DIGIT_PRIMES * gq + e];
+        digit_mixed_radix<DIGIT_PRIMES>(r3, DIGIT_PRIMES * gq);
+#pragma unroll
+        for (int e = 1; e < DIGIT_PRIMES; ++e) out[DIGIT_PRIMES * gq + e] = r3[e];
+      }
+    } else if ((bj % 3) == 2 && dp == DIGIT_PRIMES5) {  // d2 as five-prime key-switching digits
+#pragma unroll
+      for (int gq = 0; gq < NDIG5; ++gq) {
+        uint64_t r5[DIGIT_PRIMES5];
+#pragma unroll
+        for (int e = 0; e < DIGIT_PRIMES5; ++e) r5[e] = out[DIGIT_PRIMES5 * gq + e];
+        digit_mixed_radix<DIGIT_PRIMES5>(r5, DIGIT_PRIMES5 * gq);
+#pragma unroll
+        for (int e = 1; e < DIGIT_PRIMES5; ++e) out[DIGIT_PRIMES5 * gq + e] = r5[e];
       }
     }
 #pragma unroll

@@ -34,7 +34,10 @@ struct hp_handle {
   // transform tables [NPRIME][N] and scaling constants [NSCALE][NPRIME][4]
   ulonglong2 *tw = nullptr, *itw = nullptr;  // (value, Shoup) pairs
   uint64_t* scale = nullptr;
-  // relinearisation key, NTT domain, Montgomery form: [NDIG][2][NKS][N]
+  // key-switching digits of the relinearisation and Galois keys: dp primes
+  // each (3 or 5), nd = L / dp of them
+  int dp = DIGIT_PRIMES, nd = NDIG;
+  // relinearisation key, NTT domain, Montgomery form: [nd][2][NKS][N]
   uint64_t* rkm = nullptr;
   bool have_rk = false;
   // products at output depth <= fine_depth are relinearised with the per-prime
@@ -194,7 +197,14 @@ static void ntt_fwd_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, Dig
   const double half = (double)npoly * (h->N / 2);
   {
     ProfScope ps(h, PK_NTT_FWD_COLS, s, half * LR);
-    k_ntt_fwd_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
+    if (!dig.w3)
+      k_ntt_fwd_cols<LR, LC, 0><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
+    else if (dig.dp == 1)
+      k_ntt_fwd_cols<LR, LC, 1><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
+    else if (dig.dp == DIGIT_PRIMES5)
+      k_ntt_fwd_cols<LR, LC, DIGIT_PRIMES5><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
+    else
+      k_ntt_fwd_cols<LR, LC, DIGIT_PRIMES><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
   }
   {
     ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * LC);
@@ -216,7 +226,7 @@ static void ntt_fwd_sq_t(hp_handle* h, uint64_t* ext, uint64_t* dprod, int nct, 
   d.dp = DIGIT_PRIMES;
   {
     ProfScope ps(h, PK_NTT_FWD_COLS, s, half * LR);
-    k_ntt_fwd_cols<LR, LC><<<gc, NTT_THREADS, 0, s>>>(ext, MAP_QB, tabs(h), d);
+    k_ntt_fwd_cols<LR, LC, 0><<<gc, NTT_THREADS, 0, s>>>(ext, MAP_QB, tabs(h), d);
   }
   {
     ProfScope ps(h, PK_NTT_FWD_ROWS, s, half * LC);
@@ -314,11 +324,24 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
 // product lies at multiplicative depth `depth`, which selects the key:
 // per-prime digits up to the handle's fine depth, three-prime digits below it
 // ---------------------------------------------------------------------------
+// The key-switching multiply-accumulate for keys of nd digits (3, 5 or 15).
+static void ks_mac(hp_handle* h, const uint64_t* rk, int nd, int b, cudaStream_t s) {
+  const unsigned grid = ew_blocks((size_t)NKS * h->N);
+  ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * nd * NKS * h->N);
+  if (nd == NDIG_FINE)
+    k_ks_mac<NDIG_FINE><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
+  else if (nd == NDIG5)
+    k_ks_mac<NDIG5><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
+  else
+    k_ks_mac<NDIG><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
+  h->launches += 1;
+}
+
 static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int one_minus, cudaStream_t s,
                            int depth) {
   const int N = h->N, logN = h->logn;
   const bool fine = depth <= (int)h->fine_depth;
-  const int nd = fine ? NDIG_FINE : NDIG;
+  const int nd = fine ? NDIG_FINE : h->nd, dp = fine ? 1 : h->dp;
   if (general) {  // SELECT: general product
     ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
@@ -333,22 +356,15 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
     ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
     const size_t tiles = ((size_t)b * 3 * N) >> 7, ctas = (tiles + SRT_GROUPS - 1) / SRT_GROUPS;
     k_scale_round_tc<<<(unsigned)std::min<size_t>(ctas, (size_t)h->sms), SRT_THREADS, SRT_SMEM, s>>>(
-        h->dprod, h->w3, h->status, h->tct, h->tctab, logN, b, fine ? 0 : 1);
+        h->dprod, h->w3, h->status, h->tct, h->tctab, logN, b, dp);
   }
   h->launches += 1;
-  // key switching: the digits [d2]_{Q_a} (three data primes each, stored in
+  // key switching: the digits [d2]_{Q_a} (dp data primes each, stored in
   // mixed radix by the scale-and-round, or one prime each) reduced mod every
   // target prime p_j in the first transform pass, key multiply-accumulate,
   // inverse transform, mod-down
-  ntt_fwd(h, h->ksin, (size_t)b * nd * NKS, MAP_KS, s, h->w3, fine ? 1 : DIGIT_PRIMES);
-  {
-    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * nd * NKS * N);
-    if (fine)
-      k_ks_mac<NDIG_FINE><<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm1, h->ksout, logN, b);
-    else
-      k_ks_mac<NDIG><<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->rkm, h->ksout, logN, b);
-  }
-  h->launches += 1;
+  ntt_fwd(h, h->ksin, (size_t)b * nd * NKS, MAP_KS, s, h->w3, dp);
+  ks_mac(h, fine ? h->rkm1 : h->rkm, nd, b, s);
   ntt_inv_moddown(h, h->ksout, b, out, one_minus, s);
 }
 
@@ -714,6 +730,13 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   h->t = prm->t;
   h->max_depth = prm->max_depth;
   h->fine_depth = prm->ks_fine_depth;
+  if (prm->ks_digit_primes != 0 && prm->ks_digit_primes != DIGIT_PRIMES && prm->ks_digit_primes != DIGIT_PRIMES5) {
+    g_create_err = "ks_digit_primes must be 0 (default 3), 3 or 5";
+    delete h;
+    return HP_ERR_UNSUPPORTED;
+  }
+  h->dp = prm->ks_digit_primes ? (int)prm->ks_digit_primes : DIGIT_PRIMES;
+  h->nd = L / h->dp;
   char eb[256] = {0};
   int rc = build_consts(h->q, h->P, h->t, &h->C, eb, sizeof(eb));
   if (rc != 0) {
@@ -743,7 +766,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
 
   if ((rc = build_tables(h)) != HP_OK) return fail(rc);
   if ((rc = build_tc(h)) != HP_OK) return fail(rc);
-  const int nd_ws = h->fine_depth > 0 ? NDIG_FINE : NDIG;
+  const int nd_ws = h->fine_depth > 0 ? NDIG_FINE : h->nd;
   size_t per = ws_words_per_ct(h->N, nd_ws) * sizeof(uint64_t);
   // default: about 11 GB of workspace, i.e. the largest tile (64 ciphertexts at N = 32768)
   h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)11 << 30) / per);
@@ -758,7 +781,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
                 {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
                 {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
                 {&h->stx2, T * 2 * L * N},   {&h->sty2, T * 2 * L * N},   {&h->sto2, T * 2 * L * N},
-                {&h->rkm, (size_t)NDIG * 2 * NKS * N},
+                {&h->rkm, (size_t)h->nd * 2 * NKS * N},
                 {&h->rkm1, h->fine_depth > 0 ? (size_t)NDIG_FINE * 2 * NKS * N : 0}};
   for (auto& a : allocs) {
     if (a.words == 0) continue;
@@ -797,7 +820,7 @@ static int install_ks_key(hp_handle* h, uint64_t* dst, const uint64_t* key, int 
 int hp_set_relin_key(hp_handle* h, const uint64_t* rk) {
   if (!h) return HP_ERR_ARG;
   if (!rk) HP_FAIL(h, HP_ERR_ARG, "null relinearisation key");
-  if (int rc = install_ks_key(h, h->rkm, rk, NDIG, 0)) return rc;
+  if (int rc = install_ks_key(h, h->rkm, rk, h->nd, 0)) return rc;
   CU(h, cudaDeviceSynchronize());
   h->have_rk = true;
   return HP_OK;
@@ -818,7 +841,7 @@ static bool keys_ready(const hp_handle* h) { return h->have_rk && (h->fine_depth
 
 // The static budget estimate of `op` on this handle's parameters.
 static double budget_of(const hp_handle* h, int op, int in_depth = 0, double in_bits = 0) {
-  return budget_estimate(h->logn, h->q, L, h->P, h->t, (int)h->fine_depth, op, in_depth, in_bits);
+  return budget_estimate(h->logn, h->q, L, h->P, h->t, h->dp, (int)h->fine_depth, op, in_depth, in_bits);
 }
 #define HP_NEED_BUDGET(h, op, what)                                                                        \
   do {                                                                                                     \
@@ -1265,14 +1288,14 @@ int hp_galois_elements(int logn, uint64_t* g_out) {
   return HP_OK;
 }
 
-static size_t key_words(const hp_handle* h) { return (size_t)NDIG * 2 * NKS * h->N; }
+static size_t key_words(const hp_handle* h) { return (size_t)h->nd * 2 * NKS * h->N; }
 
 static int install_galois_key(hp_handle* h, int st, const uint64_t* gk, cudaStream_t s) {
   const size_t kw = key_words(h);
   uint64_t* dst = h->gkm + (size_t)st * kw;
   CU(h, cudaMemcpyAsync(dst, gk, kw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-  ntt_fwd(h, dst, (size_t)NDIG * 2 * NKS, MAP_KS, s);
-  k_to_mont<<<ew_blocks(kw), EW_THREADS, 0, s>>>(dst, NKS, 0, ID_P, (size_t)NDIG * 2 * NKS, h->logn);
+  ntt_fwd(h, dst, (size_t)h->nd * 2 * NKS, MAP_KS, s);
+  k_to_mont<<<ew_blocks(kw), EW_THREADS, 0, s>>>(dst, NKS, 0, ID_P, (size_t)h->nd * 2 * NKS, h->logn);
   CU(h, cudaGetLastError());
   return HP_OK;
 }
@@ -1308,7 +1331,7 @@ int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk
   int8_t* ts = nullptr;
   CU(h, cudaMalloc(&S, (size_t)NKS * N * 8));
   CU(h, cudaMalloc(&S2, (size_t)NKS * N * 8));
-  CU(h, cudaMalloc(&A, (size_t)NDIG * NKS * N * 8));
+  CU(h, cudaMalloc(&A, (size_t)h->nd * NKS * N * 8));
   CU(h, cudaMalloc(&ts, N));
   if (!gk) CU(h, cudaMalloc(&K, kw * 8));
   k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(sk, S, NKS, 0, ID_P, N);
@@ -1318,13 +1341,14 @@ int hp_galois_keygen(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* gk
     const uint32_t obj = (uint32_t)(g[st] << 5);
     k_secret_automorph<<<ew_blocks(N), EW_THREADS, 0, s>>>(sk, ts, (uint32_t)g[st], logN);
     k_secret_to_primes<<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(ts, S2, NKS, 0, ID_P, N);
-    k_rk_sample_a<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(key, A, seed, logN, DOM_A_GK, obj, NDIG);
-    ntt_fwd(h, A, (size_t)NDIG * NKS, MAP_KS, s);
-    k_pointwise_mont<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P,
-                                                                          (size_t)NDIG * NKS, logN);
-    ntt_inv(h, A, (size_t)NDIG * NKS, MAP_KS, SCALE_NINV_R, s);
-    k_rk_finish<<<ew_blocks((size_t)NDIG * NKS * N), EW_THREADS, 0, s>>>(key, A, S2, seed, logN, DOM_E_GK, obj, NDIG,
-                                                                         DIGIT_PRIMES);
+    const int nd = h->nd;
+    k_rk_sample_a<<<ew_blocks((size_t)nd * NKS * N), EW_THREADS, 0, s>>>(key, A, seed, logN, DOM_A_GK, obj, nd);
+    ntt_fwd(h, A, (size_t)nd * NKS, MAP_KS, s);
+    k_pointwise_mont<<<ew_blocks((size_t)nd * NKS * N), EW_THREADS, 0, s>>>(A, S, A, NKS, NKS, 0, ID_P,
+                                                                        (size_t)nd * NKS, logN);
+    ntt_inv(h, A, (size_t)nd * NKS, MAP_KS, SCALE_NINV_R, s);
+    k_rk_finish<<<ew_blocks((size_t)nd * NKS * N), EW_THREADS, 0, s>>>(key, A, S2, seed, logN, DOM_E_GK, obj, nd,
+                                                                       h->dp);
     if (int rc = install_galois_key(h, st, key, s)) return rc;
   }
   CU(h, cudaGetLastError());
@@ -1343,16 +1367,14 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
   const int N = h->N, logN = h->logn;
   {
     ProfScope ps(h, PK_AUTOMORPH, s, 3.0 * b * L * N);
-    k_automorph<<<ew_blocks((size_t)b * NDIG * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+    if (h->dp == DIGIT_PRIMES5)
+      k_automorph<DIGIT_PRIMES5><<<ew_blocks((size_t)b * NDIG5 * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+    else
+      k_automorph<DIGIT_PRIMES><<<ew_blocks((size_t)b * NDIG * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
   }
   h->launches += 1;
-  ntt_fwd(h, h->ksin, (size_t)b * NDIG * NKS, MAP_KS, s, h->w3);
-  {
-    ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * NDIG * NKS * N);
-    k_ks_mac<NDIG><<<ew_blocks((size_t)NKS * N), EW_THREADS, 0, s>>>(h->ksin, h->gkm + (size_t)st * key_words(h),
-                                                                    h->ksout, logN, b);
-  }
-  h->launches += 1;
+  ntt_fwd(h, h->ksin, (size_t)b * h->nd * NKS, MAP_KS, s, h->w3, h->dp);
+  ks_mac(h, h->gkm + (size_t)st * key_words(h), h->nd, b, s);
   ntt_inv_moddown(h, h->ksout, b, ct, 0, s);
 }
 
@@ -1596,8 +1618,10 @@ int hp_select_mask(hp_handle* h, const uint64_t* col, const uint64_t* mask, size
 int hp_budget_estimate(const hp_params* prm, int op, uint32_t in_depth, double in_bits, double* out_bits) {
   if (!prm || !prm->q || !out_bits || op < BUDGET_EQ || op > BUDGET_ROTATE_SUM) return HP_ERR_ARG;
   if (prm->log_n < LOGN_MIN || prm->log_n > LOGN_MAX || prm->L != (uint32_t)L || prm->t < 2) return HP_ERR_ARG;
-  *out_bits = budget_estimate((int)prm->log_n, prm->q, L, prm->P, prm->t, (int)prm->ks_fine_depth, op, (int)in_depth,
-                              in_bits);
+  const int dp = prm->ks_digit_primes ? (int)prm->ks_digit_primes : DIGIT_PRIMES;
+  if (dp != DIGIT_PRIMES && dp != DIGIT_PRIMES5) return HP_ERR_ARG;
+  *out_bits = budget_estimate((int)prm->log_n, prm->q, L, prm->P, prm->t, dp, (int)prm->ks_fine_depth, op,
+                              (int)in_depth, in_bits);
   return HP_OK;
 }
 
@@ -1677,7 +1701,7 @@ int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* strea
   if (!sk || !rk) HP_FAIL(h, HP_ERR_ARG, "null output");
   cudaStream_t s = (cudaStream_t)stream;
   k_sample_secret<<<ew_blocks(h->N), EW_THREADS, 0, s>>>(sk, seed, h->N);
-  if (int rc = make_relin_key(h, seed, sk, rk, NDIG, DIGIT_PRIMES, 0, s)) return rc;
+  if (int rc = make_relin_key(h, seed, sk, rk, h->nd, h->dp, 0, s)) return rc;
   if (int rc = hp_set_relin_key(h, rk)) return rc;
   if (h->fine_depth > 0) return hp_keygen_fine(h, seed, sk, nullptr, stream);
   return HP_OK;
@@ -1914,9 +1938,9 @@ int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, voi
     HP_FAIL(h, HP_ERR_UNSUPPORTED,
             "hp_square_noalloc: ring degree %d exceeds the static scratch limit of %d (%zu words)", h->N,
             1 << NOALLOC_MAX_LOGN, NOALLOC_WORDS);
-  if (h->fine_depth > 0)
-    HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: handles with ks_fine_depth > 0 are not supported (its scratch "
-                                   "holds three-prime key-switching digits only)");
+  if (h->fine_depth > 0 || h->dp != DIGIT_PRIMES)
+    HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: only handles with three-prime key-switching digits and "
+                                   "ks_fine_depth = 0 are supported (its scratch holds three-prime digits only)");
   if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
   if (((uintptr_t)ct_in | (uintptr_t)ct_out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
   int cur = -1;

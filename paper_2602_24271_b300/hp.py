@@ -64,7 +64,7 @@ KERNEL_OF_CLASS = ["k_ntt_fwd_cols", "k_ntt_fwd_rows(_sq)", "k_ntt_inv_rows", "k
                    "k_scale_round_tc", "k_automorph", "k_ks_mac", "k_moddown"]
 
 
-DIGIT_PRIMES = 3  # data primes per key-switching digit (D = L / 3 digits)
+DIGIT_PRIMES = 3  # default data primes per key-switching digit (D = L / 3 digits); 5 is the other choice
 
 
 class HpError(RuntimeError):
@@ -82,6 +82,7 @@ class hp_params(ctypes.Structure):
         ("t", ctypes.c_uint64),
         ("max_depth", ctypes.c_uint32),
         ("ks_fine_depth", ctypes.c_uint32),
+        ("ks_digit_primes", ctypes.c_uint32),
     ]
 
 
@@ -193,7 +194,7 @@ class Context:
     """One libhp handle: parameters, tables, relinearisation key, workspace."""
 
     def __init__(self, log_n: int, max_tile_ct: int = 0, max_depth: int = 17, q=None, P=None, t=T,
-                 ks_fine_depth: int = 0):
+                 ks_fine_depth: int = 0, ks_digit_primes: int = DIGIT_PRIMES):
         import torch  # device memory and streams only
 
         self.torch = torch
@@ -201,11 +202,11 @@ class Context:
         if q is None:
             q, P, t = default_params()
         self.log_n, self.N, self.L = log_n, 1 << log_n, len(q)
-        self.D = self.L // DIGIT_PRIMES  # key-switching digits
+        self.D = self.L // ks_digit_primes  # key-switching digits
         self.q, self.P, self.t = list(q), int(P), int(t)
         self._q = (ctypes.c_uint64 * len(q))(*q)
-        self.ks_fine_depth = ks_fine_depth
-        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth, ks_fine_depth)
+        self.ks_fine_depth, self.ks_digit_primes = ks_fine_depth, ks_digit_primes
+        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth, ks_fine_depth, ks_digit_primes)
         h = ctypes.c_void_p()
         _check(self.lib.hp_create(ctypes.byref(prm), None, max_tile_ct, ctypes.byref(h)))
         self.h = h
@@ -310,7 +311,8 @@ class Context:
         return out
 
     def params(self, max_depth: int = 17) -> hp_params:
-        return hp_params(self.log_n, self.L, self._q, self.P, self.t, max_depth, self.ks_fine_depth)
+        return hp_params(self.log_n, self.L, self._q, self.P, self.t, max_depth, self.ks_fine_depth,
+                         self.ks_digit_primes)
 
     def eq_fanout(self, x, consts, masks=True, in_set=True, stream=None):
         """GROUP BY masks EQ(x, c_k) ([n_const, n_ct, 2, L, N]) and/or IN(x, consts)
@@ -330,7 +332,7 @@ class Context:
 
     def galois_keygen(self, seed: int, sk=None, keep: bool = False, stream=None):
         """Galois keys of the rotate-and-add reduction (installed); returned as
-        [logN, L, 2, L+1, N] when `keep`."""
+        [logN, D, 2, L+1, N] (D key-switching digits) when `keep`."""
         sk = self.sk if sk is None else sk
         gk = self.torch.empty((self.log_n, self.D, 2, self.L + 1, self.N), dtype=self.torch.int64,
                               device="cuda") if keep else None

@@ -1,7 +1,8 @@
 """GPU parity of the batched form (hp_run_batched): uneven instances, packed
 into shared ciphertexts or one group of ciphertexts each, graph-replayed tiles,
 autotuned tile size — bit-exact against hp_run and the oracle, and against the
-closed form per instance after decryption."""
+closed form per instance after decryption; with key-switching digits of three
+and of five primes."""
 import numpy as np
 import pytest
 
@@ -15,21 +16,21 @@ LOGN = 12
 SEED_KEY = 2024
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[3, 5])
+def ctx(request):
     import torch
 
     assert torch.cuda.is_available()
     build.build()
-    c = hp.Context(LOGN, max_tile_ct=3)
+    c = hp.Context(LOGN, max_tile_ct=3, ks_digit_primes=request.param)
     c.keygen(SEED_KEY)
     yield c
     c.close()
 
 
 @pytest.fixture(scope="module")
-def orc():
-    o = oracle.Oracle(LOGN)
+def orc(ctx):
+    o = oracle.Oracle(LOGN, dp=ctx.ks_digit_primes)
     o.keygen(SEED_KEY)
     return o
 

@@ -1,6 +1,7 @@
 """Full-size parity at N = 32768 in the benchmark's launch configuration
-(autotuned tiles): the plain workload (2^26 slots = 2048 ciphertext pairs) and
-the constant form at 2^28 slots (8192 ciphertexts).  Every slot of every
+(autotuned tiles, key-switching digits of five primes): the plain workload
+(2^26 slots = 2048 ciphertext pairs) and the constant form at 2^28 slots (8192
+ciphertexts).  Every slot of every
 result is checked against the closed form [x == y] after GPU decryption (whose
 own parity with the oracle is tested at N = 4096 and again here on samples),
 and 16 seeded sampled ciphertexts of each workload (the first and the last
@@ -19,6 +20,7 @@ pytestmark = pytest.mark.gpu
 LOGN = 15
 SEED_KEY = 1
 N_SAMPLES = 16
+DP = 5  # data primes per key-switching digit, as the benchmark's EQ workloads use
 
 
 def sample_indices(n_ct: int, seed: int):
@@ -36,10 +38,10 @@ def big():
     import torch
 
     build.build()
-    ctx = hp.Context(LOGN)
+    ctx = hp.Context(LOGN, ks_digit_primes=DP)
     ctx.keygen(SEED_KEY)
     ctx.autotune()
-    o = oracle.Oracle(LOGN)
+    o = oracle.Oracle(LOGN, dp=DP)
     o.keygen(SEED_KEY)
     yield ctx, o
     ctx.close()
@@ -76,7 +78,7 @@ def test_plain_workload_2048_pairs(big):
     assert np.array_equal(dec.reshape(-1), (x == y).astype(np.uint32))
     ctx.check_status()
     idx = sample_indices(n_ct, 101)
-    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], [hp.to_u64(cy[c]) for c in idx])
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], [hp.to_u64(cy[c]) for c in idx], dp=DP)
     for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
         assert np.array_equal(hp.to_u64(out[c]), w), c
     import torch
@@ -94,14 +96,14 @@ def test_const_workload_2_28_slots(big):
     x = rng.integers(0, 1 << 16, n_ct * N, dtype=np.uint32)
     x[rng.random(n_ct * N) < 0.25] = cval
     cx = encrypt_chunked(ctx, x, n_ct, 3, 0)
-    out = ctx.eq(cx, None, const_val=cval)
+    out = ctx.eq(cx, None, const_val=cval, dp=DP)
     ctx.check_status()
     for c0 in range(0, n_ct, 512):
         c1 = min(n_ct, c0 + 512)
         dec = decrypt_chunked(ctx, out[c0:c1])
         assert np.array_equal(dec.reshape(-1), (x[c0 * N:c1 * N] == cval).astype(np.uint32))
     idx = sample_indices(n_ct, 103)
-    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], None, const_val=cval)
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], None, const_val=cval, dp=DP)
     for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
         assert np.array_equal(hp.to_u64(out[c]), w), c
     del cx, out

@@ -49,11 +49,11 @@ def test_default_params_bad_args(lib):
     assert lib.hp_default_params(16, q, ctypes.byref(P), ctypes.byref(t)) == hp.HP_ERR_ARG
 
 
-def _create(lib, log_n=15, max_depth=16, q=None, P=None, t=65537):
+def _create(lib, log_n=15, max_depth=16, q=None, P=None, t=65537, dp=0):
     if q is None:
         q, P, t = hp.default_params()
     qa = (ctypes.c_uint64 * len(q))(*q)
-    prm = hp.hp_params(log_n, len(q), qa, P, t, max_depth)
+    prm = hp.hp_params(log_n, len(q), qa, P, t, max_depth, 0, dp)
     h = ctypes.c_void_p()
     rc = lib.hp_create(ctypes.byref(prm), None, 1, ctypes.byref(h))
     return rc, h
@@ -70,6 +70,10 @@ def test_create_rejects_bad_parameters(lib):
     assert rc == hp.HP_ERR_ARG
     rc, _ = _create(lib, q=q, P=P, t=257)
     assert rc == hp.HP_ERR_UNSUPPORTED
+    for dp in (1, 2, 4, 15):  # key-switching digits of 3 or 5 primes only
+        rc, _ = _create(lib, dp=dp)
+        assert rc == hp.HP_ERR_UNSUPPORTED
+        assert b"ks_digit_primes" in lib.hp_last_error(None)
 
 
 def test_backward_is_unsupported(lib):
