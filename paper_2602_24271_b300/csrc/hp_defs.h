@@ -105,10 +105,19 @@ uint64_t h_shoup(uint64_t w, uint64_t p);
 //   B2:           row 8i+b (i < L, b < 7), column 8k+a (k < K, a < 7):
 //                 limb b of [2^(8a) (B/b_k)]_{q_i}; row 120+l: limb l of
 //                 floor(2^(64+8a) / b_k) (the fixed-point sum of y_k / b_k).
+//   Bias columns: 2048 in every row of columns TC_BIAS1 (B1L, B1S: 120, 121,
+//                 where the A operand's unused residue slot 15 holds 2048, 2048)
+//                 and TC_BIAS2 (B2: 7, 15, the zero eighth columns of residues
+//                 0 and 1, where A holds 2048): every accumulator word receives
+//                 2 x 2048 x 2048 = 2^23, so it holds the f32 value 2^23 + D with
+//                 D < 2^23 in its low 23 bits.
 // Correction tables (uint64):
 //   T1 [16][16]:  [-v Q]_{b_k} for v < 16 (k < K);  T1S: the same times [Q^{-1} (B/b_k)^{-1}]_{b_k}
-//   T2 [17][16]:  [-v B]_{q_i} for v <= K (i < L; column 15 unused)
-constexpr int TC_ROWS = 128, TC_K = 128, TC_T1 = 16 * 16, TC_T2 = 17 * 16;
+//   T2 [33][16]:  [-v B]_{q_i} for v <= 2K (i < L; column 15 unused): the B -> Q
+//                 operand's residues lie in [0, 2 b_k), so its centring count is at most 2K
+constexpr int TC_ROWS = 128, TC_K = 128, TC_T1 = 16 * 16, TC_T2 = 33 * 16;
+constexpr int TC_BIAS1[2] = {120, 121}, TC_BIAS2[2] = {7, 15};
+static_assert(TC_T2 == (2 * K + 1) * 16 && L < TC_K / 8 && K == TC_K / 8, "table and slot sizes");
 constexpr int TC_OPER = TC_ROWS * TC_K;                       // f16 elements of one operand
 constexpr int TCT_B1L = 0, TCT_B1S = TC_OPER, TCT_B2 = 2 * TC_OPER, TCT_OPS = 3 * TC_OPER;  // in f16 elements
 constexpr int TCT_T1 = 0, TCT_T1S = TC_T1, TCT_T2 = 2 * TC_T1, TCT_TABS = 2 * TC_T1 + TC_T2;  // in words

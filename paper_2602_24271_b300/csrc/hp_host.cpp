@@ -294,10 +294,13 @@ int lt_coefficients(uint32_t* out) {
 }
 
 // f16 bit pattern of an integer below 2048 (exact: at most 11 significant bits)
+// f16 bit pattern of an integer v < 2^16 that f16 holds exactly (v < 2048, or
+// v with no bits below its eleven leading ones)
 static uint16_t f16_of_int(uint32_t v) {
   if (v == 0) return 0;
-  int e = 31 - __builtin_clz(v);  // v = 1.m 2^e
-  return (uint16_t)(((uint32_t)(e + 15) << 10) | ((v << (10 - e)) & 0x3FFu));
+  const int e = 31 - __builtin_clz(v);  // v = 1.m 2^e
+  const uint32_t m = e <= 10 ? v << (10 - e) : v >> (e - 10);
+  return (uint16_t)(((uint32_t)(e + 15) << 10) | (m & 0x3FFu));
 }
 static int tc_cm_host(int r, int k) { return ((r >> 3) * (TC_K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
@@ -340,6 +343,12 @@ void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs) {
   for (int l = 0; l < 8; ++l)  // the fixed-point sum of y_k / b_k in columns 120 .. 127
     for (int k = 0; k < K; ++k)
       for (int a = 0; a < 7; ++a) B2[tc_cm_host(8 * L + l, 8 * k + a)] = f16_of_int(fix_limb(b[k], a, l));
+  for (int n = 0; n < TC_ROWS; ++n)  // the bias columns: 2^23 added to every accumulator word
+    for (int c = 0; c < 2; ++c) {
+      B1L[tc_cm_host(n, TC_BIAS1[c])] = f16_of_int(2048);
+      B1S[tc_cm_host(n, TC_BIAS1[c])] = f16_of_int(2048);
+      B2[tc_cm_host(n, TC_BIAS2[c])] = f16_of_int(2048);
+    }
   uint64_t* T1 = tabs + TCT_T1;
   uint64_t* T1S = tabs + TCT_T1S;
   uint64_t* T2 = tabs + TCT_T2;
@@ -349,7 +358,7 @@ void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs) {
       T1[v * 16 + k] = (b[k] - h_mulmod((uint64_t)v, Qb, b[k])) % b[k];
       T1S[v * 16 + k] = h_mulmod(T1[v * 16 + k], C.QBinv[k], b[k]);
     }
-  for (int v = 0; v < 17; ++v)
+  for (int v = 0; v <= 2 * K; ++v)
     for (int i = 0; i < 16; ++i) {
       if (i >= L) {
         T2[v * 16 + i] = 0;

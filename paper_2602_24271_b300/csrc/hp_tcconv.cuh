@@ -10,8 +10,11 @@
 // (tcgen05.mma, M = 128 coefficients, N = 128 = 16 primes x 8 limb columns,
 // K = 128 = 16 residues x 8 columns, the eighth zero) then gives, per
 // coefficient and prime, the seven limb sums D_l = sum y^(a) c^(l)
-// < 112 * 255^2 < 2^23: exact in the f32 accumulator.  The value
-// sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime on the CUDA cores.
+// < 112 * 255^2 < 2^23: exact in the f32 accumulator.  Two bias columns
+// (2048 x 2048 each, in K columns the residues leave free) add 2^23 to every
+// accumulator word, so each holds 2^23 + D_l < 2^24 exactly and D_l is its low
+// 23 bits.  The value sum_l D_l 2^(8l) < 2^72 is reduced modulo the prime on
+// the CUDA cores.
 //
 // The eighth column of each prime's block is free, and the centring sums go
 // there: column 8l + 7 (l < 8) of the Q -> B product holds
@@ -78,7 +81,9 @@ HPD void tc_ld64(uint32_t taddr, uint32_t (&r)[64]) {
 // seven 8-bit limbs as f16 and a zero; columns of residues i >= R are zero.
 // Two limbs at a time: a byte permute builds the f16 pair (1024 + u, 1024 + v)
 // (bit patterns 0x64uu, 0x64vv), and one packed subtraction of 1024 leaves
-// the exact f16 values u, v.
+// the exact f16 values u, v.  The bias columns hold 2048 (f16 0x6800): for
+// R = 15 the first two columns of the free slot 15 (columns 120, 121), for
+// R = 16 the eighth columns of residues 0 and 1 (columns 7, 15).
 HPD uint32_t limb_pair(uint32_t w, uint32_t sel) {
   const uint32_t biased = __byte_perm(w, 0x64006400u, sel);
   const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&biased), __float2half2_rn(1024.0f));
@@ -86,6 +91,7 @@ HPD uint32_t limb_pair(uint32_t w, uint32_t sel) {
 }
 template <int R>
 HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
+  static_assert(R == TC_K / 8 - 1 || R == TC_K / 8, "bias columns: a free slot 15 (R = 15) or residues 0, 1 (R = 16)");
 #pragma unroll
   for (int i = 0; i < TC_K / 8; ++i) {
     uint4 v = make_uint4(0, 0, 0, 0);
@@ -95,13 +101,16 @@ HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
       v.y = limb_pair(lo, 0x7352u);  // bytes 2, 3
       v.z = limb_pair(hi, 0x7150u);  // bytes 4, 5
       v.w = limb_pair(hi, 0x7452u);  // byte 6 and 0 (the constant's zero byte)
+      if (R == TC_K / 8 && i < 2) v.w |= 0x68000000u;  // column 8 i + 7: 2048
+    } else if (i == TC_K / 8 - 1) {
+      v.x = 0x68006800u;  // columns 120, 121: 2048
     }
     *(uint4*)(tile + tc_cm(m, 8 * i, TC_K)) = v;
   }
 }
 
-// value of an exact integer below 2^23 held in an f32 accumulator word
-HPD uint32_t acc_int(uint32_t bits) { return __float_as_uint(__uint_as_float(bits) + 8388608.0f) & 0x7FFFFFu; }
+// D < 2^23 from an accumulator word holding the f32 value 2^23 + D (the bias)
+HPD uint32_t acc_int(uint32_t bits) { return bits & 0x7FFFFFu; }
 
 // The fixed-point sum sum_l E_l 2^(8l) (< 2^80) of eight accumulator words
 // holding exact integers E_l < 2^23, as a Fix (64 low bits, the rest above).
@@ -127,16 +136,22 @@ __device__ __noinline__ int lift_v_y_mem(const uint64_t* y, size_t stride, uint3
   return (int)Fhi + greater_than_half(r, 1);
 }
 
-// sum_l D_l 2^(8l) + corr mod p, for the limb sums D_0..D_6 of one prime;
-// c32 = [2^32]_p (Shoup pair).  The low part is < 2^48 < p, the high part
-// times 2^32 reduces to [0, 2p), corr < p: the total is below 4p.
-// r points at the prime's 8 accumulator columns (constant offsets into a register array).
+// sum_l D_l 2^(8l) + corr mod p in [0, 2p), for the limb sums D_0..D_6 of one
+// prime; c32 = [2^32]_p (Shoup pair).  With the 32-bit pairs
+// A = D_0 + 2^8 D_1, B = D_2 + 2^8 D_3, C = D_4 + 2^8 D_5 (each < 2^32, D_l < 2^23)
+// the sum is lo + 2^32 hi, lo = A + 2^16 B < 2^49 < p, hi = C + 2^16 D_6 < 2^40;
+// 2^32 hi reduces to [0, 2p), corr < p: below 4p before the one subtraction
+// of 2p.  r points at the prime's 8 accumulator columns (constant offsets into
+// a register array).
+HPD uint64_t limb_sum_mod2(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t c32, uint64_t c32s) {
+  const uint32_t A = acc_int(r[0]) + (acc_int(r[1]) << 8), B = acc_int(r[2]) + (acc_int(r[3]) << 8),
+                 C = acc_int(r[4]) + (acc_int(r[5]) << 8);
+  const uint64_t lo = (uint64_t)B * 65536u + A, hi = (uint64_t)acc_int(r[6]) * 65536u + C;
+  return csub(lo + mul_shoup_lazy(hi, c32, c32s, p) + corr, 2 * p);
+}
+// the same, reduced to [0, p)
 HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t c32, uint64_t c32s) {
-  const uint64_t lo = (uint64_t)acc_int(r[0]) + ((uint64_t)acc_int(r[1]) << 8) + ((uint64_t)acc_int(r[2]) << 16) +
-                      ((uint64_t)acc_int(r[3]) << 24);
-  const uint64_t hi = (uint64_t)acc_int(r[4]) + ((uint64_t)acc_int(r[5]) << 8) + ((uint64_t)acc_int(r[6]) << 16);
-  const uint64_t x = lo + mul_shoup_lazy(hi, c32, c32s, p) + corr;
-  return csub(csub(x, 2 * p), p);
+  return csub(limb_sum_mod2(r, corr, p, c32, c32s), p);
 }
 
 // Persistent: SRT_GROUPS groups of four warps, each taking tiles of 128
@@ -233,7 +248,10 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
       for (int kk = 0; kk < 4; ++kk) {
         const int k = kb * 4 + kk;
         const uint64_t b = cK.p[L + k];
-        yb[k] = sub_mod(dB[k], limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]), b);
+        // [0, 2p) is enough here: yb only feeds the B -> Q operand (2p < 2^56, seven limbs),
+        // whose sums are congruent and whose centring sum uses the same yb
+        const uint64_t x = limb_sum_mod2(r32 + 8 * kk, T1s[v * 16 + k], b, cK.r32b[k], cK.r32b_s[k]);
+        yb[k] = dB[k] + (dB[k] < x ? 2 * b : 0) - x;
       }
     }
     tc_fence_before();
