@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     uint64_t dB[K];  // [t d Q^{-1} (B/b_k)^{-1}]_{b_k}, loaded while the MMA runs
 #pragma unroll
     for (int k = 0; k < K; ++k) dB[k] = d[(size_t)(L + k) * N];
-    named_sync(1 + g, 128);
+    tc_fence_before();
+    named_sync(1 + g, 128);  // A written; every lane has read the previous tile's D
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
@@ -254,11 +255,10 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
         yb[k] = dB[k] + (dB[k] < x ? 2 * b : 0) - x;
       }
     }
-    tc_fence_before();
-    named_sync(1 + g, 128);  // every lane has read D; the first MMA finished with A
-    put_limb_row<K>(A, m, yb);
+    put_limb_row<K>(A, m, yb);  // the first MMA has finished with A
     fence_async_smem();
-    named_sync(1 + g, 128);
+    tc_fence_before();
+    named_sync(1 + g, 128);  // A written; every lane has read D
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
@@ -325,8 +325,6 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     }
 #pragma unroll
     for (int i = 0; i < L; ++i) o[(size_t)i * N] = out[i];
-    tc_fence_before();
-    named_sync(1 + g, 128);  // D and A free for the next tile
   }
   tc_fence_before();
   __syncthreads();
@@ -419,7 +417,8 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
     put_limb_row<L>(A, m, y);
     fence_async_smem();
     if (tile + stride < ntiles) lift_tile_load<SUBCT>(src, sub, tile + stride, m, logN, xv, sv);
-    named_sync(1 + g, 128);
+    tc_fence_before();
+    named_sync(1 + g, 128);  // A written; every lane has read the previous tile's D
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
@@ -457,8 +456,6 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
         o[(size_t)(L + k) * N] = limb_sum_mod(r32 + 8 * kk, T1s[v * 16 + k], cK.p[L + k], cK.r32b[k], cK.r32b_s[k]);
       }
     }
-    tc_fence_before();
-    named_sync(1 + g, 128);
   }
   tc_fence_before();
   __syncthreads();
