@@ -558,14 +558,17 @@ __global__ void __launch_bounds__(NTT_THREADS, MD ? 7 : 8) k_ntt_inv_cols(uint64
     const uint64_t* uP = data + (bc * NKS + L) * N;
     const uint64_t* wv = md.w3 + (((bc >> 1) * 3 + comp) * L + i) * N;
     uint64_t* o = md.out + (bc * L + i) * N;
+    const uint64_t pinv = cK.Pinv[i], pinv_s = cK.Pinv_s[i];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int n = (rb + u * RB) * C + k0 + k;
-      const uint64_t uiP = csub(csub(x[u], 2 * p), p);  // u_i P^{-1}
       const uint64_t up = uP[n];
       const bool low = up <= (P - 1) / 2;  // [u_P] = up or up - P
-      const uint64_t m = mul_shoup(csub(csub(low ? up : P - up, 2 * p), p), cK.Pinv[i], cK.Pinv_s[i], p);
-      uint64_t r = add_mod(wv[n], low ? sub_mod(uiP, m, p) : add_mod(uiP, m, p), p);
+      // m = |[u_P]| P^{-1} in [0, 4p); x[u] = u_i P^{-1} in [0, 4p), wv < p:
+      // x + wv + (4p - m or m) < 9p, four conditional subtractions to [0, p)
+      const uint64_t m = mul_shoup4(low ? up : P - up, pinv, pinv_s, f);
+      uint64_t r = x[u] + wv[n] + (low ? 4 * p - m : m);
+      r = csub(csub(csub(csub(r, 8 * p), 4 * p), 2 * p), p);
       if (md.one_minus) {
         r = sub_mod(0, r, p);
         if (comp == 0 && n == 0) r = add_mod(r, cK.delta[i], p);
