@@ -149,10 +149,11 @@ HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "
 # G = 3: 5 (13 x 2 + 0 + 1 + 2) = 145; G = 5: 3 (11 x 4 + 0 + 1 + 2 + 3 + 4) = 162
 DIGIT_PRODUCTS_PER_HMULT = {3: 145, 5: 162}
 # key-switching digit grouping per workload (data primes per digit): five-prime
-# digits (3 digits) for the EQ workloads, whose depth-16 chain keeps about 114 bits
-# of noise budget with them at N = 32768; three-prime digits (5) for the others
-# (LT and BETWEEN would not fit with five-prime digits)
-DEFAULT_DIGIT_PRIMES = {"ctct": 5, "const": 5, "batched": 5, "in": 3, "sum": 3, "rotsum": 3, "join": 3, "lt": 3,
+# digits (3 digits) for the workloads built on EQ chains and rotations, whose
+# depth-16 chain keeps about 114 bits of noise budget with them at N = 32768
+# (enough for a product and a reduction after it); three-prime digits (5) for
+# LT and BETWEEN, which would not fit with five-prime digits
+DEFAULT_DIGIT_PRIMES = {"ctct": 5, "const": 5, "batched": 5, "in": 5, "sum": 5, "rotsum": 5, "join": 5, "lt": 3,
                         "between": 3}
 
 
@@ -524,6 +525,11 @@ def run_libhp(args):
         roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
     roof["probe_butterfly_per_s"] = hp.probe_peak(0)
     roof["probe_mac_per_s"] = hp.probe_peak(1)
+    # the same butterfly on 32-bit words (a 30-bit prime), and modulus bits per
+    # second through each: 55-bit primes here against 30-bit ones
+    roof["probe_butterfly32_per_s"] = hp.probe_peak(2)
+    roof["probe_modulus_bits_per_s"] = {"u64_55bit": 55 * roof["probe_butterfly_per_s"],
+                                        "u32_30bit": 30 * roof["probe_butterfly32_per_s"]}
     roof["traffic"] = load_traffic(kernel, ctx_tile(ctx))
     # whole path: the step's algorithmic butterflies (every transform), digit
     # recombination products (counted at the butterfly rate) and key-switching
@@ -536,6 +542,11 @@ def run_libhp(args):
     roof["path_frac"] = t_ideal / (ms_per_step / 1e3)
     roof["path_work_per_step"] = {"butterflies": butterflies, "digit_products": digit_products, "ks_macs": ks_macs,
                                   "ideal_ms": t_ideal * 1e3}
+    # the same ideal against the part of the step outside the two tensor-core
+    # conversion kernels, whose work the ideal leaves out
+    tc = sum(shares.get(hp.PROFILE_CLASSES.index(c), 0.0) for c in ("lift", "scale_round")) / tot if tot else 0.0
+    roof["tc_conversion_share"] = tc
+    roof["path_frac_outside_tc"] = t_ideal / (ms_per_step / 1e3 * (1.0 - tc)) if tc < 1.0 else None
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -113,17 +113,16 @@ HPD void put_limb_row(uint16_t* tile, int m, const uint64_t (&y)[R]) {
 HPD uint32_t acc_int(uint32_t bits) { return bits & 0x7FFFFFu; }
 
 // The fixed-point sum sum_l E_l 2^(8l) (< 2^80) of eight accumulator words
-// holding exact integers E_l < 2^23, as a Fix (64 low bits, the rest above).
+// holding exact integers E_l < 2^23, as a Fix (64 low bits, the rest above):
+// with the 32-bit pairs A = E_0 + 2^8 E_1, B = E_2 + 2^8 E_3, C = E_4 + 2^8 E_5,
+// D = E_6 + 2^8 E_7 it is lo + 2^32 hi, lo = A + 2^16 B, hi = C + 2^16 D.
 HPD Fix fix_from_limbs(const uint32_t* e) {
-  Fix F = {0, 0};
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const uint64_t v = acc_int(e[l]);
-    const uint64_t lo = v << (8 * l);
-    const uint32_t hi = l == 0 ? 0u : (uint32_t)(v >> (64 - 8 * l));
-    F.lo += lo;
-    F.hi += hi + (F.lo < lo ? 1u : 0u);
-  }
+  const uint32_t A = acc_int(e[0]) + (acc_int(e[1]) << 8), B = acc_int(e[2]) + (acc_int(e[3]) << 8),
+                 C = acc_int(e[4]) + (acc_int(e[5]) << 8), D = acc_int(e[6]) + (acc_int(e[7]) << 8);
+  const uint64_t lo = (uint64_t)B * 65536u + A, hi = (uint64_t)D * 65536u + C;  // each < 2^49
+  Fix F;
+  F.lo = lo + (hi << 32);
+  F.hi = (uint32_t)(hi >> 32) + (F.lo < lo ? 1u : 0u);
   return F;
 }
 

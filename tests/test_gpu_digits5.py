@@ -14,7 +14,9 @@ N = 4096:
   tests/golden/make_n4096_budgets.py --digits5 wrote, and BETWEEN gives
   [lo <= x <= hi] in every slot;
 * the allocation-free squaring, which holds three-prime digits only, refuses
-  the handle."""
+  the handle;
+* with per-prime digits up to depth 2 and five-prime digits below, the
+  per-prime key and an EQ chain are bit-exact against the oracle."""
 import hashlib
 
 import numpy as np
@@ -123,3 +125,30 @@ def test_lt_digest_and_between(env):
     assert np.array_equal(ctx.decrypt(lt)[0], (x < y).astype(np.uint32))
     assert _digest(lt[0]) == gold["lt_sha256"]
     assert np.array_equal(ctx.decrypt(bt)[0], ((x >= LO) & (x <= HI)).astype(np.uint32))
+
+
+def test_per_prime_first_levels_with_five_prime_digits():
+    """ks_fine_depth = 2 with five-prime digits below it: the per-prime key and
+    an EQ chain (its first two squarings per-prime, the rest five-prime) are
+    bit-exact against the oracle with the same rule."""
+    import torch
+
+    build.build()
+    ctx = hp.Context(LOGN, max_tile_ct=1, ks_digit_primes=DP, ks_fine_depth=2)
+    ctx.keygen(SEED_KEY)
+    rk_fine = ctx.keygen_fine(SEED_KEY)
+    o = oracle.Oracle(LOGN, dp=DP, fine_depth=2)
+    o.keygen(SEED_KEY)
+    torch.cuda.synchronize()
+    assert np.array_equal(hp.to_u64(rk_fine), o.fine_key())
+    N = ctx.N
+    rng = np.random.default_rng(23)
+    x = rng.integers(0, hp.T, (1, N)).astype(np.uint32)
+    y = np.where(rng.random((1, N)) < 0.5, x, rng.integers(0, hp.T, (1, N))).astype(np.uint32)
+    cx, cy = ctx.encrypt(x, seed=SEED_ENC), ctx.encrypt(y, seed=SEED_ENC, ct_index0=1)
+    eq = ctx.run(hp.HP_EQ_CT_CT, cx, cy)
+    torch.cuda.synchronize()
+    ctx.check_status()
+    assert np.array_equal(ctx.decrypt(eq), (x == y).astype(np.uint32))
+    assert np.array_equal(hp.to_u64(eq[0]), o.eq(hp.to_u64(cx[0]), hp.to_u64(cy[0])))
+    ctx.close()

@@ -96,7 +96,7 @@ def test_const_workload_2_28_slots(big):
     x = rng.integers(0, 1 << 16, n_ct * N, dtype=np.uint32)
     x[rng.random(n_ct * N) < 0.25] = cval
     cx = encrypt_chunked(ctx, x, n_ct, 3, 0)
-    out = ctx.eq(cx, None, const_val=cval, dp=DP)
+    out = ctx.eq(cx, None, const_val=cval)
     ctx.check_status()
     for c0 in range(0, n_ct, 512):
         c1 = min(n_ct, c0 + 512)

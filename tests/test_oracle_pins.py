@@ -353,7 +353,7 @@ def _key_relation_ok(o, rk, groups, s2):
     return True
 
 
-@pytest.mark.parametrize("dp", [1, 2, 3])
+@pytest.mark.parametrize("dp", [1, 2, 3, 5])
 def test_digit_groupings_keys_and_relinearisation_bruteforce(dp):
     """Key switching with digits of dp consecutive data primes (the last group
     shorter when dp does not divide L = 15): the keys satisfy their defining
