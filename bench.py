@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--n-ct", type=int, default=0, help="override the ciphertext count (diagnostics only)")
     ap.add_argument("--ks-digit-primes", type=int, default=0, choices=[0, 3, 5],
                     help="data primes per key-switching digit (0: the workload's default)")
+    ap.add_argument("--ks-fine-depth", type=int, default=-1,
+                    help="depth up to which per-prime digits relinearise (-1: the workload's default)")
+    ap.add_argument("--ks-coarse-from", type=int, default=-1,
+                    help="depth from which the two-digit key relinearises (0: never; -1: the workload's default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched-vs-plain comparison")
@@ -146,19 +150,32 @@ HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "
 # Shoup products of the digit recombination per ciphertext and multiplication, in
 # units of N, for digits of G primes: per digit (15 / G) and target prime (16),
 # G - 1 products, or o for the digit's own prime at offset o:
-# G = 3: 5 (13 x 2 + 0 + 1 + 2) = 145; G = 5: 3 (11 x 4 + 0 + 1 + 2 + 3 + 4) = 162
-DIGIT_PRODUCTS_PER_HMULT = {3: 145, 5: 162}
-# key-switching digit grouping per workload (data primes per digit): five-prime
-# digits (3 digits) for the workloads built on EQ chains and rotations, whose
-# depth-16 chain keeps about 114 bits of noise budget with them at N = 32768
-# (enough for a product and a reduction after it); three-prime digits (5) for
-# LT and BETWEEN, which would not fit with five-prime digits
-DEFAULT_DIGIT_PRIMES = {"ctct": 5, "const": 5, "batched": 5, "in": 5, "sum": 5, "rotsum": 5, "join": 5, "lt": 3,
-                        "between": 3}
+# G = 3: 5 (13 x 2 + 0 + 1 + 2) = 145; G = 5: 3 (11 x 4 + 0 + 1 + 2 + 3 + 4) = 162;
+# the two-digit key (8 and 7 primes): (8 x 7 + 28) + (9 x 6 + 21) = 159
+DIGIT_PRODUCTS_PER_HMULT = {3: 145, 5: 162, 8: 159}
+# key switching per workload: (per-prime digits up to this depth, data primes
+# per digit, depth from which the two-digit key relinearises).  The workloads
+# built on EQ chains and rotations: five-prime digits (3 digits), whose depth-16
+# chain keeps about 114 bits of noise budget with them at N = 32768 (enough for
+# a product and a reduction after it), and the two-digit key from depth 7, where
+# it no longer costs budget.  LT and BETWEEN: per-prime digits for their 8
+# products up to depth 4 (the first levels, where key-switching noise costs
+# budget), five-prime digits for depths 5 .. 9, the two-digit key from depth 10
+DEFAULT_KEY_SWITCHING = {"ctct": (0, 5, 7), "const": (0, 5, 7), "batched": (0, 5, 7), "in": (0, 5, 7),
+                         "sum": (0, 5, 7), "rotsum": (0, 5, 7), "join": (0, 5, 7), "lt": (4, 5, 10),
+                         "between": (4, 5, 10)}
+
+
+def fine_depth(args, op):
+    return DEFAULT_KEY_SWITCHING[op][0] if args.ks_fine_depth < 0 else args.ks_fine_depth
 
 
 def digit_primes(args, op):
-    return args.ks_digit_primes or DEFAULT_DIGIT_PRIMES[op]
+    return args.ks_digit_primes or DEFAULT_KEY_SWITCHING[op][1]
+
+
+def coarse_from(args, op):
+    return DEFAULT_KEY_SWITCHING[op][2] if args.ks_coarse_from < 0 else args.ks_coarse_from
 
 
 KERNEL_SOURCES = {  # files whose text determines a kernel's code
@@ -195,55 +212,92 @@ def load_traffic(kernel: str, tile: int):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
+def _ceil_log2(i: int) -> int:
+    return (i - 1).bit_length()
+
+
+def lt_product_depths():
+    """Multiplicative depths of LT's 511 products (Eq. 4, the depth-optimal
+    baby-step / giant-step schedule): w = z^2 at 1, baby powers w^i at
+    1 + ceil(log2 i), giant powers w^(256 j) at 9 + ceil(log2 j), the giant-step
+    products at 10 + ceil(log2 j), the final product with z at 18."""
+    d = [1] + [1 + _ceil_log2(i) for i in range(2, 256)] + [9] + [9 + _ceil_log2(j) for j in range(2, 129)]
+    return d + [10 + _ceil_log2(j) for j in range(1, 128)] + [18]
+
+
+def product_depths(op: str):
+    """Multiplicative depths of the multiplications one unit of a workload performs."""
+    eq = list(range(1, 17))
+    return {"ctct": eq, "const": eq, "batched": eq, "in": eq, "sum": eq + [17], "join": eq + [17, 17],
+            "rotsum": [], "lt": lt_product_depths(), "between": 2 * lt_product_depths() + [19]}[op]
+
+
 class OracleSample:
     """One ciphertext of the workload (N = 32768) on the CPU oracle, keys and
-    encryptions made once.  `time(n_mul)` times the oracle's primitives on it
-    single-threaded (difference, `n_mul` multiplications with relinearisation,
-    "1 -", and one rotation with key switching where the workload rotates) and
-    composes the time of one unit of the workload from the counts below.  The
-    composition counts the multiplications and rotations the workload performs
-    and the difference and "1 -" of each EQ chain; ciphertext additions, the
-    plaintext products of Extract and LT's inner sums (255 scalar products per
-    giant step) are left out, so for those workloads the rate is an upper bound
-    on the oracle's."""
+    encryptions made once, with the workload's key switching.  `time(n_mul)`
+    times the oracle's primitives on it single-threaded (difference, `n_mul`
+    multiplications with relinearisation by each key the workload uses, "1 -",
+    and one rotation with key switching where the workload rotates) and composes
+    the time of one unit of the workload from the counts below and the depths of
+    its multiplications (product_depths: those at depth coarse_from or more are
+    relinearised with the two-digit key).  The composition counts the
+    multiplications and rotations the workload performs and the difference and
+    "1 -" of each EQ chain; ciphertext additions, the plaintext products of
+    Extract and LT's inner sums (255 scalar products per giant step) are left
+    out, so for those workloads the rate is an upper bound on the oracle's."""
 
-    # per ciphertext (per ciphertext and B row for join): (differences, multiplications,
-    # "1 -", rotations, what is left out)
+    # per ciphertext (per ciphertext and B row for join): (differences, "1 -",
+    # rotations, what is left out)
     COUNTS = {
-        "ctct": (1, 16, 1, 0, ""),
-        "const": (1, 16, 1, 0, ""),
-        "batched": (1, 16, 1, 0, ""),
-        "in": (1, 16, 1, 0, "the additions of the IN sum"),
-        "lt": (1, 511, 0, 0, "the 128 inner sums of 255 scalar products and the additions"),
-        "between": (3, 1023, 2, 0, "the 2 x 128 inner sums of 255 scalar products and the additions"),
-        "sum": (1, 17, 1, 15 / 2048, "the additions"),
-        "rotsum": (0, 0, 0, 15, "the additions"),
-        "join": (1, 18, 1, 45 / 64, "the plaintext products of Extract and the additions"),
+        "ctct": (1, 1, 0, ""),
+        "const": (1, 1, 0, ""),
+        "batched": (1, 1, 0, ""),
+        "in": (1, 1, 0, "the additions of the IN sum"),
+        "lt": (1, 0, 0, "the 128 inner sums of 255 scalar products and the additions"),
+        "between": (3, 2, 0, "the 2 x 128 inner sums of 255 scalar products and the additions"),
+        "sum": (1, 1, 15 / 2048, "the additions"),
+        "rotsum": (0, 0, 15, "the additions"),
+        "join": (1, 1, 45 / 64, "the plaintext products of Extract and the additions"),
     }
 
-    def __init__(self, op: str = "ctct", dp: int = 3):
+    def __init__(self, op: str = "ctct", dp: int = 3, coarse_from: int = 0, fine_depth: int = 0):
         import oracle
         from paper_2602_24271_b300.inputs import eq_pair_columns
 
-        self.op = op
-        self.o = oracle.Oracle(LOGN, dp=dp)
+        self.op, self.coarse_from, self.fine_depth = op, coarse_from, fine_depth
+        self.o = oracle.Oracle(LOGN, dp=dp, coarse_from=coarse_from, fine_depth=fine_depth)
         self.o.keygen(SEED_KEY)
         x, y = eq_pair_columns(self.o.N, seed=SEED_DATA)
         self.cx, self.cy = self.o.encrypt(x, 7, 0), self.o.encrypt(y, 7, 1)
         self.g = None
-        if self.COUNTS[op][3]:
+        if self.COUNTS[op][2]:
             self.g = self.o.galois_elements()[0]
             self.o.galois_keygen(SEED_KEY, self.g)
 
     def time(self, n_mul: int = 1):
         o = self.o
-        n_sub, n_m, n_1m, n_rot, left_out = self.COUNTS[self.op]
-        n_mul = n_mul if n_m else 0  # a workload without multiplications times none
+        n_sub, n_1m, n_rot, left_out = self.COUNTS[self.op]
+        depths = product_depths(self.op)
+        cf, F = self.coarse_from, self.fine_depth
+        n_fine = sum(1 for d in depths if d <= F)
+        n_coarse = sum(1 for d in depths if d > F and cf and d >= cf)
+        n_main = len(depths) - n_fine - n_coarse
+        # (operand depth, count timed, count in the unit) per key: the per-prime
+        # key relinearises a product of fresh operands (F > 0), the main key one
+        # at depth F + 1, the two-digit key one at depth cf
+        keys = [(0, n_mul if n_fine else 0, n_fine), (F, n_mul if n_main else 0, n_main),
+                (cf - 1, n_mul if n_coarse else 0, n_coarse)]
         t0 = time.perf_counter()
         d = o.sub(self.cx, self.cy)
         t1 = time.perf_counter()
-        for _ in range(n_mul):
-            d = o.mul_relin(d, d)
+        t_mults = 0.0
+        for depth_a, n_timed, n_unit in keys:
+            if not n_timed:
+                continue
+            ta = time.perf_counter()
+            for _ in range(n_timed):
+                o.mul_relin(d, d, depth_a=depth_a, depth_b=depth_a)
+            t_mults += n_unit * (time.perf_counter() - ta) / n_timed
         t2 = time.perf_counter()
         o.one_minus(d)
         t3 = time.perf_counter()
@@ -251,24 +305,26 @@ class OracleSample:
         if self.g is not None:
             o.rotate(d, self.g)
             t_rot = time.perf_counter() - t3
-        t_sub, t_mul, t_1m = t1 - t0, (t2 - t1) / max(1, n_mul), t3 - t2
-        per_unit = n_sub * t_sub + n_m * t_mul + n_1m * t_1m + n_rot * t_rot
+        per_unit = n_sub * (t1 - t0) + t_mults + n_1m * (t3 - t2) + n_rot * t_rot
         desc = ("1 ciphertext at N=32768 (32768 slots) on the oracle, single-threaded, key-switching digits of %d "
-                "primes: a difference, %d multiplication(s) with relinearisation, '1 -'%s timed; one unit of the "
-                "workload composed as %d difference(s) + %d multiplications + %d x '1 -'%s%s" % (
-                    o.dp, n_mul, " and one rotation" if self.g is not None else "", n_sub, n_m, n_1m,
+                "primes%s%s: a difference, %d multiplication(s) with relinearisation per key used, '1 -'%s timed; "
+                "one unit of the workload composed as %d difference(s) + %d multiplications (%d with the per-prime "
+                "key, %d with the two-digit key) + %d x '1 -'%s%s" % (
+                    o.dp, ", per-prime digits up to depth %d" % F if F else "",
+                    ", the two-digit key from depth %d" % cf if cf else "", n_mul,
+                    " and one rotation" if self.g is not None else "", n_sub, len(depths), n_fine, n_coarse, n_1m,
                     " + %.3g rotations" % n_rot if n_rot else "",
                     "; not counted: %s (the rate is an upper bound)" % left_out if left_out else ""))
         return o.N / per_unit, time.perf_counter() - t0, desc
 
 
-def _oracle_worker(op, n_mul, barrier, results, dp):
-    sample = OracleSample(op, dp)
+def _oracle_worker(op, n_mul, barrier, results, dp, cf, F):
+    sample = OracleSample(op, dp, cf, F)
     barrier.wait(timeout=120)  # every worker set up: the timed samples run concurrently
     results.put(sample.time(n_mul))
 
 
-def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32, dp: int = 3):
+def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32, dp: int = 3, cf: int = 0, F: int = 0):
     """The paper's multi-threaded form (Sec. 5.3: independent predicates
     assigned to threads): W = min(32, host cores) single-threaded oracle
     processes (about 0.45 GB of host memory each), started with spawn, set up
@@ -284,7 +340,7 @@ def multicore_baseline(op: str, n_mul: int = 1, max_workers: int = 32, dp: int =
     w = max(1, min(max_workers, cores))
     ctx = mp.get_context("spawn")
     barrier, results = ctx.Barrier(w), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(op, n_mul, barrier, results, dp)) for _ in range(w)]
+    procs = [ctx.Process(target=_oracle_worker, args=(op, n_mul, barrier, results, dp, cf, F)) for _ in range(w)]
     for pr in procs:
         pr.start()
     got, deadline = [], time.time() + 300
@@ -312,7 +368,7 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args.config)
-    sample = OracleSample(wl["op"], digit_primes(args, wl["op"]))
+    sample = OracleSample(wl["op"], digit_primes(args, wl["op"]), coarse_from(args, wl["op"]), fine_depth(args, wl["op"]))
     vals, step_ms, desc = [], [], ""
     for i in range(args.warmup + args.steps):
         v, secs, desc = sample.time(1)
@@ -350,7 +406,8 @@ def run_libhp(args):
 
     wl = workload(args.config)
     n_ct = args.n_ct or wl["n_ct"]
-    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, wl["op"]))
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, wl["op"]),
+                     ks_coarse_from=coarse_from(args, wl["op"]), ks_fine_depth=fine_depth(args, wl["op"]))
     ctx.keygen(SEED_KEY)
     if not args.ncu_region:
         ctx.autotune()
@@ -536,7 +593,11 @@ def run_libhp(args):
     # multiply-accumulates at the derived ALU ceilings, against the step time;
     # the base conversions run on the tensor cores and are not counted
     butterflies = sum(works[c] for c in NTT_CLASSES)
-    digit_products = DIGIT_PRODUCTS_PER_HMULT[ctx.ks_digit_primes] * N * n_ct * HMULT_PER_CT[wl["op"]] * wl.get("n_const", 1)
+    cf, F = ctx.ks_coarse_from, ctx.ks_fine_depth
+    # per-prime digits need no recombination products (one conditional subtraction)
+    per_unit = sum(0 if d <= F else DIGIT_PRODUCTS_PER_HMULT[8 if cf and d >= cf else ctx.ks_digit_primes]
+                   for d in product_depths(wl["op"]))
+    digit_products = per_unit * N * n_ct * wl.get("n_const", 1)
     ks_macs = works.get(8, 0.0)
     t_ideal = (butterflies + digit_products) / (mul_rate / MUL_PER_BUTTERFLY) + ks_macs / (mul_rate / MUL_PER_MAC)
     roof["path_frac"] = t_ideal / (ms_per_step / 1e3)
@@ -553,6 +614,7 @@ def run_libhp(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n_ct_per_gpu": n_ct, "slots_per_gpu": n_ct * N,
                        "tile_ct": ctx_tile(ctx), "ks_digit_primes": ctx.ks_digit_primes,
+                       "ks_coarse_from": ctx.ks_coarse_from, "ks_fine_depth": ctx.ks_fine_depth,
                        "l2": "inputs larger than L2 (%.1f GB of ciphertexts read per step)"
                        % (n_ct * 2 * 15 * N * 8 * (2 if cy is not None else 1) / 1e9),
                        "parallelism": "replicas" if world == 1 else "dp%d (independent ciphertexts)" % world},
@@ -576,11 +638,11 @@ def run_libhp(args):
             line["extras"] = extras_measure(ctx, stream)
     # ---- CPU baseline (rank 0, N = 1 only) ----
     if not args.no_cpu and rank == 0 and world == 1:
-        v, secs, desc = OracleSample(wl["op"], ctx.ks_digit_primes).time(8)
+        v, secs, desc = OracleSample(wl["op"], ctx.ks_digit_primes, ctx.ks_coarse_from, ctx.ks_fine_depth).time(4)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": secs}
         try:
-            mc = multicore_baseline(wl["op"], dp=ctx.ks_digit_primes)
+            mc = multicore_baseline(wl["op"], dp=ctx.ks_digit_primes, cf=ctx.ks_coarse_from, F=ctx.ks_fine_depth)
             mc["speedup_over_one_core_sample"] = mc["value"] / v
         except Exception as e:  # the single-core baseline above stands on its own
             mc = {"value": None, "error": str(e)[:200]}
@@ -641,11 +703,13 @@ def extras_measure(ctx, stream):
                       "check": "closed form on ciphertexts 0, 4096, 8191"}
     del x28, o28
     torch.cuda.empty_cache()
-    # LT over 16 ciphertext pairs, closed form on every slot; its depth-18 chain
-    # keeps three-prime key-switching digits
+    # LT over 16 ciphertext pairs, closed form on every slot, with LT's own key
+    # switching (per-prime digits up to depth 4, five-prime digits, the two-digit
+    # key from depth 10)
     lctx = ctx
-    if ctx.ks_digit_primes != 3:
-        lctx = hp.Context(LOGN, max_tile_ct=ctx_tile(ctx), ks_digit_primes=3)
+    if (ctx.ks_fine_depth, ctx.ks_digit_primes, ctx.ks_coarse_from) != DEFAULT_KEY_SWITCHING["lt"]:
+        F, dp, cf = DEFAULT_KEY_SWITCHING["lt"]
+        lctx = hp.Context(LOGN, max_tile_ct=ctx_tile(ctx), ks_digit_primes=dp, ks_coarse_from=cf, ks_fine_depth=F)
         lctx.keygen(SEED_KEY)
     nl = 16
     xl, yl = eq_pair_columns(nl * N, seed=SEED_DATA + 7, value_bits=15)
@@ -657,7 +721,8 @@ def extras_measure(ctx, stream):
     out["lt"] = {"workload": "LT(x, y) (Eq. 4): 16 ciphertext pairs = 2^19 slots, x, y in [0, 2^15], N=32768, "
                  "511 multiplications per ciphertext (depth 18)", "value": nl * N / (ms / 1e3), "unit": UNIT,
                  "ms_per_step": ms, "steps": 1, "warmup": 1, "check": "closed form [x < y] on every slot",
-                 "hmult_per_s": nl * 511 / (ms / 1e3), "ks_digit_primes": lctx.ks_digit_primes}
+                 "hmult_per_s": nl * 511 / (ms / 1e3), "ks_fine_depth": lctx.ks_fine_depth,
+                 "ks_digit_primes": lctx.ks_digit_primes, "ks_coarse_from": lctx.ks_coarse_from}
     del cxl, cyl, ol
     if lctx is not ctx:
         lctx.close()
@@ -809,7 +874,8 @@ def run_batched(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     wl = workload("batched")
-    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, "batched"))
+    ctx = hp.Context(LOGN, max_tile_ct=args.tile, ks_digit_primes=digit_primes(args, "batched"),
+                     ks_coarse_from=coarse_from(args, "batched"), ks_fine_depth=fine_depth(args, "batched"))
     ctx.keygen(SEED_KEY)
     tile = ctx.autotune()
     stream = torch.cuda.current_stream()
@@ -820,7 +886,7 @@ def run_batched(args):
     value = r["packed_batched_elements_per_s"]
     cpu = None
     if not args.no_cpu:
-        v, secs, desc = OracleSample("batched", ctx.ks_digit_primes).time(8)
+        v, secs, desc = OracleSample("batched", ctx.ks_digit_primes, ctx.ks_coarse_from, ctx.ks_fine_depth).time(4)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "cpu_seconds": secs}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["packed_ms_per_pass"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -86,6 +86,13 @@ typedef struct {
                                default, also for 0; D = 5 digits) or 5 (D = 3 digits: 48 instead of
                                80 key-switching transforms per product, for more key-switching noise:
                                EQ then leaves about 114 bits of budget at N = 32768, against 224) */
+  uint32_t ks_coarse_from;  /* products at multiplicative depth >= this are relinearised with a
+                               two-digit key (digits [d2] mod q_0..q_7 and mod q_8..q_14: 32 key-
+                               switching transforms per product).  Its key-switching noise (about
+                               2^400 at N = 32768) costs nothing once the product's own noise is
+                               larger: the oracle measures the same EQ budget with it from depth 7
+                               on (five-prime digits below), 8 bits less from depth 6.  0 = never;
+                               otherwise above ks_fine_depth (HP_ERR_ARG).  See hp_budget_estimate. */
 } hp_params;
 
 /* Operations of hp_run / hp_run_batched. */
@@ -130,6 +137,20 @@ int hp_set_relin_key(hp_handle* h, const uint64_t* relin_key_dev);
  * Both synchronous. */
 int hp_set_relin_key_fine(hp_handle* h, const uint64_t* rk_fine_dev);
 int hp_keygen_fine(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_fine_out, void* stream);
+
+/* The two-digit relinearisation key of a handle created with ks_coarse_from > 0
+ * (HP_ERR_STATE otherwise): digit a = [d2]_{Q_a}, Q_0 = q_0 ... q_7,
+ * Q_1 = q_8 ... q_14, key rk_a = (-(a_a s + e_a) + P g_a s^2, a_a) mod QP with
+ * g_a = (Q/Q_a) [(Q/Q_a)^{-1}]_{Q_a}; layout [2][2][L+1][N] (residues mod
+ * q_0..q_{L-1}, P; coefficient domain).
+ *   hp_set_relin_key_coarse: install a key made elsewhere (device memory);
+ *   hp_keygen_coarse: make it from the secret sk (device int8 [N]) and `seed`
+ *     (Philox counter (k, j, 48 + a, 5) for a_a, (k, 0, 48 + a, 4) for e_a) and
+ *     install it; rk_coarse_out (device, optional) receives it.  hp_keygen
+ *     calls it itself for such handles.
+ * Both synchronous. */
+int hp_set_relin_key_coarse(hp_handle* h, const uint64_t* rk_coarse_dev);
+int hp_keygen_coarse(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_coarse_out, void* stream);
 
 /* Evaluate `op` on n_ct ciphertexts.
  *   HP_EQ_CT_CT    out[i] = EQ(x[i], y[i])
@@ -286,7 +307,7 @@ int hp_join(hp_handle* h, const uint64_t* a_key, size_t n_a, const uint64_t* b_k
  * hp_budget_estimate: a static, conservative estimate of the invariant-noise
  * budget in bits (log2(Q / (2 |v|)); decryption is exact while it is positive)
  * left in the result of `op` for the parameters `params` (log_n, q, P, t,
- * ks_fine_depth; no GPU needed):
+ * ks_fine_depth, ks_digit_primes, ks_coarse_from; no GPU needed):
  *   HP_BUDGET_EQ / _SELECT / _SQUARE / _LT / _BETWEEN   the operation on fresh inputs
  *   HP_BUDGET_PRODUCT      a fresh column times an operand of budget in_bits
  *                          lying at multiplicative depth in_depth (hp_select_mask)
@@ -381,7 +402,9 @@ int hp_check_status(hp_handle* h);
  * (312 words per coefficient for ring degree <= 4096: 10.2 MB, held by every
  * GPU that loads the library until the process exits) instead of the
  * handle's workspace.  It calls no allocation routine.
- *   - ring degree above 4096: HP_ERR_UNSUPPORTED, nothing launched;
+ *   - ring degree above 4096, or a handle with ks_fine_depth > 0,
+ *     ks_digit_primes = 5 or ks_coarse_from > 0 (the array holds three-prime
+ *     key-switching digits only): HP_ERR_UNSUPPORTED, nothing launched;
  *   - ct_in / ct_out: device, [2][L][N], 16-byte aligned; ct_out may alias ct_in;
  *   - the handle's device must be current (HP_ERR_ARG otherwise);
  *   - the first call on a device looks up the array's device address

@@ -55,10 +55,10 @@ def build(force: bool = False) -> str:
 
 
 def build_mutant(k: int, force: bool = False) -> str:
-    """A separate copy of the oracle with planted mistake number k (1..15, listed
+    """A separate copy of the oracle with planted mistake number k (1..16, listed
     at the top of bfv_oracle.cpp), for the tests that check that the pins catch
     such mistakes.  Never loaded by anything but those tests."""
-    if not 1 <= k <= 15:
+    if not 1 <= k <= 16:
         raise ValueError("no planted mistake %d" % k)
     return _compile(os.path.join(_BUILD, "liboracle_mutant%d.so" % k), ["-DORC_MUTANT=%d" % k], force)
 
@@ -121,6 +121,8 @@ def _load(path=None):
         "orc_between": (ctypes.c_int, [V, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p]),
         "orc_set_digits": (ctypes.c_int, [V, ctypes.c_int, ctypes.c_int]),
         "orc_fine_key": (ctypes.c_int, [V, _u64p]),
+        "orc_set_coarse": (ctypes.c_int, [V, ctypes.c_int]),
+        "orc_coarse_key": (ctypes.c_int, [V, _u64p]),
         "orc_mul_relin_depth": (ctypes.c_int, [V, _u64p, ctypes.c_int, _u64p, ctypes.c_int, _u64p]),
     }
     for name, (res, args) in sig.items():
@@ -193,10 +195,12 @@ class Oracle:
     Key switching: the relinearisation and Galois keys have digits of `dp`
     consecutive data primes (3 by default); products whose multiplicative depth
     is at most `fine_depth` are relinearised with a second key of one prime per
-    digit instead (0 = never).  Depths count from fresh ciphertexts (depth 0)."""
+    digit instead (0 = never), and products at depth `coarse_from` or more with a
+    third key of two digits, data primes 0..7 and 8..14 (0 = never).  Depths
+    count from fresh ciphertexts (depth 0)."""
 
     def __init__(self, logn: int, q=None, P=None, t: int = T_DEFAULT, L: int = L_DEFAULT, lib_path=None,
-                 dp: int = 3, fine_depth: int = 0):
+                 dp: int = 3, fine_depth: int = 0, coarse_from: int = 0):
         if q is None:
             q, P = default_primes(L)
         self.lib = _load(lib_path)
@@ -212,7 +216,9 @@ class Oracle:
             raise RuntimeError("orc_create failed")
         if self.lib.orc_set_digits(self.h, dp, fine_depth) != 0:
             raise ValueError("digit grouping must be 1..L data primes and fine_depth >= 0")
-        self.dp, self.fine_depth = dp, fine_depth
+        if self.lib.orc_set_coarse(self.h, coarse_from) != 0:
+            raise ValueError("coarse_from must be 0 or above fine_depth")
+        self.dp, self.fine_depth, self.coarse_from = dp, fine_depth, coarse_from
         self.D = self.lib.orc_num_digits(self.h)
         self.s = None
         self.rk = None
@@ -330,6 +336,14 @@ class Oracle:
         out = np.zeros((self.L, 2, self.L + 1, self.N), dtype=np.uint64)
         if self.lib.orc_fine_key(self.h, _p(out, ctypes.c_uint64)) != 0:
             raise RuntimeError("no per-prime key (fine_depth = 0)")
+        return out
+
+    def coarse_key(self) -> np.ndarray:
+        """The two-digit relinearisation key (uint64 [2][2][L+1][N]) made by keygen()
+        when coarse_from > 0."""
+        out = np.zeros((2, 2, self.L + 1, self.N), dtype=np.uint64)
+        if self.lib.orc_coarse_key(self.h, _p(out, ctypes.c_uint64)) != 0:
+            raise RuntimeError("no two-digit key (coarse_from = 0)")
         return out
 
     def eq(self, x, y=None, const_val: int = 0, squarings: int = 16):

@@ -48,6 +48,7 @@
 //  13 LT's first giant step taken as w^128 instead of w^256
 //  14 the noise budget without the factor 2 of its definition
 //  15 the per-prime relinearisation key used only below the fine depth, not at it
+//  16 the two-digit relinearisation key used from one level after its first depth
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
@@ -536,6 +537,12 @@ struct KsKey {
 // matters only while the product's own noise is still small, i.e. at the first
 // levels of a chain.
 enum { DIGIT_PRIMES_DEFAULT = 3, FINE_OBJ = 16 };  // fine key digits draw with object index 16 + i
+// Products whose output lies at depth >= c.coarse_from (0 = never) are
+// relinearised with a third key of two digits, the data primes 0..7 and 8..14:
+// its key-switching noise |digit| sqrt(N) / P (|digit| < 2^440) is far above the
+// other keys', which matters only while it is not below the product's own noise,
+// i.e. it costs nothing once a chain is deep enough.
+enum { COARSE_DIGIT_PRIMES = 8, COARSE_OBJ = 48 };  // coarse key digits draw with object index 48 + a
 
 struct Ctx {
   int logn, N, L;
@@ -552,9 +559,11 @@ struct Ctx {
   // relinearisation and Galois keys; products at output depth <= fine_depth
   // use the per-prime relinearisation key rk1
   int dp = DIGIT_PRIMES_DEFAULT, fine_depth = 0;
+  // products at output depth >= coarse_from (0 = never) use the two-digit key rk2
+  int coarse_from = 0;
   // relinearisation keys and Galois keys (switching from s^2, resp. tau_g(s), to s)
-  bool have_rk = false, have_rk1 = false;
-  KsKey rk, rk1;
+  bool have_rk = false, have_rk1 = false, have_rk2 = false;
+  KsKey rk, rk1, rk2;
   std::map<uint64_t, KsKey> gk;   // by Galois element g
   std::vector<uint32_t> lt_h;     // LT polynomial's odd coefficients (computed on first use)
 };
@@ -829,7 +838,8 @@ static Ct key_switch(const Ctx& c, const KsKey& K, const Poly& d0, const Poly& d
 }
 
 // Relinearisation of a product at multiplicative depth `depth`: the per-prime
-// key when depth <= fine_depth, else the key of dp-prime digits.
+// key when depth <= fine_depth, the two-digit key when depth >= coarse_from
+// (coarse_from > 0), else the key of dp-prime digits.
 static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& d2, int depth) {
   if (!c.have_rk) fail("relinearisation key not set");
 #if ORC_MUTANT == 15
@@ -839,6 +849,14 @@ static Ct relinearize(const Ctx& c, const Poly& d0, const Poly& d1, const Poly& 
 #endif
     if (!c.have_rk1) fail("per-prime relinearisation key not set");
     return key_switch(c, c.rk1, d0, d1, d2);
+  }
+#if ORC_MUTANT == 16
+  if (c.coarse_from > 0 && depth > c.coarse_from) {
+#else
+  if (c.coarse_from > 0 && depth >= c.coarse_from) {
+#endif
+    if (!c.have_rk2) fail("two-digit relinearisation key not set");
+    return key_switch(c, c.rk2, d0, d1, d2);
   }
   return key_switch(c, c.rk, d0, d1, d2);
 }
@@ -1078,7 +1096,18 @@ int orc_set_digits(void* h, int dp, int fine_depth) {
   if (dp < 1 || dp > c->L || fine_depth < 0) return -1;
   c->dp = dp;
   c->fine_depth = fine_depth;
-  c->have_rk = c->have_rk1 = false;
+  c->have_rk = c->have_rk1 = c->have_rk2 = false;
+  c->gk.clear();
+  return 0;
+}
+
+// The depth from which products are relinearised with the two-digit key (before
+// orc_keygen; 0 = never; above the fine depth when both are set).
+int orc_set_coarse(void* h, int coarse_from) {
+  Ctx* c = (Ctx*)h;
+  if (coarse_from < 0 || (coarse_from > 0 && coarse_from <= c->fine_depth)) return -1;
+  c->coarse_from = coarse_from;
+  c->have_rk = c->have_rk1 = c->have_rk2 = false;
   c->gk.clear();
   return 0;
 }
@@ -1162,6 +1191,10 @@ int orc_keygen(void* h, uint64_t seed, int8_t* s_out, uint64_t* rk_out) {
     make_ks_key(c, seed, s, s2, DOM_A_RK, DOM_E_RK, FINE_OBJ, 1, c.rk1, nullptr);
     c.have_rk1 = true;
   }
+  if (c.coarse_from > 0) {
+    make_ks_key(c, seed, s, s2, DOM_A_RK, DOM_E_RK, COARSE_OBJ, COARSE_DIGIT_PRIMES, c.rk2, nullptr);
+    c.have_rk2 = true;
+  }
   return 0;
 }
 
@@ -1175,6 +1208,22 @@ int orc_fine_key(void* h, uint64_t* out) {
       for (int j = 0; j <= c.L; ++j)
         for (int k = 0; k < c.N; ++k) {
           const Big& v = comp ? c.rk1.k1[a][k] : c.rk1.k0[a][k];
+          out[((((size_t)a * 2 + comp) * (c.L + 1)) + j) * c.N + k] = big_mod_u64(v, c.qp[j]);
+        }
+  return 0;
+}
+
+// The two-digit relinearisation key made by orc_keygen when coarse_from > 0:
+// uint64 [2][2][L+1][N] (digits [d2] mod q_0..q_7 and mod q_8..q_14, drawn with
+// object index 48 + a).
+int orc_coarse_key(void* h, uint64_t* out) {
+  Ctx& c = *(Ctx*)h;
+  if (!c.have_rk2) return -2;
+  for (int a = 0; a < c.rk2.D; ++a)
+    for (int comp = 0; comp < 2; ++comp)
+      for (int j = 0; j <= c.L; ++j)
+        for (int k = 0; k < c.N; ++k) {
+          const Big& v = comp ? c.rk2.k1[a][k] : c.rk2.k0[a][k];
           out[((((size_t)a * 2 + comp) * (c.L + 1)) + j) * c.N + k] = big_mod_u64(v, c.qp[j]);
         }
   return 0;

@@ -23,11 +23,11 @@ import numpy as np
 _worker_oracle = None
 
 
-def _init(logn: int, key_seed: int, dp: int) -> None:
+def _init(logn: int, key_seed: int, dp: int, coarse_from: int) -> None:
     global _worker_oracle
     from oracle import Oracle
 
-    _worker_oracle = Oracle(logn, dp=dp)
+    _worker_oracle = Oracle(logn, dp=dp, coarse_from=coarse_from)
     _worker_oracle.keygen(key_seed)
 
 
@@ -44,11 +44,13 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def eq_many(logn: int, key_seed: int, xs, ys=None, const_val: int = 0, workers: int | None = None, dp: int = 3):
+def eq_many(logn: int, key_seed: int, xs, ys=None, const_val: int = 0, workers: int | None = None, dp: int = 3,
+            coarse_from: int = 0):
     """The oracle's EQ (Eq. 3: 1 - (x - y)^(p-1), or against the constant
     ``const_val`` when ``ys`` is None) of each ciphertext ``xs[i]`` (uint64
     [2][L][N]), with the default parameters at ring degree 2^logn, key-switching
-    digits of ``dp`` primes and the keys of ``keygen(key_seed)``.  Returns the list of result ciphertexts, in the
+    digits of ``dp`` primes (the two-digit key from depth ``coarse_from`` on, 0 =
+    never) and the keys of ``keygen(key_seed)``.  Returns the list of result ciphertexts, in the
     order of ``xs``.  ``workers`` defaults to min(len(xs), host cores)."""
     n = len(xs)
     if ys is not None and len(ys) != n:
@@ -60,5 +62,5 @@ def eq_many(logn: int, key_seed: int, xs, ys=None, const_val: int = 0, workers: 
             for i in range(n)]
     workers = max(1, min(n, workers or host_cores()))
     with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
-                             initializer=_init, initargs=(logn, key_seed, dp)) as ex:
+                             initializer=_init, initargs=(logn, key_seed, dp, coarse_from)) as ex:
         return list(ex.map(_eq_one, jobs))

@@ -30,6 +30,13 @@ static_assert(L % DIGIT_PRIMES5 == 0, "digits are whole groups of data primes");
 // object index FINE_OBJ + i.
 constexpr int NDIG_FINE = L;
 constexpr uint32_t FINE_OBJ = 16;
+// The two-digit relinearisation key (digits [d]_{q_0 ... q_7} and
+// [d]_{q_8 ... q_14}) used for products at output depth >= the handle's
+// ks_coarse_from (0 = never); its digits draw Philox with object index
+// COARSE_OBJ + a.  Digit a covers data primes 8a .. min(L, 8a + 8) - 1.
+constexpr int COARSE_DIGIT_PRIMES = 8, NDIG2 = 2;
+constexpr uint32_t COARSE_OBJ = 48;
+static_assert(L > COARSE_DIGIT_PRIMES && L <= NDIG2 * COARSE_DIGIT_PRIMES, "two digits, the second shorter");
 constexpr int LOGN_MIN = 12, LOGN_MAX = 15;
 
 // Constants for the exact RNS base conversions, relinearisation and the
@@ -74,6 +81,8 @@ struct Consts {
   // their recombination modulo a target prime p_j uses [q_ga ... q_ga+m-1]_{p_j}:
   uint64_t digm3[2][NDIG][NKS], digm3_s[2][NDIG][NKS];    // g = 3, m = 1, 2 (index m - 1)
   uint64_t digm5[4][NDIG5][NKS], digm5_s[4][NDIG5][NKS];  // g = 5, m = 1 .. 4
+  uint64_t digm8[COARSE_DIGIT_PRIMES - 1][NDIG2][NKS];    // the two-digit key's groups, m = 1 .. 7 (6 for the second)
+  uint64_t digm8_s[COARSE_DIGIT_PRIMES - 1][NDIG2][NKS];
   uint64_t r32b[K], r32b_s[K];                  // [2^32]_{b_k}
 };
 
@@ -141,7 +150,7 @@ int supported_depth(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t
 enum { BUDGET_EQ = 0, BUDGET_SELECT = 1, BUDGET_SQUARE = 2, BUDGET_LT = 3, BUDGET_BETWEEN = 4, BUDGET_PRODUCT = 5,
        BUDGET_ROTATE_SUM = 6 };
 constexpr double BUDGET_MARGIN = 10.0;
-double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth, int op,
-                       int in_depth, double in_bits);
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth,
+                       int coarse_from, int op, int in_depth, double in_bits);
 
 }  // namespace hp

@@ -27,6 +27,15 @@ HPD uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t p) {
 HPD uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t wp, uint64_t p) {
   return csub(mul_shoup_lazy(a, w, wp, p), p);
 }
+// The same product with the quotient from three 32-bit partial products
+// (ah wh + hi(ah wl) + hi(al wh), the low partial product and two carries
+// dropped: at most 2 below floor(a wp / 2^64)), so the result lies in [0, 4p)
+// for any a < 2^64.
+HPD uint64_t mul_shoup_q3(uint64_t a, uint64_t w, uint64_t wp, uint64_t p) {
+  const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32), wl = (uint32_t)wp, wh = (uint32_t)(wp >> 32);
+  const uint64_t q = (uint64_t)ah * wh + __umulhi(ah, wl) + __umulhi(al, wh);
+  return a * w - q * p;
+}
 
 // 128-bit accumulator for lazy multiply-accumulate
 struct Acc {

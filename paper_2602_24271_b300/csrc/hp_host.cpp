@@ -236,6 +236,15 @@ int build_consts(const uint64_t* q, uint64_t P, uint64_t t, Consts* C, char* err
         C->digm5_s[m - 1][a][j] = h_shoup(c, pj);
       }
     }
+    for (int a = 0; a < NDIG2; ++a) {
+      uint64_t c = 1;
+      const int base = COARSE_DIGIT_PRIMES * a, g = std::min(COARSE_DIGIT_PRIMES, L - base);
+      for (int m = 1; m < COARSE_DIGIT_PRIMES; ++m) {
+        if (m < g) c = h_mulmod(c, q[base + m - 1] % pj, pj);
+        C->digm8[m - 1][a][j] = m < g ? c : 0;
+        C->digm8_s[m - 1][a][j] = m < g ? h_shoup(c, pj) : 0;
+      }
+    }
   }
   C->negQt = to_mont((t - Qt) % t, t);
   // 28-bit limb splits of the conversion matrices (device multiply-accumulate)
@@ -378,55 +387,62 @@ void build_tc_tables(const Consts& C, uint16_t* ops, uint64_t* tabs) {
 //                  (log Q - log t) - (log |digit| + log N / 2 + 6 - log P)
 // B(d) = min(B(d-1) - per level, key-switching bound of the key used at depth d):
 // the three-prime key's bound (about 686 bits at N = 32768; the five-prime
-// key's about 576) is what costs the first levels' budget when they use it;
-// the per-prime key's lies above the fresh budget.  Every constant sits on the conservative side of the oracle's
+// key's about 576, the two-digit key's about 410) is what costs budget when a
+// level uses it while the product's own budget is still above it; the
+// per-prime key's lies above the fresh budget.  Every constant sits on the conservative side of the oracle's
 // measured budgets (per level 27.6 bits measured at N = 4096, 30.3 at N = 32768).
 struct NoiseModel {
-  double fresh, per_level, ks3, ks1;  // ks3: the cap of the handle's main grouping (3 or 5 primes)
+  double fresh, per_level, ks3, ks1, ks8;  // ks3: the cap of the handle's main grouping (3 or 5 primes)
+  int fine_depth, coarse_from;
+  // the cap of the key that relinearises a product at depth d
+  double cap(int d) const { return d <= fine_depth ? ks1 : (coarse_from > 0 && d >= coarse_from ? ks8 : ks3); }
 };
-static NoiseModel noise_model(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp) {
-  double lq = 0, l3 = 0, l1 = 0;
-  for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
+// the largest digit, in bits, of digits of dp consecutive data primes
+static double digit_bits(const uint64_t* q, int nq, int dp) {
+  double best = 0;
   for (int a = 0; a * dp < nq; ++a) {
     double g = 0;
     for (int i = a * dp; i < nq && i < (a + 1) * dp; ++i) g += log2((double)q[i]);
-    l3 = l3 > g ? l3 : g;
+    best = best > g ? best : g;
   }
-  for (int i = 0; i < nq; ++i) l1 = l1 > log2((double)q[i]) ? l1 : log2((double)q[i]);
+  return best;
+}
+static NoiseModel noise_model(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth,
+                              int coarse_from) {
+  double lq = 0;
+  for (int i = 0; i < nq; ++i) lq += log2((double)q[i]);
   const double lt = log2((double)t), lp = log2((double)P);
+  auto ks_cap = [&](int g) { return (lq - lt) - (digit_bits(q, nq, g) + 0.5 * log_n + 6.0 - lp); };
   NoiseModel m;
   m.fresh = lq - lt - log_n - 8.0;
   m.per_level = lt + log_n + 1.0;
-  m.ks3 = (lq - lt) - (l3 + 0.5 * log_n + 6.0 - lp);
-  m.ks1 = (lq - lt) - (l1 + 0.5 * log_n + 6.0 - lp);
+  m.ks3 = ks_cap(dp);
+  m.ks1 = ks_cap(1);
+  m.ks8 = ks_cap(COARSE_DIGIT_PRIMES);
+  m.fine_depth = fine_depth;
+  m.coarse_from = coarse_from;
   return m;
 }
 // budget after a chain of products whose d-th lies at depth d (d = 1 .. depth)
-static double chain_budget(const NoiseModel& m, int depth, int fine_depth) {
+static double chain_budget(const NoiseModel& m, int depth) {
   double b = m.fresh;
-  for (int d = 1; d <= depth; ++d) {
-    const double floor_d = d <= fine_depth ? m.ks1 : m.ks3;
-    b = std::min(b - m.per_level, floor_d);
-  }
+  for (int d = 1; d <= depth; ++d) b = std::min(b - m.per_level, m.cap(d));
   return b;
 }
 
-double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth, int op,
-                       int in_depth, double in_bits) {
-  const NoiseModel m = noise_model(log_n, q, nq, P, t, dp);
+double budget_estimate(int log_n, const uint64_t* q, int nq, uint64_t P, uint64_t t, int dp, int fine_depth,
+                       int coarse_from, int op, int in_depth, double in_bits) {
+  const NoiseModel m = noise_model(log_n, q, nq, P, t, dp, fine_depth, coarse_from);
   // a product of a fresh operand with one of budget `bits` lying at depth `d`
-  auto product = [&](double bits, int d) {
-    const double floor_d = d <= fine_depth ? m.ks1 : m.ks3;
-    return std::min(std::min(bits, m.fresh) - m.per_level, floor_d);
-  };
+  auto product = [&](double bits, int d) { return std::min(std::min(bits, m.fresh) - m.per_level, m.cap(d)); };
   // LT: the giant-step sum adds 128 products of depth <= 17 (7 bits), the
   // scalar combinations before them scale the baby-step noise by < 2^24, which
   // stays below the giant powers' (at least 7 levels deeper)
-  const double lt = chain_budget(m, 18, fine_depth) - 8.0;
+  const double lt = chain_budget(m, 18) - 8.0;
   switch (op) {
-    case BUDGET_EQ: return chain_budget(m, 16, fine_depth);
-    case BUDGET_SELECT: return product(chain_budget(m, 16, fine_depth), 17);
-    case BUDGET_SQUARE: return chain_budget(m, 1, fine_depth);
+    case BUDGET_EQ: return chain_budget(m, 16);
+    case BUDGET_SELECT: return product(chain_budget(m, 16), 17);
+    case BUDGET_SQUARE: return chain_budget(m, 1);
     case BUDGET_LT: return lt;
     case BUDGET_BETWEEN: return product(lt, 19) - 1.0;  // two LT results, each at budget lt
     case BUDGET_PRODUCT: return product(in_bits, in_depth + 1);

@@ -70,12 +70,13 @@ enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3
 // j.  A digit of G = dp primes (3 or 5) is stored in mixed radix as
 // (t_0, ..., t_{G-1}) in w3[b][2][Gg .. Gg+G-1] and recombined as
 // t_0 + sum_{m >= 1} [q_Gg ... q_Gg+m-1]_{p_j} t_m mod p_j (the terms whose
-// constant contains p_j itself vanish); a per-prime digit (dp = 1) is the
+// constant contains p_j itself vanish); the two-digit key's digits are the
+// same with G = 8 for data primes 0..7 and G = 7 for 8..14; a per-prime digit (dp = 1) is the
 // residue w3[b][2][g] < q_g, which one conditional subtraction reduces modulo
 // any target (q_g < 2 p_j).
 struct DigitSrc {
   const uint64_t* w3;  // nullptr: the pass transforms `data` in place
-  int dp;              // data primes per digit: 1, 3 or 5
+  int dp;              // data primes per digit: 1, 3, 5 or COARSE_DIGIT_PRIMES (the two-digit key)
 };
 
 // ---- modular helpers for the transform ------------------------------------------
@@ -156,6 +157,39 @@ HPD void load_digit(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly
   if constexpr (G > 3) {
     if (nt == 2) return digit_terms<2, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
     if (nt == 3) return digit_terms<3, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+  }
+}
+
+// Polynomial (b, a, j) of a key-switching batch of the two-digit key: digit a
+// (data primes 8a .. 8a + 7, the second digit one prime shorter) of ciphertext
+// b reduced modulo target prime j, as load_digit.
+template <int LOGR, int LOGC>
+HPD void load_digit2(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly, int rb, int col, const PForm& f) {
+  constexpr int N = 1 << (LOGR + LOGC), C = 1 << LOGC, RB = 1 << (LOGR - 4), G = COARSE_DIGIT_PRIMES;
+  const int b = poly / (NDIG2 * NKS), a = (poly / NKS) % NDIG2, j = poly % NKS;
+  const int base = G * a, g = a == 0 ? G : L - G;  // primes in this digit
+  const uint64_t* src = w3 + ((size_t)(b * 3 + 2) * L + base) * N;
+  const int o = j - base;
+  if (o == 0) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + col];
+    return;
+  }
+  uint64_t c[G - 1], cs[G - 1];
+#pragma unroll
+  for (int m = 1; m < G; ++m) {
+    c[m - 1] = cK.digm8[m - 1][a][j];
+    cs[m - 1] = cK.digm8_s[m - 1][a][j];
+  }
+  const int nt = (o > 0 && o < g) ? o : g - 1;
+  switch (nt) {
+    case 1: return digit_terms<1, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    case 2: return digit_terms<2, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    case 3: return digit_terms<3, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    case 4: return digit_terms<4, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    case 5: return digit_terms<5, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    case 6: return digit_terms<6, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
+    default: return digit_terms<7, G, LOGR, LOGC>(x, src, rb, col, c, cs, f);
   }
 }
 
@@ -291,9 +325,10 @@ HPD void inv_block_scaled(uint64_t (&x)[1 << A], uint32_t base, int logN, const 
 // Block: COLS = 2048 / R adjacent columns.  Step A: thread (k, rb) holds rows
 // rb + 16-stride (stages 0..3); step B: groups of 2^(LOGR-4) consecutive rows.
 // DG selects the input: 0 the polynomials of `data` (in place), 1, 3 or 5 a
-// key-switching batch built from dig.w3 in digits of that many data primes.
+// key-switching batch built from dig.w3 in digits of that many data primes,
+// COARSE_DIGIT_PRIMES the two-digit key's batch.
 template <int LOGR, int LOGC, int DG>
-__global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
+__global__ void __launch_bounds__(NTT_THREADS, DG == COARSE_DIGIT_PRIMES ? 6 : 7) k_ntt_fwd_cols(uint64_t* __restrict__ data, PolyMap map, NttTabs T,
                                                                  DigitSrc dig) {
   constexpr int logN = LOGR + LOGC, N = 1 << logN, C = 1 << LOGC;
   constexpr int COLS = NTT_TILE >> LOGR, A2 = LOGR - 4, RB = 1 << (LOGR - 4);
@@ -311,6 +346,8 @@ __global__ void __launch_bounds__(NTT_THREADS, 7) k_ntt_fwd_cols(uint64_t* __res
     const uint64_t* src = dig.w3 + ((size_t)(b * 3 + 2) * L + g) * N;
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = csub(src[(size_t)(rb + u * RB) * C + k0 + k], p);
+  } else if constexpr (DG == COARSE_DIGIT_PRIMES) {  // the two-digit key: poly = (b * NDIG2 + a) * NKS + j
+    load_digit2<LOGR, LOGC>(x, dig.w3, poly, rb, k0 + k, f);
   } else if constexpr (DG > 1) {  // digits of DG primes: poly = (b * (L / DG) + g) * NKS + j
     load_digit<DG, LOGR, LOGC>(x, dig.w3, poly, rb, k0 + k, f);
   } else {

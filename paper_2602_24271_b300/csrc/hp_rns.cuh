@@ -118,8 +118,11 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_gen(const uint64_t* __res
 // q_{base+m} (m < G): the digit [d]_{q_base ... q_base+G-1} = t_0 + q_base t_1 +
 // q_base q_base+1 t_2 + ... is kept as its mixed-radix form (t_0, ..., t_{G-1}),
 // t_0 = r_0 and t_m = (((r_m - t_0) q_base^{-1} - t_1) q_base+1^{-1} - ...) q_base+m-1^{-1}
-// mod q_base+m (Garner).  Data primes lie within a factor 2 of each other, so one
-// conditional subtraction reduces a residue of one prime modulo another.
+// mod q_base+m (Garner).  Data primes lie within a factor 2 of each other, so a
+// canonical t_k < q_k < 2 q_m: each step takes v + 2 q_m - t_k (positive, below
+// 6 q_m for v < 4 q_m) times the inverse with the three-partial-product Shoup
+// quotient (result in [0, 4 q_m)); two conditional subtractions make t_m
+// canonical at the end.
 template <int G>
 HPD void digit_mixed_radix(uint64_t (&r)[G], int base) {
 #pragma unroll
@@ -129,8 +132,8 @@ HPD void digit_mixed_radix(uint64_t (&r)[G], int base) {
     uint64_t v = r[m];
 #pragma unroll
     for (int k = 0; k < m; ++k)
-      v = mul_shoup(sub_mod(v, csub(r[k], qm), qm), cK.mrc_inv[base + k][im], cK.mrc_inv_s[base + k][im], qm);
-    r[m] = v;
+      v = mul_shoup_q3(v + 2 * qm - r[k], cK.mrc_inv[base + k][im], cK.mrc_inv_s[base + k][im], qm);
+    r[m] = csub(csub(v, 2 * qm), qm);
   }
 }
 

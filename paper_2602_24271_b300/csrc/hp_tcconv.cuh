@@ -157,8 +157,9 @@ HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t
 // consecutive coefficients (one per thread) of the nct x 3 coefficient
 // polynomials.  ops / tabs: the operand and correction tables of
 // build_tc_tables (B1S, B2; T1S, T2).  d2 is written as key-switching digits
-// of dp primes in mixed radix (dp = 3 or 5), or as plain residues (dp = 1: the
-// per-prime digits).
+// of dp primes in mixed radix (dp = 3 or 5; COARSE_DIGIT_PRIMES: the two-digit
+// key's digits of 8 and 7 primes), or as plain residues (dp = 1: the per-prime
+// digits).
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_scale_round_tc(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3, int* __restrict__ status,
                      const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int dp) {
@@ -311,6 +312,18 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
 #pragma unroll
         for (int e = 1; e < DIGIT_PRIMES; ++e) out[DIGIT_PRIMES * gq + e] = r3[e];
       }
+    } else if ((bj % 3) == 2 && dp == COARSE_DIGIT_PRIMES) {  // d2 as the two-digit key's digits (8 + 7 primes)
+      uint64_t r8[COARSE_DIGIT_PRIMES], r7[L - COARSE_DIGIT_PRIMES];
+#pragma unroll
+      for (int e = 0; e < COARSE_DIGIT_PRIMES; ++e) r8[e] = out[e];
+#pragma unroll
+      for (int e = 0; e < L - COARSE_DIGIT_PRIMES; ++e) r7[e] = out[COARSE_DIGIT_PRIMES + e];
+      digit_mixed_radix<COARSE_DIGIT_PRIMES>(r8, 0);
+      digit_mixed_radix<L - COARSE_DIGIT_PRIMES>(r7, COARSE_DIGIT_PRIMES);
+#pragma unroll
+      for (int e = 1; e < COARSE_DIGIT_PRIMES; ++e) out[e] = r8[e];
+#pragma unroll
+      for (int e = 1; e < L - COARSE_DIGIT_PRIMES; ++e) out[COARSE_DIGIT_PRIMES + e] = r7[e];
     } else if ((bj % 3) == 2 && dp == DIGIT_PRIMES5) {  // d2 as five-prime key-switching digits
 #pragma unroll
       for (int gq = 0; gq < NDIG5; ++gq) {

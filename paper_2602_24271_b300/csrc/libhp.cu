@@ -45,6 +45,11 @@ struct hp_handle {
   uint32_t fine_depth = 0;
   uint64_t* rkm1 = nullptr;
   bool have_rk1 = false;
+  // products at output depth >= coarse_from (> 0) are relinearised with the
+  // two-digit key rkm2 ([NDIG2][2][NKS][N], same form), allocated when set
+  uint32_t coarse_from = 0;
+  uint64_t* rkm2 = nullptr;
+  bool have_rk2 = false;
   // workspace for one pipeline tile of `tile` ciphertexts
   size_t tile = 0;
   uint64_t *ext = nullptr, *ext2 = nullptr, *dprod = nullptr, *w3 = nullptr, *ksin = nullptr, *ksout = nullptr,
@@ -203,6 +208,8 @@ static void ntt_fwd_t(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, Dig
       k_ntt_fwd_cols<LR, LC, 1><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
     else if (dig.dp == DIGIT_PRIMES5)
       k_ntt_fwd_cols<LR, LC, DIGIT_PRIMES5><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
+    else if (dig.dp == COARSE_DIGIT_PRIMES)
+      k_ntt_fwd_cols<LR, LC, COARSE_DIGIT_PRIMES><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
     else
       k_ntt_fwd_cols<LR, LC, DIGIT_PRIMES><<<gc, NTT_THREADS, 0, s>>>(data, m, tabs(h), dig);
   }
@@ -324,7 +331,7 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
 // product lies at multiplicative depth `depth`, which selects the key:
 // per-prime digits up to the handle's fine depth, three-prime digits below it
 // ---------------------------------------------------------------------------
-// The key-switching multiply-accumulate for keys of nd digits (3, 5 or 15).
+// The key-switching multiply-accumulate for keys of nd digits (2, 3, 5 or 15).
 static void ks_mac(hp_handle* h, const uint64_t* rk, int nd, int b, cudaStream_t s) {
   const unsigned grid = ew_blocks((size_t)NKS * h->N);
   ProfScope ps(h, PK_KS_MAC, s, 2.0 * b * nd * NKS * h->N);
@@ -332,6 +339,8 @@ static void ks_mac(hp_handle* h, const uint64_t* rk, int nd, int b, cudaStream_t
     k_ks_mac<NDIG_FINE><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
   else if (nd == NDIG5)
     k_ks_mac<NDIG5><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
+  else if (nd == NDIG2)
+    k_ks_mac<NDIG2><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
   else
     k_ks_mac<NDIG><<<grid, EW_THREADS, 0, s>>>(h->ksin, rk, h->ksout, h->logn, b);
   h->launches += 1;
@@ -341,7 +350,9 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
                            int depth) {
   const int N = h->N, logN = h->logn;
   const bool fine = depth <= (int)h->fine_depth;
-  const int nd = fine ? NDIG_FINE : h->nd, dp = fine ? 1 : h->dp;
+  const bool coarse = !fine && h->coarse_from > 0 && depth >= (int)h->coarse_from;
+  const int nd = fine ? NDIG_FINE : (coarse ? NDIG2 : h->nd), dp = fine ? 1 : (coarse ? COARSE_DIGIT_PRIMES : h->dp);
+  const uint64_t* rk = fine ? h->rkm1 : (coarse ? h->rkm2 : h->rkm);
   if (general) {  // SELECT: general product
     ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
@@ -364,7 +375,7 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
   // target prime p_j in the first transform pass, key multiply-accumulate,
   // inverse transform, mod-down
   ntt_fwd(h, h->ksin, (size_t)b * nd * NKS, MAP_KS, s, h->w3, dp);
-  ks_mac(h, fine ? h->rkm1 : h->rkm, nd, b, s);
+  ks_mac(h, rk, nd, b, s);
   ntt_inv_moddown(h, h->ksout, b, out, one_minus, s);
 }
 
@@ -689,7 +700,7 @@ static void free_all(hp_handle* h) {
     if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
   }
-  void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->rkm1, h->ext, h->ext2, h->dprod, h->w3,
+  void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->rkm1, h->rkm2, h->ext, h->ext2, h->dprod, h->w3,
                   h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
                   h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef, h->gkm, h->tct, h->tctab};
   for (void* p : ptrs)
@@ -737,6 +748,12 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   }
   h->dp = prm->ks_digit_primes ? (int)prm->ks_digit_primes : DIGIT_PRIMES;
   h->nd = L / h->dp;
+  if (prm->ks_coarse_from != 0 && prm->ks_coarse_from <= prm->ks_fine_depth) {
+    g_create_err = "ks_coarse_from must be 0 or above ks_fine_depth";
+    delete h;
+    return HP_ERR_ARG;
+  }
+  h->coarse_from = prm->ks_coarse_from;
   char eb[256] = {0};
   int rc = build_consts(h->q, h->P, h->t, &h->C, eb, sizeof(eb));
   if (rc != 0) {
@@ -782,7 +799,8 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
                 {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
                 {&h->stx2, T * 2 * L * N},   {&h->sty2, T * 2 * L * N},   {&h->sto2, T * 2 * L * N},
                 {&h->rkm, (size_t)h->nd * 2 * NKS * N},
-                {&h->rkm1, h->fine_depth > 0 ? (size_t)NDIG_FINE * 2 * NKS * N : 0}};
+                {&h->rkm1, h->fine_depth > 0 ? (size_t)NDIG_FINE * 2 * NKS * N : 0},
+                {&h->rkm2, h->coarse_from > 0 ? (size_t)NDIG2 * 2 * NKS * N : 0}};
   for (auto& a : allocs) {
     if (a.words == 0) continue;
     if (cudaMalloc(a.p, a.words * sizeof(uint64_t)) != cudaSuccess) {
@@ -836,12 +854,25 @@ int hp_set_relin_key_fine(hp_handle* h, const uint64_t* rk) {
   return HP_OK;
 }
 
-// Both relinearisation keys the handle's products may use are installed.
-static bool keys_ready(const hp_handle* h) { return h->have_rk && (h->fine_depth == 0 || h->have_rk1); }
+int hp_set_relin_key_coarse(hp_handle* h, const uint64_t* rk) {
+  if (!h) return HP_ERR_ARG;
+  if (!rk) HP_FAIL(h, HP_ERR_ARG, "null two-digit relinearisation key");
+  if (!h->rkm2) HP_FAIL(h, HP_ERR_STATE, "the handle was created with ks_coarse_from = 0");
+  if (int rc = install_ks_key(h, h->rkm2, rk, NDIG2, 0)) return rc;
+  CU(h, cudaDeviceSynchronize());
+  h->have_rk2 = true;
+  return HP_OK;
+}
+
+// Every relinearisation key the handle's products may use is installed.
+static bool keys_ready(const hp_handle* h) {
+  return h->have_rk && (h->fine_depth == 0 || h->have_rk1) && (h->coarse_from == 0 || h->have_rk2);
+}
 
 // The static budget estimate of `op` on this handle's parameters.
 static double budget_of(const hp_handle* h, int op, int in_depth = 0, double in_bits = 0) {
-  return budget_estimate(h->logn, h->q, L, h->P, h->t, h->dp, (int)h->fine_depth, op, in_depth, in_bits);
+  return budget_estimate(h->logn, h->q, L, h->P, h->t, h->dp, (int)h->fine_depth, (int)h->coarse_from, op, in_depth,
+                         in_bits);
 }
 #define HP_NEED_BUDGET(h, op, what)                                                                        \
   do {                                                                                                     \
@@ -1620,8 +1651,9 @@ int hp_budget_estimate(const hp_params* prm, int op, uint32_t in_depth, double i
   if (prm->log_n < LOGN_MIN || prm->log_n > LOGN_MAX || prm->L != (uint32_t)L || prm->t < 2) return HP_ERR_ARG;
   const int dp = prm->ks_digit_primes ? (int)prm->ks_digit_primes : DIGIT_PRIMES;
   if (dp != DIGIT_PRIMES && dp != DIGIT_PRIMES5) return HP_ERR_ARG;
-  *out_bits = budget_estimate((int)prm->log_n, prm->q, L, prm->P, prm->t, dp, (int)prm->ks_fine_depth, op,
-                              (int)in_depth, in_bits);
+  if (prm->ks_coarse_from != 0 && prm->ks_coarse_from <= prm->ks_fine_depth) return HP_ERR_ARG;
+  *out_bits = budget_estimate((int)prm->log_n, prm->q, L, prm->P, prm->t, dp, (int)prm->ks_fine_depth,
+                              (int)prm->ks_coarse_from, op, (int)in_depth, in_bits);
   return HP_OK;
 }
 
@@ -1696,6 +1728,20 @@ int hp_keygen_fine(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_f
   return rc;
 }
 
+int hp_keygen_coarse(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk_coarse, void* stream) {
+  if (!h) return HP_ERR_ARG;
+  if (!sk) HP_FAIL(h, HP_ERR_ARG, "null secret key");
+  if (!h->rkm2) HP_FAIL(h, HP_ERR_STATE, "the handle was created with ks_coarse_from = 0");
+  if (!is_device_ptr(sk) || (rk_coarse && !is_device_ptr(rk_coarse))) HP_FAIL(h, HP_ERR_ARG, "keys must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t* K = rk_coarse;
+  if (!K) CU(h, cudaMalloc(&K, (size_t)NDIG2 * 2 * NKS * h->N * 8));
+  int rc = make_relin_key(h, seed, sk, K, NDIG2, COARSE_DIGIT_PRIMES, COARSE_OBJ, s);
+  if (rc == HP_OK) rc = hp_set_relin_key_coarse(h, K);
+  if (!rk_coarse) cudaFree(K);
+  return rc;
+}
+
 int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* stream) {
   if (!h) return HP_ERR_ARG;
   if (!sk || !rk) HP_FAIL(h, HP_ERR_ARG, "null output");
@@ -1703,7 +1749,9 @@ int hp_keygen(hp_handle* h, uint64_t seed, int8_t* sk, uint64_t* rk, void* strea
   k_sample_secret<<<ew_blocks(h->N), EW_THREADS, 0, s>>>(sk, seed, h->N);
   if (int rc = make_relin_key(h, seed, sk, rk, h->nd, h->dp, 0, s)) return rc;
   if (int rc = hp_set_relin_key(h, rk)) return rc;
-  if (h->fine_depth > 0) return hp_keygen_fine(h, seed, sk, nullptr, stream);
+  if (h->fine_depth > 0)
+    if (int rc = hp_keygen_fine(h, seed, sk, nullptr, stream)) return rc;
+  if (h->coarse_from > 0) return hp_keygen_coarse(h, seed, sk, nullptr, stream);
   return HP_OK;
 }
 
@@ -1938,9 +1986,10 @@ int hp_square_noalloc(hp_handle* h, const uint64_t* ct_in, uint64_t* ct_out, voi
     HP_FAIL(h, HP_ERR_UNSUPPORTED,
             "hp_square_noalloc: ring degree %d exceeds the static scratch limit of %d (%zu words)", h->N,
             1 << NOALLOC_MAX_LOGN, NOALLOC_WORDS);
-  if (h->fine_depth > 0 || h->dp != DIGIT_PRIMES)
-    HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: only handles with three-prime key-switching digits and "
-                                   "ks_fine_depth = 0 are supported (its scratch holds three-prime digits only)");
+  if (h->fine_depth > 0 || h->coarse_from > 0 || h->dp != DIGIT_PRIMES)
+    HP_FAIL(h, HP_ERR_UNSUPPORTED, "hp_square_noalloc: only handles with three-prime key-switching digits, "
+                                   "ks_fine_depth = 0 and ks_coarse_from = 0 are supported (its scratch holds "
+                                   "three-prime digits only)");
   if (!h->have_rk) HP_FAIL(h, HP_ERR_STATE, "relinearisation key not set");
   if (((uintptr_t)ct_in | (uintptr_t)ct_out) & 15) HP_FAIL(h, HP_ERR_ARG, "ciphertexts must be 16-byte aligned");
   int cur = -1;

@@ -55,6 +55,7 @@ EXPORTED = [
     "hp_galois_elements", "hp_galois_keygen", "hp_set_galois_keys", "hp_rotate_sum",
     "hp_extract_broadcast", "hp_join", "hp_ct_sum", "hp_probe_tc_gemm", "hp_probe_tc_timeout", "hp_between",
     "hp_set_relin_key_fine", "hp_keygen_fine", "hp_budget_estimate", "hp_select_mask",
+    "hp_set_relin_key_coarse", "hp_keygen_coarse",
 ]
 
 PROFILE_CLASSES = ["ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols", "lift", "tensor",
@@ -83,6 +84,7 @@ class hp_params(ctypes.Structure):
         ("max_depth", ctypes.c_uint32),
         ("ks_fine_depth", ctypes.c_uint32),
         ("ks_digit_primes", ctypes.c_uint32),
+        ("ks_coarse_from", ctypes.c_uint32),
     ]
 
 
@@ -146,6 +148,8 @@ def load():
         "hp_join": (ctypes.c_int, [H, P64, SZ, P64, P64, SZ, SZ, P64, V]),
         "hp_set_relin_key_fine": (ctypes.c_int, [H, P64]),
         "hp_keygen_fine": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
+        "hp_set_relin_key_coarse": (ctypes.c_int, [H, P64]),
+        "hp_keygen_coarse": (ctypes.c_int, [H, ctypes.c_uint64, V, P64, V]),
         "hp_budget_estimate": (ctypes.c_int, [ctypes.POINTER(hp_params), ctypes.c_int, ctypes.c_uint32,
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
         "hp_select_mask": (ctypes.c_int, [H, P64, P64, SZ, ctypes.c_uint32, ctypes.c_double, P64, V]),
@@ -194,7 +198,7 @@ class Context:
     """One libhp handle: parameters, tables, relinearisation key, workspace."""
 
     def __init__(self, log_n: int, max_tile_ct: int = 0, max_depth: int = 17, q=None, P=None, t=T,
-                 ks_fine_depth: int = 0, ks_digit_primes: int = DIGIT_PRIMES):
+                 ks_fine_depth: int = 0, ks_digit_primes: int = DIGIT_PRIMES, ks_coarse_from: int = 0):
         import torch  # device memory and streams only
 
         self.torch = torch
@@ -205,8 +209,9 @@ class Context:
         self.D = self.L // ks_digit_primes  # key-switching digits
         self.q, self.P, self.t = list(q), int(P), int(t)
         self._q = (ctypes.c_uint64 * len(q))(*q)
-        self.ks_fine_depth, self.ks_digit_primes = ks_fine_depth, ks_digit_primes
-        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth, ks_fine_depth, ks_digit_primes)
+        self.ks_fine_depth, self.ks_digit_primes, self.ks_coarse_from = ks_fine_depth, ks_digit_primes, ks_coarse_from
+        prm = hp_params(log_n, len(q), self._q, self.P, self.t, max_depth, ks_fine_depth, ks_digit_primes,
+                        ks_coarse_from)
         h = ctypes.c_void_p()
         _check(self.lib.hp_create(ctypes.byref(prm), None, max_tile_ct, ctypes.byref(h)))
         self.h = h
@@ -250,6 +255,17 @@ class Context:
 
     def set_relin_key_fine(self, rk):
         _check(self.lib.hp_set_relin_key_fine(self.h, _ptr(rk)), self.h)
+
+    def keygen_coarse(self, seed: int, sk=None, stream=None):
+        """The two-digit relinearisation key ([2, 2, L+1, N]) from the secret, installed."""
+        torch = self.torch
+        sk = self.sk if sk is None else sk
+        rk = torch.empty((2, 2, self.L + 1, self.N), dtype=torch.int64, device="cuda")
+        _check(self.lib.hp_keygen_coarse(self.h, seed, _ptr(sk), _ptr(rk), _stream(stream)), self.h)
+        return rk
+
+    def set_relin_key_coarse(self, rk):
+        _check(self.lib.hp_set_relin_key_coarse(self.h, _ptr(rk)), self.h)
 
     def encrypt(self, slots, seed: int, ct_index0: int = 0, sk=None, stream=None):
         torch = self.torch
@@ -312,7 +328,7 @@ class Context:
 
     def params(self, max_depth: int = 17) -> hp_params:
         return hp_params(self.log_n, self.L, self._q, self.P, self.t, max_depth, self.ks_fine_depth,
-                         self.ks_digit_primes)
+                         self.ks_digit_primes, self.ks_coarse_from)
 
     def eq_fanout(self, x, consts, masks=True, in_set=True, stream=None):
         """GROUP BY masks EQ(x, c_k) ([n_const, n_ct, 2, L, N]) and/or IN(x, consts)

@@ -9,14 +9,14 @@ for bit without re-running the oracle:
     JOIN          A.key = B.key over the first JOIN_ROWS rows of B with one
                   attribute (Extract + Broadcast, EQ masks, products, sums), A ciphertext 0
 
-With --digits5 the oracle uses key-switching digits of five data primes (the
-grouping the benchmark's EQ workloads use) and the digests go to
-tests/golden/aggregates_d5_n32768.txt.
+With --bench-grouping the oracle uses the benchmark's key switching for these
+workloads (digits of five data primes, the two-digit key from depth 7 on) and
+the digests go to tests/golden/aggregates_d5c7_n32768.txt.
 
 Calls only oracle/ and the seeded input recipe below (a few minutes of
 single-threaded CPU, most of it in the Galois keys and the EQ chains).
 
-    python tests/golden/make_aggregates_n32768.py [--digits5]
+    python tests/golden/make_aggregates_n32768.py [--bench-grouping]
 """
 import hashlib
 import os
@@ -64,8 +64,9 @@ def digest(ct):
 
 def main(argv):
     t0 = time.time()
-    dp = 5 if "--digits5" in argv else 3
-    o = oracle.Oracle(LOGN, dp=dp)
+    bench = "--bench-grouping" in argv
+    dp, cf = (5, 7) if bench else (3, 0)
+    o = oracle.Oracle(LOGN, dp=dp, coarse_from=cf)
     o.keygen(SEED_KEY)
     N = o.N
     for g in o.galois_elements():
@@ -91,14 +92,15 @@ def main(argv):
     for r in range(JOIN_ROWS):
         want[akey[:N] == bkey[r]] = battr[r]
     assert np.array_equal(o.decrypt(jn), want)
-    name = "aggregates_d5_n32768.txt" if dp == 5 else "aggregates_n32768.txt"
+    name = "aggregates_d5c7_n32768.txt" if bench else "aggregates_n32768.txt"
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
         f.write("# COUNT/SUM, IN and JOIN at N = 32768: SHA-256 of the oracle's ciphertexts (uint64 [2][15][32768],\n")
-        f.write("# little endian); written by tests/golden/make_aggregates_n32768.py%s\n" % (" --digits5" if dp == 5 else ""))
+        f.write("# little endian); written by tests/golden/make_aggregates_n32768.py%s\n"
+                % (" --bench-grouping" if bench else ""))
         f.write("log_n = %d\nseed_key = %d\nseed_enc = %d\n" % (LOGN, SEED_KEY, SEED_ENC))
-        if dp == 5:
-            f.write("ks_digit_primes = 5\n")
+        if bench:
+            f.write("ks_digit_primes = %d\nks_coarse_from = %d\n" % (dp, cf))
         f.write("rotate_sum_sha256 = %s\nin_sha256 = %s\njoin_sha256 = %s\n" % (digest(red), digest(ins), digest(jn)))
         f.write("oracle_seconds = %.0f\n" % (time.time() - t0))
     print(path)

@@ -1,5 +1,6 @@
 """Writes tests/golden/budgets_n4096.txt and tests/golden/fine_lt_n4096.txt
-(or, with --digits5, tests/golden/digits5_n4096.txt).
+(or, with --digits5, tests/golden/digits5_n4096.txt; with --coarse DP:C,
+tests/golden/coarse_d<DP>c<C>_n4096.txt).
 
 budgets_n4096.txt: the invariant-noise budgets the oracle measures at N = 4096
 (same primes and plaintext modulus as the paper's N = 32768, Sec. 5.1) in the
@@ -19,9 +20,14 @@ key-switching digits of five primes (three digits) instead of three, for the
 budget test and the GPU parity test of that grouping
 (tests/test_gpu_digits5.py).
 
+coarse_d<DP>c<C>_n4096.txt (--coarse DP:C): the same with digits of DP primes
+and the two-digit key from depth C on (tests/test_gpu_coarse_digits.py);
+coarse_f<F>d<DP>c<C>_n4096.txt (--coarse F:DP:C) with per-prime digits up to
+depth F as well.
+
 Calls only oracle/ and the seeded inputs below.
 
-    python tests/golden/make_n4096_budgets.py [--digits5]
+    python tests/golden/make_n4096_budgets.py [--digits5 | --coarse [F:]DP:C]
 """
 import hashlib
 import os
@@ -48,11 +54,12 @@ def lt_inputs(N):
     return x, y, col
 
 
-def measure(F, dp, here):
+def measure(F, dp, here, coarse_from=0):
     """Budgets of EQ, LT, BETWEEN, SELECT and SUM with per-prime relinearisation
-    up to depth F and digits of dp primes elsewhere; returns them with the
-    SHA-256 of the LT ciphertext."""
-    o = oracle.Oracle(LOGN, fine_depth=F, dp=dp)
+    up to depth F, the two-digit key from depth coarse_from on (0 = never) and
+    digits of dp primes elsewhere; returns them with the SHA-256 of the LT
+    ciphertext."""
+    o = oracle.Oracle(LOGN, fine_depth=F, dp=dp, coarse_from=coarse_from)
     o.keygen(SEED_KEY)
     N = o.N
     x, y, col = lt_inputs(N)
@@ -84,6 +91,24 @@ NAMES = ("eq", "lt", "between", "select", "sum")
 
 def main(argv):
     here = os.path.dirname(os.path.abspath(__file__))
+    if "--coarse" in argv:
+        spec = [int(v) for v in argv[argv.index("--coarse") + 1].split(":")]
+        F, dp, cf = spec if len(spec) == 3 else [0] + spec
+        row, lt_sha = measure(F, dp, here, cf)
+        name = ("coarse_f%dd%dc%d_n4096.txt" % (F, dp, cf)) if F else ("coarse_d%dc%d_n4096.txt" % (dp, cf))
+        with open(os.path.join(here, name), "w") as f:
+            f.write("# %sDigits of %d primes with the two-digit key from depth %d on, at N = 4096: the noise budgets\n"
+                    % ("Per-prime digits up to depth %d, then " % F if F else "", dp, cf))
+            f.write("# (bits) the oracle measures in the results of EQ, LT, BETWEEN, SELECT on the BETWEEN mask and its\n")
+            f.write("# SUM, and the SHA-256 of its LT ciphertext (uint64 [2][15][4096], little endian); written by\n")
+            f.write("# tests/golden/make_n4096_budgets.py --coarse %s (inputs: its lt_inputs, ciphertext indices 0, 1)\n"
+                    % ":".join(str(v) for v in spec))
+            f.write("log_n = %d\nseed_key = %d\nseed_enc = %d\nks_fine_depth = %d\nks_digit_primes = %d\n"
+                    "ks_coarse_from = %d\n" % (LOGN, SEED_KEY, SEED_ENC, F, dp, cf))
+            for name, b in zip(NAMES, row):
+                f.write("%s = %.2f\n" % (name, b))
+            f.write("lt_sha256 = %s\n" % lt_sha)
+        return
     if "--digits5" in argv:
         row, lt_sha = measure(0, 5, here)
         with open(os.path.join(here, "digits5_n4096.txt"), "w") as f:

@@ -1,4 +1,5 @@
-"""Writes tests/golden/range_n32768_f<F>.txt (and, with --lt, lt_n32768.txt):
+"""Writes tests/golden/range_n32768_f<F>.txt (and, with --lt, lt_n32768.txt;
+with --digit-primes 5 and --coarse-from C > 0 the names end in _d5, _c<C>):
 the SHA-256 digests of the ciphertexts the oracle computes at the paper's ring
 degree N = 32768 for a range filter followed by an aggregate, the pattern of
 TPC-H Q6 (Table 5: filter, then SUM):
@@ -8,7 +9,10 @@ TPC-H Q6 (Table 5: filter, then SUM):
     agg  = rotate-and-add(sel)       (SUM, Sec. 4.2.2: every slot holds the column's sum)
 
 and, with --lt, LT(x, y) (Eq. 4) on its own, together with the noise budget
-the oracle measures in each result.  The GPU test (tests/test_gpu_range_n32768.py)
+the oracle measures in each result.  --digit-primes sets the key-switching
+digits between the per-prime ones (up to --fine-depth) and the two-digit key
+(data primes 0..7 and 8..14) that relinearises the products at depth
+--coarse-from and beyond.  The GPU test (tests/test_gpu_range_n32768.py)
 compares its own ciphertexts with these digests bit for bit, so it does not
 re-run the oracle (each LT is about forty minutes of single-threaded CPU at this
 ring degree).  Calls only oracle/ and the seeded input recipe below.
@@ -16,6 +20,8 @@ ring degree).  Calls only oracle/ and the seeded input recipe below.
     python tests/golden/make_range_n32768.py --fine-depth 0
     python tests/golden/make_range_n32768.py --fine-depth 3
     python tests/golden/make_range_n32768.py --lt
+    python tests/golden/make_range_n32768.py --fine-depth 4 --digit-primes 5 --coarse-from 10
+    python tests/golden/make_range_n32768.py --lt --fine-depth 4 --digit-primes 5 --coarse-from 10
 """
 import argparse
 import hashlib
@@ -67,11 +73,16 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--fine-depth", type=int, default=0)
     ap.add_argument("--lt", action="store_true")
+    ap.add_argument("--coarse-from", type=int, default=0)
+    ap.add_argument("--digit-primes", type=int, default=3)
     a = ap.parse_args()
-    F = 0 if a.lt else a.fine_depth
+    F, C, dp = a.fine_depth, a.coarse_from, a.digit_primes
+    sfx = ("_d%d" % dp if dp != 3 else "") + ("_c%d" % C if C else "")
     t0 = time.time()
-    o = oracle.Oracle(LOGN, fine_depth=F)
+    o = oracle.Oracle(LOGN, fine_depth=F, coarse_from=C, dp=dp)
     o.keygen(SEED_KEY)
+    opts = "".join([" --lt" if a.lt else "", " --fine-depth %d" % F if (F or not a.lt) else "",
+                    " --digit-primes %d" % dp if dp != 3 else "", " --coarse-from %d" % C if C else ""])
     N = o.N
     x, y, col = range_inputs(N)
     cx = o.encrypt(x, SEED_ENC, CT_X)
@@ -80,10 +91,12 @@ def main():
         lt = o.lt(cx, cy)
         got, nb = o.decrypt(lt, with_noise=True)
         assert np.array_equal(got, (x < y).astype(np.uint32))
-        write("lt_n32768.txt",
+        write("lt_n32768%s.txt" % (("_f%d" % F if F else "") + sfx),
               ["LT(x, y) (Eq. 4) at N = 32768: SHA-256 of the oracle's ciphertext (uint64 [2][15][32768],",
-               "little endian) and its measured noise budget; written by tests/golden/make_range_n32768.py --lt"],
-              [("log_n", LOGN), ("seed_key", SEED_KEY), ("seed_enc", SEED_ENC), ("ks_fine_depth", 0),
+               "little endian) and its measured noise budget; written by tests/golden/make_range_n32768.py --lt%s"
+               % opts],
+              [("log_n", LOGN), ("seed_key", SEED_KEY), ("seed_enc", SEED_ENC), ("ks_fine_depth", F)]
+              + ([("ks_digit_primes", dp)] if dp != 3 else []) + ([("ks_coarse_from", C)] if C else []) + [
                ("lt_sha256", digest(lt)), ("lt_budget_bits", "%.2f" % nb),
                ("oracle_seconds", "%.0f" % (time.time() - t0))])
         return
@@ -101,11 +114,13 @@ def main():
     got, nb_agg = o.decrypt(agg, with_noise=True)
     total = int(col[sel_rows].astype(np.int64).sum() % 65537)
     assert np.all(got == total)
-    write("range_n32768_f%d.txt" % F,
-          ["BETWEEN -> SELECT -> SUM at N = 32768 with per-prime relinearisation up to depth %d:" % F,
+    write("range_n32768_f%d%s.txt" % (F, sfx),
+          ["BETWEEN -> SELECT -> SUM at N = 32768 with per-prime relinearisation up to depth %d%s:"
+           % (F, "".join([", digits of %d primes" % dp if dp != 3 else "", ", two-digit from depth %d" % C if C else ""])),
            "SHA-256 of the oracle's ciphertexts (uint64 [2][15][32768], little endian) and their measured",
-           "noise budgets; written by tests/golden/make_range_n32768.py --fine-depth %d" % F],
-          [("log_n", LOGN), ("seed_key", SEED_KEY), ("seed_enc", SEED_ENC), ("ks_fine_depth", F), ("lo", LO),
+           "noise budgets; written by tests/golden/make_range_n32768.py%s" % opts],
+          [("log_n", LOGN), ("seed_key", SEED_KEY), ("seed_enc", SEED_ENC), ("ks_fine_depth", F)]
+          + ([("ks_digit_primes", dp)] if dp != 3 else []) + ([("ks_coarse_from", C)] if C else []) + [("lo", LO),
            ("hi", HI), ("mask_depth", MASK_DEPTH), ("between_sha256", digest(mask)),
            ("between_budget_bits", "%.2f" % nb_mask), ("select_sha256", digest(sel)),
            ("select_budget_bits", "%.2f" % nb_sel), ("sum_sha256", digest(agg)), ("sum_budget_bits", "%.2f" % nb_agg),

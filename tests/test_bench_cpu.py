@@ -20,11 +20,15 @@ def test_every_config_has_a_composition_and_a_multiplication_count():
     for op in OPS:
         assert op in bench.OracleSample.COUNTS
         assert op == "batched" or op in bench.HMULT_PER_CT
-    # an EQ chain is 16 squarings (p - 1 = 2^16, Eq. 3); LT's schedule 511 products
-    assert bench.OracleSample.COUNTS["ctct"][1] == 16 == bench.HMULT_PER_CT["ctct"]
-    assert bench.OracleSample.COUNTS["lt"][1] == 511 == bench.HMULT_PER_CT["lt"]
-    # BETWEEN: two LT evaluations and their product (Sec. 4.2.2)
-    assert bench.OracleSample.COUNTS["between"][1] == 2 * 511 + 1 == bench.HMULT_PER_CT["between"]
+    for op in OPS:  # the multiplications' depths agree with the counts
+        assert op == "batched" or len(bench.product_depths(op)) == bench.HMULT_PER_CT[op]
+    # an EQ chain is 16 squarings (p - 1 = 2^16, Eq. 3), at depths 1 .. 16
+    assert bench.product_depths("ctct") == list(range(1, 17)) and bench.HMULT_PER_CT["ctct"] == 16
+    # LT's schedule: 511 products, the deepest at 18; 255 of them at depth 10 or more
+    d = bench.lt_product_depths()
+    assert len(d) == 511 == bench.HMULT_PER_CT["lt"] and max(d) == 18 and sum(v >= 10 for v in d) == 255
+    # BETWEEN: two LT evaluations and their product at depth 19 (Sec. 4.2.2)
+    assert bench.HMULT_PER_CT["between"] == 2 * 511 + 1 and max(bench.product_depths("between")) == 19
 
 
 def test_stored_traffic_scales_with_the_tile_and_follows_the_sources():

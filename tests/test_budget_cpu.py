@@ -6,19 +6,20 @@ import ctypes
 from paper_2602_24271_b300 import hp
 
 
-def _budget(logn, fine_depth, op, in_depth=0, in_bits=0.0, dp=3):
+def _budget(logn, fine_depth, op, in_depth=0, in_bits=0.0, dp=3, cf=0):
     q, P, t = hp.default_params()
     qa = (ctypes.c_uint64 * len(q))(*q)
-    return hp.budget_estimate(hp.hp_params(logn, len(q), qa, P, t, 17, fine_depth, dp), op, in_depth, in_bits)
+    return hp.budget_estimate(hp.hp_params(logn, len(q), qa, P, t, 17, fine_depth, dp, cf), op, in_depth, in_bits)
 
 
 def test_budget_estimate_lies_below_the_oracle_measurements():
     """The library's static noise-budget estimate (the depth guard of every
     operation) never promises more than the oracle measured: EQ, LT, BETWEEN,
     SELECT on the BETWEEN mask and its SUM at N = 4096 and N = 32768, with
-    three-prime key switching throughout, with per-prime digits up to depth 3
-    and with five-prime digits (measurements written by
-    tests/golden/make_n4096_budgets.py and make_range_n32768.py).  It is not vacuous either: within 80 bits of each."""
+    three-prime key switching throughout, with per-prime digits up to depth 3,
+    with five-prime digits and with the two-digit key from a given depth on
+    (measurements written by tests/golden/make_n4096_budgets.py and
+    make_range_n32768.py).  It is not vacuous either: within 80 bits of each."""
     from tests.conftest import read_golden_kv
 
     hp.load()
@@ -30,6 +31,13 @@ def test_budget_estimate_lies_below_the_oracle_measurements():
         sel = _budget(12, F, PR, 19, bt)
         pairs += [(_budget(12, F, E), g["f%d_eq" % F]), (_budget(12, F, LT), g["f%d_lt" % F]), (bt, g["f%d_between" % F]),
                   (sel, g["f%d_select" % F]), (_budget(12, F, RS, 0, sel), g["f%d_sum" % F])]
+    for name, F, dp, cf in (("coarse_d5c7_n4096.txt", 0, 5, 7), ("coarse_d3c10_n4096.txt", 0, 3, 10),
+                            ("coarse_f4d5c10_n4096.txt", 4, 5, 10)):
+        g = read_golden_kv(name)
+        bt = _budget(12, F, BT, dp=dp, cf=cf)
+        sel = _budget(12, F, PR, 19, bt, dp=dp, cf=cf)
+        pairs += [(_budget(12, F, E, dp=dp, cf=cf), g["eq"]), (_budget(12, F, LT, dp=dp, cf=cf), g["lt"]),
+                  (bt, g["between"]), (sel, g["select"]), (_budget(12, F, RS, 0, sel, dp=dp, cf=cf), g["sum"])]
     d5 = read_golden_kv("digits5_n4096.txt")
     bt = _budget(12, 0, BT, dp=5)
     sel = _budget(12, 0, PR, 19, bt, dp=5)

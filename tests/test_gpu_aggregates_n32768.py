@@ -1,8 +1,9 @@
 """COUNT / SUM, IN and JOIN (Sec. 4.2.2, Eq. 6) at the paper's ring degree
-N = 32768 (Sec. 5.1), with key-switching digits of three and of five primes.  Every slot of every result is checked against its closed
+N = 32768 (Sec. 5.1), with three-prime key-switching digits and with the
+benchmark's key switching for these workloads.  Every slot of every result is checked against its closed
 form after GPU decryption, and one ciphertext of each against the oracle bit for
 bit through the SHA-256 digests that tests/golden/make_aggregates_n32768.py
-(with --digits5 for five-prime digits) wrote from the oracle:
+(with --bench-grouping for the benchmark's key switching) wrote from the oracle:
 
 * SUM over a 2^26-slot column (2048 ciphertexts summed, then reduced by
   rotate-and-add): the column's total mod p in every slot; the reduction of
@@ -28,18 +29,20 @@ def _digest(ct):
     return hashlib.sha256(np.ascontiguousarray(hp.to_u64(ct), dtype=np.uint64).tobytes()).hexdigest()
 
 
-@pytest.fixture(scope="module", params=[3, 5])
+@pytest.fixture(scope="module", params=[(3, 0), (5, 7)], ids=["three-prime", "bench"])
 def agg(request):
-    """The handle with key-switching digits of three primes and of five (the
-    grouping the benchmark's aggregate workloads use), each against the
-    digests the oracle wrote with the same grouping."""
+    """The handle with three-prime key-switching digits, and with the key
+    switching the benchmark's aggregate workloads use (five-prime digits, the
+    two-digit key from depth 7 on), each against the digests the oracle wrote
+    with the same rule."""
     import torch
 
     build.build()
-    dp = request.param
-    gold = read_golden_kv("aggregates_d5_n32768.txt" if dp == 5 else "aggregates_n32768.txt")
-    assert gold["seed_key"] == SEED_KEY and gold["log_n"] == LOGN and gold.get("ks_digit_primes", 3) == dp
-    ctx = hp.Context(LOGN, ks_digit_primes=dp)
+    dp, cf = request.param
+    gold = read_golden_kv("aggregates_d5c7_n32768.txt" if cf else "aggregates_n32768.txt")
+    assert gold["seed_key"] == SEED_KEY and gold["log_n"] == LOGN
+    assert gold.get("ks_digit_primes", 3) == dp and gold.get("ks_coarse_from", 0) == cf
+    ctx = hp.Context(LOGN, ks_digit_primes=dp, ks_coarse_from=cf)
     ctx.keygen(SEED_KEY)
     ctx.galois_keygen(SEED_KEY)
     ctx.autotune()

@@ -1,5 +1,6 @@
 """Full-size parity at N = 32768 in the benchmark's launch configuration
-(autotuned tiles, key-switching digits of five primes): the plain workload
+(autotuned tiles, key-switching digits of five primes, the two-digit key from
+depth 7 on): the plain workload
 (2^26 slots = 2048 ciphertext pairs) and the constant form at 2^28 slots (8192
 ciphertexts).  Every slot of every
 result is checked against the closed form [x == y] after GPU decryption (whose
@@ -20,7 +21,7 @@ pytestmark = pytest.mark.gpu
 LOGN = 15
 SEED_KEY = 1
 N_SAMPLES = 16
-DP = 5  # data primes per key-switching digit, as the benchmark's EQ workloads use
+DP, COARSE = 5, 7  # key switching as the benchmark's EQ workloads use it
 
 
 def sample_indices(n_ct: int, seed: int):
@@ -38,10 +39,10 @@ def big():
     import torch
 
     build.build()
-    ctx = hp.Context(LOGN, ks_digit_primes=DP)
+    ctx = hp.Context(LOGN, ks_digit_primes=DP, ks_coarse_from=COARSE)
     ctx.keygen(SEED_KEY)
     ctx.autotune()
-    o = oracle.Oracle(LOGN, dp=DP)
+    o = oracle.Oracle(LOGN, dp=DP, coarse_from=COARSE)
     o.keygen(SEED_KEY)
     yield ctx, o
     ctx.close()
@@ -78,7 +79,8 @@ def test_plain_workload_2048_pairs(big):
     assert np.array_equal(dec.reshape(-1), (x == y).astype(np.uint32))
     ctx.check_status()
     idx = sample_indices(n_ct, 101)
-    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], [hp.to_u64(cy[c]) for c in idx], dp=DP)
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], [hp.to_u64(cy[c]) for c in idx], dp=DP,
+                   coarse_from=COARSE)
     for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
         assert np.array_equal(hp.to_u64(out[c]), w), c
     import torch
@@ -103,7 +105,7 @@ def test_const_workload_2_28_slots(big):
         dec = decrypt_chunked(ctx, out[c0:c1])
         assert np.array_equal(dec.reshape(-1), (x[c0 * N:c1 * N] == cval).astype(np.uint32))
     idx = sample_indices(n_ct, 103)
-    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], None, const_val=cval, dp=DP)
+    want = eq_many(LOGN, SEED_KEY, [hp.to_u64(cx[c]) for c in idx], None, const_val=cval, dp=DP, coarse_from=COARSE)
     for c, w in zip(idx, want):  # sampled ciphertexts, bit for bit
         assert np.array_equal(hp.to_u64(out[c]), w), c
     del cx, out

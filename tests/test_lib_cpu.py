@@ -49,11 +49,11 @@ def test_default_params_bad_args(lib):
     assert lib.hp_default_params(16, q, ctypes.byref(P), ctypes.byref(t)) == hp.HP_ERR_ARG
 
 
-def _create(lib, log_n=15, max_depth=16, q=None, P=None, t=65537, dp=0):
+def _create(lib, log_n=15, max_depth=16, q=None, P=None, t=65537, dp=0, fine=0, coarse=0):
     if q is None:
         q, P, t = hp.default_params()
     qa = (ctypes.c_uint64 * len(q))(*q)
-    prm = hp.hp_params(log_n, len(q), qa, P, t, max_depth, 0, dp)
+    prm = hp.hp_params(log_n, len(q), qa, P, t, max_depth, fine, dp, coarse)
     h = ctypes.c_void_p()
     rc = lib.hp_create(ctypes.byref(prm), None, 1, ctypes.byref(h))
     return rc, h
@@ -74,6 +74,10 @@ def test_create_rejects_bad_parameters(lib):
         rc, _ = _create(lib, dp=dp)
         assert rc == hp.HP_ERR_UNSUPPORTED
         assert b"ks_digit_primes" in lib.hp_last_error(None)
+    for fine, coarse in ((3, 3), (3, 1)):  # the two-digit key starts above the fine depth
+        rc, _ = _create(lib, fine=fine, coarse=coarse)
+        assert rc == hp.HP_ERR_ARG
+        assert b"ks_coarse_from" in lib.hp_last_error(None)
 
 
 def test_backward_is_unsupported(lib):

@@ -31,13 +31,19 @@ CASES = [
     (13, "first giant step w^128", pins.test_lt_closed_form_n16),
     (14, "noise budget without its factor 2", pins.test_noise_budget_bruteforce),
     (15, "per-prime key only below the fine depth", lambda o: pins.check_fine_depth_selection(oracle.build_mutant(15))),
+    (16, "two-digit key from one level late", lambda o: pins.check_coarse_selection(oracle.build_mutant(16))),
 ]
 
 
 def _name(pin):
     if pin.__name__.startswith("test_"):
         return pin.__name__[5:]
-    return "fine_depth_selection" if "check_fine_depth_selection" in pin.__code__.co_names else "automorphism_permutes_slots"
+    names = pin.__code__.co_names
+    if "check_fine_depth_selection" in names:
+        return "fine_depth_selection"
+    if "check_coarse_selection" in names:
+        return "coarse_selection"
+    return "automorphism_permutes_slots"
 
 
 def _oracle16(lib_path=None):

@@ -353,7 +353,7 @@ def _key_relation_ok(o, rk, groups, s2):
     return True
 
 
-@pytest.mark.parametrize("dp", [1, 2, 3, 5])
+@pytest.mark.parametrize("dp", [1, 2, 3, 5, 8])
 def test_digit_groupings_keys_and_relinearisation_bruteforce(dp):
     """Key switching with digits of dp consecutive data primes (the last group
     shorter when dp does not divide L = 15): the keys satisfy their defining
@@ -395,6 +395,34 @@ def check_fine_depth_selection(lib_path=None):
     b = o.encrypt(rng.integers(0, T, o.N).astype(np.uint32), seed=3, ct_index=1)
     d3 = o.tensor_round(a, b)
     for depth_a, key, groups in [(0, fine, per_prime), (1, o.rk, three)]:
+        got = o.mul_relin(a, b, depth_a=depth_a)
+        want = _relin_bruteforce(o, d3, key, groups)
+        assert to_ints(got[0], o.q) == want[0] and to_ints(got[1], o.q) == want[1], depth_a
+
+
+def test_coarse_from_selects_the_two_digit_key_bruteforce():
+    """With coarse_from C = 2 the oracle keeps a third relinearisation key of two
+    digits (data primes 0..7 and 8..14; its own relation holds) and relinearises
+    a product of fresh ciphertexts (depth 1) with the three-prime key, products
+    at depth 2 and 3 with the two-digit key: each equals tensor-and-round
+    followed by the integer key switching of its key, by brute force."""
+    check_coarse_selection()
+
+
+def check_coarse_selection(lib_path=None):
+    o = oracle.Oracle(4, coarse_from=2, lib_path=lib_path)
+    o.keygen(7)
+    coarse = o.coarse_key()
+    sl = [int(v) for v in o.s]
+    s2 = negacyclic_schoolbook(sl, sl, o.N)
+    two = [list(range(8)), list(range(8, o.L))]
+    three = [[3 * a, 3 * a + 1, 3 * a + 2] for a in range(5)]
+    assert _key_relation_ok(o, coarse, two, s2)
+    rng = np.random.default_rng(62)
+    a = o.encrypt(rng.integers(0, T, o.N).astype(np.uint32), seed=3, ct_index=0)
+    b = o.encrypt(rng.integers(0, T, o.N).astype(np.uint32), seed=3, ct_index=1)
+    d3 = o.tensor_round(a, b)
+    for depth_a, key, groups in [(0, o.rk, three), (1, coarse, two), (2, coarse, two)]:
         got = o.mul_relin(a, b, depth_a=depth_a)
         want = _relin_bruteforce(o, d3, key, groups)
         assert to_ints(got[0], o.q) == want[0] and to_ints(got[1], o.q) == want[1], depth_a
