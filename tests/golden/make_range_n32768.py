@@ -93,7 +93,7 @@ def main():
         assert np.array_equal(got, (x < y).astype(np.uint32))
         write("lt_n32768%s.txt" % (("_f%d" % F if F else "") + sfx),
               ["LT(x, y) (Eq. 4) at N = 32768: SHA-256 of the oracle's ciphertext (uint64 [2][15][32768],",
-               "little endian) and its measured noise budget; written by tests/golden/make_range_n32768.py --lt%s"
+               "little endian) and its measured noise budget; written by tests/golden/make_range_n32768.py%s"
                % opts],
               [("log_n", LOGN), ("seed_key", SEED_KEY), ("seed_enc", SEED_ENC), ("ks_fine_depth", F)]
               + ([("ks_digit_primes", dp)] if dp != 3 else []) + ([("ks_coarse_from", C)] if C else []) + [
