@@ -568,6 +568,18 @@ __global__ void __launch_bounds__(NTT_THREADS, MD ? 7 : 8) k_ntt_inv_cols(uint64
   const uint64_t p = f.p;
   const ulonglong2* itw = T.itw + (size_t)id * N;
   uint64_t* a = data + (size_t)poly * N;
+  if (MD) {  // the epilogue's operands into L2 while the transform runs
+    const size_t bc = (size_t)(y0 / L);
+    const int i = y0 % L, comp = (int)(bc & 1);
+    const uint64_t* uP = data + (bc * NKS + L) * N;
+    const uint64_t* wv = md.w3 + (((bc >> 1) * 3 + comp) * L + i) * N;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int n = (rb + u * RB) * C + k0 + k;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(uP + n));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(wv + n));
+    }
+  }
 #pragma unroll
   for (int m = 0; m < (16 >> A2); ++m) {
     const int g = rb + m * RB;
