@@ -50,6 +50,13 @@ def test_budget_estimate_lies_below_the_oracle_measurements():
         pairs += [(bt, r["between_budget_bits"]), (sel, r["select_budget_bits"]),
                   (_budget(15, F, RS, 0, sel), r["sum_budget_bits"])]
     pairs.append((_budget(15, 0, LT), read_golden_kv("lt_n32768.txt")["lt_budget_bits"]))
+    # the benchmark's LT / BETWEEN key switching: per-prime up to depth 4, five-prime, two-digit from depth 10
+    r = read_golden_kv("range_n32768_f4_d5_c10.txt")
+    bt = _budget(15, 4, BT, dp=5, cf=10)
+    sel = _budget(15, 4, PR, 19, bt, dp=5, cf=10)
+    pairs += [(bt, r["between_budget_bits"]), (sel, r["select_budget_bits"]),
+              (_budget(15, 4, RS, 0, sel, dp=5, cf=10), r["sum_budget_bits"]),
+              (_budget(15, 4, LT, dp=5, cf=10), read_golden_kv("lt_n32768_f4_d5_c10.txt")["lt_budget_bits"])]
     for est, measured in pairs:
         assert 0 < est <= measured < est + 80, (est, measured)
     # the guard's margin: a product on a mask with too little budget left is refused

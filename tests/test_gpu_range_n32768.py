@@ -6,7 +6,9 @@ the shape of TPC-H Q6 (Table 5: the filter, then SUM):
     agg  = rotate-and-add(sel)  (SUM, Sec. 4.2.2)
 
 with per-prime relinearisation up to depth 0 (three-prime key switching
-throughout) and 3.  Every slot of every result is checked against its closed
+throughout) and 3, and with the benchmark's key switching for LT and BETWEEN
+(per-prime digits up to depth 4, five-prime digits, the two-digit key from
+depth 10).  Every slot of every result is checked against its closed
 form after GPU decryption ([lo <= x <= hi], col where selected, the column's
 sum in every slot), and each ciphertext bit for bit against the oracle's
 through the SHA-256 that tests/golden/make_range_n32768.py wrote from the
@@ -29,14 +31,25 @@ def _digest(ct):
     return hashlib.sha256(np.ascontiguousarray(hp.to_u64(ct), dtype=np.uint64).tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("fine_depth", [0, 3])
-def test_between_select_sum_n32768(fine_depth):
+SCHEDULES = [(0, 3, 0), (3, 3, 0), (4, 5, 10)]  # (per-prime up to, digit primes, two-digit key from)
+
+
+def _golden(kind, F, dp, cf):
+    sfx = ("_d%d" % dp if dp != 3 else "") + ("_c%d" % cf if cf else "")
+    if kind == "lt":
+        return read_golden_kv("lt_n32768%s.txt" % (("_f%d" % F if F else "") + sfx))
+    return read_golden_kv("range_n32768_f%d%s.txt" % (F, sfx))
+
+
+@pytest.mark.parametrize("fine_depth, dp, cf", SCHEDULES)
+def test_between_select_sum_n32768(fine_depth, dp, cf):
     import torch
 
     build.build()
-    gold = read_golden_kv("range_n32768_f%d.txt" % fine_depth)
+    gold = _golden("range", fine_depth, dp, cf)
     assert gold["lo"] == LO and gold["hi"] == HI and gold["seed_key"] == SEED_KEY
-    ctx = hp.Context(LOGN, max_tile_ct=1, ks_fine_depth=fine_depth)
+    assert gold.get("ks_digit_primes", 3) == dp and gold.get("ks_coarse_from", 0) == cf
+    ctx = hp.Context(LOGN, max_tile_ct=1, ks_fine_depth=fine_depth, ks_digit_primes=dp, ks_coarse_from=cf)
     ctx.keygen(SEED_KEY)
     ctx.galois_keygen(SEED_KEY)
     N = ctx.N
@@ -69,13 +82,15 @@ def test_between_select_sum_n32768(fine_depth):
     torch.cuda.empty_cache()
 
 
-def test_lt_n32768():
+@pytest.mark.parametrize("fine_depth, dp, cf", [(0, 3, 0), (4, 5, 10)])
+def test_lt_n32768(fine_depth, dp, cf):
     import torch
 
     build.build()
-    gold = read_golden_kv("lt_n32768.txt")
-    assert gold["seed_key"] == SEED_KEY and gold["ks_fine_depth"] == 0
-    ctx = hp.Context(LOGN, max_tile_ct=1)
+    gold = _golden("lt", fine_depth, dp, cf)
+    assert gold["seed_key"] == SEED_KEY and gold["ks_fine_depth"] == fine_depth
+    assert gold.get("ks_digit_primes", 3) == dp and gold.get("ks_coarse_from", 0) == cf
+    ctx = hp.Context(LOGN, max_tile_ct=1, ks_fine_depth=fine_depth, ks_digit_primes=dp, ks_coarse_from=cf)
     ctx.keygen(SEED_KEY)
     N = ctx.N
     x, y, _ = range_inputs(N)
