@@ -442,7 +442,10 @@ class Oracle:
     def join(self, a_key, b_key, b_attrs, n_rows: int):
         """Equi-join A.key = B.key over the first n_rows rows of B (Sec. 4.2.2):
         mask_r = EQ(A.key, Broadcast(B.key[r])); with attributes, out[k] =
-        sum_r mask_r * Broadcast(B.attr_k[r]); without, out = sum_r mask_r."""
+        sum_r mask_r * Broadcast(B.attr_k[r]); without, out = sum_r mask_r.  A
+        mask is an EQ result at depth 16 (Eq. 3), so its product with a
+        broadcast attribute lies at depth 17 and is relinearised with the key of
+        that depth."""
         kb = [self.extract_broadcast(b_key, r) for r in range(n_rows)]
         vb = [[self.extract_broadcast(col, r) for r in range(n_rows)] for col in b_attrs]
         outs = []
@@ -451,7 +454,8 @@ class Oracle:
             if not b_attrs:
                 outs.append(self.linear(np.stack(masks), [1] * n_rows)[None])
             else:
-                outs.append(np.stack([self.linear(np.stack([self.mul_relin(masks[r], vb[k][r]) for r in range(n_rows)]),
+                outs.append(np.stack([self.linear(np.stack([self.mul_relin(masks[r], vb[k][r], depth_a=16)
+                                                            for r in range(n_rows)]),
                                                   [1] * n_rows) for k in range(len(b_attrs))]))
         return np.stack(outs, axis=1)  # [max(1, n_attr)][n_a][2][L][N]
 
