@@ -148,11 +148,11 @@ MAC_PER_UNIT = {4: 15 * 16, 6: 2 * 15 * 16, 8: 1}  # lift, scale-and-round, key-
 # (per ciphertext; per ciphertext and B row for join); rotations are not counted
 HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "sum": 17, "rotsum": 0, "join": 18}
 # Shoup products of the digit recombination per ciphertext and multiplication, in
-# units of N, for digits of G primes: per digit (15 / G) and target prime (16),
-# G - 1 products, or o for the digit's own prime at offset o:
-# G = 3: 5 (13 x 2 + 0 + 1 + 2) = 145; G = 5: 3 (11 x 4 + 0 + 1 + 2 + 3 + 4) = 162;
-# the two-digit key (8 and 7 primes): (8 x 7 + 28) + (9 x 6 + 21) = 159
-DIGIT_PRODUCTS_PER_HMULT = {3: 145, 5: 162, 8: 159}
+# units of N, for digits of G primes: per digit (15 / G) and target prime outside
+# the digit's own primes, G - 1 products (a digit's value modulo one of its own
+# primes is d2's residue, read as stored): G = 3: 5 x 13 x 2 = 130; G = 5:
+# 3 x 11 x 4 = 132; the two-digit key (8 and 7 primes): 8 x 7 + 9 x 6 = 110
+DIGIT_PRODUCTS_PER_HMULT = {3: 130, 5: 132, 8: 110}
 # key switching per workload: (per-prime digits up to this depth, data primes
 # per digit, depth from which the two-digit key relinearises).  The workloads
 # built on EQ chains and rotations: five-prime digits (3 digits), whose depth-16

@@ -114,7 +114,7 @@ int hp_default_params(uint32_t L, uint64_t* q_out, uint64_t* P_out, uint64_t* t_
  * (HP_ERR_DEPTH if max_depth exceeds what the modulus supports).
  * `max_tile_ct` bounds how many ciphertexts are processed per pipeline tile
  * (0 = library default: the tile that fits about 11 GB of workspace, at most
- * 64); device workspace grows linearly with it (161 MB per ciphertext at
+ * 64); device workspace grows linearly with it (165 MB per ciphertext at
  * N = 32768, including two staging sets for overlapped host-memory calls).  `relin_key` may be NULL (set it later
  * with hp_set_relin_key); otherwise it is a device pointer with the layout
  * above.  On success *out owns all device memory it allocated. */

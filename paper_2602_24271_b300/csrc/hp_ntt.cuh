@@ -74,9 +74,13 @@ enum { SCALE_NINV = 0, SCALE_T_NINV_R = 1, SCALE_NINV_R = 2, SCALE_NINV_PINV = 3
 // same with G = 8 for data primes 0..7 and G = 7 for 8..14; a per-prime digit (dp = 1) is the
 // residue w3[b][2][g] < q_g, which one conditional subtraction reduces modulo
 // any target (q_g < 2 p_j).
+// A digit's value modulo one of its own primes is the residue of d2 itself: with
+// res (d2's residues, [b][L][N]) those targets are read from there instead of
+// being recombined.
 struct DigitSrc {
   const uint64_t* w3;  // nullptr: the pass transforms `data` in place
   int dp;              // data primes per digit: 1, 3, 5 or COARSE_DIGIT_PRIMES (the two-digit key)
+  const uint64_t* res = nullptr;  // d2's residues, or nullptr
 };
 
 // ---- modular helpers for the transform ------------------------------------------
@@ -135,14 +139,16 @@ HPD void digit_terms(uint64_t (&x)[16], const uint64_t* __restrict__ src, int rb
 // constant is a multiple of p_j), and at o = 0 the value is t_0 itself, already
 // canonical.
 template <int G, int LOGR, int LOGC>
-HPD void load_digit(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly, int rb, int col, const PForm& f) {
+HPD void load_digit(uint64_t (&x)[16], const uint64_t* __restrict__ w3, const uint64_t* __restrict__ res, int poly,
+                    int rb, int col, const PForm& f) {
   constexpr int N = 1 << (LOGR + LOGC), C = 1 << LOGC, RB = 1 << (LOGR - 4), ND = L / G;
   const int b = poly / (ND * NKS), g = (poly / NKS) % ND, j = poly % NKS;
   const uint64_t* src = w3 + ((size_t)(b * 3 + 2) * L + g * G) * N;
   const int o = j - G * g;  // offset of the target inside the digit's group
-  if (o == 0) {
+  if (o == 0 || (res && o > 0 && o < G)) {  // t_0, or the stored residue modulo the digit's own prime j
+    const uint64_t* r = o == 0 ? src : res + ((size_t)b * L + j) * N;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + col];
+    for (int u = 0; u < 16; ++u) x[u] = r[(size_t)(rb + u * RB) * C + col];
     return;
   }
   uint64_t c[G - 1], cs[G - 1];
@@ -164,15 +170,17 @@ HPD void load_digit(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly
 // (data primes 8a .. 8a + 7, the second digit one prime shorter) of ciphertext
 // b reduced modulo target prime j, as load_digit.
 template <int LOGR, int LOGC>
-HPD void load_digit2(uint64_t (&x)[16], const uint64_t* __restrict__ w3, int poly, int rb, int col, const PForm& f) {
+HPD void load_digit2(uint64_t (&x)[16], const uint64_t* __restrict__ w3, const uint64_t* __restrict__ res, int poly,
+                     int rb, int col, const PForm& f) {
   constexpr int N = 1 << (LOGR + LOGC), C = 1 << LOGC, RB = 1 << (LOGR - 4), G = COARSE_DIGIT_PRIMES;
   const int b = poly / (NDIG2 * NKS), a = (poly / NKS) % NDIG2, j = poly % NKS;
   const int base = G * a, g = a == 0 ? G : L - G;  // primes in this digit
   const uint64_t* src = w3 + ((size_t)(b * 3 + 2) * L + base) * N;
   const int o = j - base;
-  if (o == 0) {
+  if (o == 0 || (res && o > 0 && o < g)) {  // t_0, or the stored residue modulo the digit's own prime j
+    const uint64_t* r = o == 0 ? src : res + ((size_t)b * L + j) * N;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(rb + u * RB) * C + col];
+    for (int u = 0; u < 16; ++u) x[u] = r[(size_t)(rb + u * RB) * C + col];
     return;
   }
   uint64_t c[G - 1], cs[G - 1];
@@ -347,9 +355,9 @@ __global__ void __launch_bounds__(NTT_THREADS, DG == COARSE_DIGIT_PRIMES ? 6 : 7
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = csub(src[(size_t)(rb + u * RB) * C + k0 + k], p);
   } else if constexpr (DG == COARSE_DIGIT_PRIMES) {  // the two-digit key: poly = (b * NDIG2 + a) * NKS + j
-    load_digit2<LOGR, LOGC>(x, dig.w3, poly, rb, k0 + k, f);
+    load_digit2<LOGR, LOGC>(x, dig.w3, dig.res, poly, rb, k0 + k, f);
   } else if constexpr (DG > 1) {  // digits of DG primes: poly = (b * (L / DG) + g) * NKS + j
-    load_digit<DG, LOGR, LOGC>(x, dig.w3, poly, rb, k0 + k, f);
+    load_digit<DG, LOGR, LOGC>(x, dig.w3, dig.res, poly, rb, k0 + k, f);
   } else {
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = a[(size_t)(rb + u * RB) * C + k0 + k];

@@ -153,16 +153,35 @@ HPD uint64_t limb_sum_mod(const uint32_t* r, uint64_t corr, uint64_t p, uint64_t
   return csub(limb_sum_mod2(r, corr, p, c32, c32s), p);
 }
 
+// One key-switching digit of d2 (data primes base .. base + G - 1) of one
+// coefficient: its residues to rr (if not null), its mixed-radix form to o.
+template <int G>
+HPD void digit_group_out(const uint64_t (&out)[L], int base, uint64_t* __restrict__ o, uint64_t* __restrict__ rr,
+                         int N) {
+  uint64_t r[G];
+#pragma unroll
+  for (int e = 0; e < G; ++e) r[e] = out[base + e];
+  if (rr) {
+#pragma unroll
+    for (int e = 0; e < G; ++e) rr[(size_t)(base + e) * N] = r[e];
+  }
+  digit_mixed_radix<G>(r, base);
+#pragma unroll
+  for (int e = 0; e < G; ++e) o[(size_t)(base + e) * N] = r[e];
+}
+
 // Persistent: SRT_GROUPS groups of four warps, each taking tiles of 128
 // consecutive coefficients (one per thread) of the nct x 3 coefficient
 // polynomials.  ops / tabs: the operand and correction tables of
 // build_tc_tables (B1S, B2; T1S, T2).  d2 is written as key-switching digits
 // of dp primes in mixed radix (dp = 3 or 5; COARSE_DIGIT_PRIMES: the two-digit
 // key's digits of 8 and 7 primes), or as plain residues (dp = 1: the per-prime
-// digits).
+// digits); with `res` (not null) its residues also go to res[b][i][n], where the
+// digit transform reads a digit's value modulo its own primes.
 __global__ void __launch_bounds__(SRT_THREADS, 1)
     k_scale_round_tc(const uint64_t* __restrict__ dprod, uint64_t* __restrict__ w3, int* __restrict__ status,
-                     const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int dp) {
+                     const uint16_t* __restrict__ ops, const uint64_t* __restrict__ tabs, int logN, int nct, int dp,
+                     uint64_t* __restrict__ res) {
   extern __shared__ __align__(1024) uint8_t srt_smem[];
   uint16_t* B1s = (uint16_t*)srt_smem;  // B1S
   uint16_t* B2s = B1s + SRT_OPER;       // B2
@@ -302,41 +321,22 @@ __global__ void __launch_bounds__(SRT_THREADS, 1)
         if (i < L) out[i] = limb_sum_mod(r32 + 8 * ii, T2s[vb * 16 + i], cK.p[i], cK.r32[i], cK.r32_s[i]);
       }
     }
-    if ((bj % 3) == 2 && dp == DIGIT_PRIMES) {  // d2 as three-prime key-switching digits
+    if ((bj % 3) == 2 && dp != 1) {  // d2 as key-switching digits (and, with res, its residues)
+      uint64_t* rr = res ? res + (bj / 3) * L * N + n : nullptr;
+      if (dp == DIGIT_PRIMES) {
 #pragma unroll
-      for (int gq = 0; gq < NDIG; ++gq) {
-        uint64_t r3[DIGIT_PRIMES];
+        for (int gq = 0; gq < NDIG; ++gq) digit_group_out<DIGIT_PRIMES>(out, DIGIT_PRIMES * gq, o, rr, N);
+      } else if (dp == DIGIT_PRIMES5) {
 #pragma unroll
-        for (int e = 0; e < DIGIT_PRIMES; ++e) r3[e] = out[DIGIT_PRIMES * gq + e];
-        digit_mixed_radix<DIGIT_PRIMES>(r3, DIGIT_PRIMES * gq);
-#pragma unroll
-        for (int e = 1; e < DIGIT_PRIMES; ++e) out[DIGIT_PRIMES * gq + e] = r3[e];
+        for (int gq = 0; gq < NDIG5; ++gq) digit_group_out<DIGIT_PRIMES5>(out, DIGIT_PRIMES5 * gq, o, rr, N);
+      } else {  // the two-digit key: 8 + 7 primes
+        digit_group_out<COARSE_DIGIT_PRIMES>(out, 0, o, rr, N);
+        digit_group_out<L - COARSE_DIGIT_PRIMES>(out, COARSE_DIGIT_PRIMES, o, rr, N);
       }
-    } else if ((bj % 3) == 2 && dp == COARSE_DIGIT_PRIMES) {  // d2 as the two-digit key's digits (8 + 7 primes)
-      uint64_t r8[COARSE_DIGIT_PRIMES], r7[L - COARSE_DIGIT_PRIMES];
+    } else {
 #pragma unroll
-      for (int e = 0; e < COARSE_DIGIT_PRIMES; ++e) r8[e] = out[e];
-#pragma unroll
-      for (int e = 0; e < L - COARSE_DIGIT_PRIMES; ++e) r7[e] = out[COARSE_DIGIT_PRIMES + e];
-      digit_mixed_radix<COARSE_DIGIT_PRIMES>(r8, 0);
-      digit_mixed_radix<L - COARSE_DIGIT_PRIMES>(r7, COARSE_DIGIT_PRIMES);
-#pragma unroll
-      for (int e = 1; e < COARSE_DIGIT_PRIMES; ++e) out[e] = r8[e];
-#pragma unroll
-      for (int e = 1; e < L - COARSE_DIGIT_PRIMES; ++e) out[COARSE_DIGIT_PRIMES + e] = r7[e];
-    } else if ((bj % 3) == 2 && dp == DIGIT_PRIMES5) {  // d2 as five-prime key-switching digits
-#pragma unroll
-      for (int gq = 0; gq < NDIG5; ++gq) {
-        uint64_t r5[DIGIT_PRIMES5];
-#pragma unroll
-        for (int e = 0; e < DIGIT_PRIMES5; ++e) r5[e] = out[DIGIT_PRIMES5 * gq + e];
-        digit_mixed_radix<DIGIT_PRIMES5>(r5, DIGIT_PRIMES5 * gq);
-#pragma unroll
-        for (int e = 1; e < DIGIT_PRIMES5; ++e) out[DIGIT_PRIMES5 * gq + e] = r5[e];
-      }
+      for (int i = 0; i < L; ++i) o[(size_t)i * N] = out[i];
     }
-#pragma unroll
-    for (int i = 0; i < L; ++i) o[(size_t)i * N] = out[i];
   }
   tc_fence_before();
   __syncthreads();

@@ -54,6 +54,7 @@ struct hp_handle {
   size_t tile = 0;
   uint64_t *ext = nullptr, *ext2 = nullptr, *dprod = nullptr, *w3 = nullptr, *ksin = nullptr, *ksout = nullptr,
            *ctbuf = nullptr, *maskbuf = nullptr;
+  uint64_t* d2res = nullptr;  // [tile][L][N]: d2's residues (the digits' values modulo their own primes)
   // staging for host-memory calls and graph-replayed tiles: x, y, out, and the
   // plaintext polynomials of packed per-instance constants ([tile][N])
   uint64_t *stx = nullptr, *sty = nullptr, *sto = nullptr, *stm = nullptr;
@@ -172,6 +173,7 @@ static size_t ws_words_per_ct(int N, int nd) {
                       + 2 * NQB    // ext2 (SELECT operand)
                       + 3 * NQB    // dprod
                       + 3 * L      // w3
+                      + L          // d2res
                       + nd * NKS   // ksin
                       + 2 * NKS    // ksout
                       + 2 * L      // ctbuf
@@ -293,9 +295,10 @@ static void ntt_inv_moddown(hp_handle* h, uint64_t* ksout, int nct, uint64_t* ou
 
 // N = R x C with log R = floor(log N / 2)
 static void ntt_fwd(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, cudaStream_t s,
-                    const uint64_t* digits = nullptr, int dp = DIGIT_PRIMES) {
+                    const uint64_t* digits = nullptr, int dp = DIGIT_PRIMES, const uint64_t* res = nullptr) {
   if (npoly == 0) return;
   DigitSrc d;
+  d.res = res;
   d.w3 = digits;
   d.dp = dp;
   switch (h->logn) {
@@ -367,14 +370,14 @@ static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int
     ProfScope ps(h, PK_SCALE_ROUND, s, 3.0 * b * N);
     const size_t tiles = ((size_t)b * 3 * N) >> 7, ctas = (tiles + SRT_GROUPS - 1) / SRT_GROUPS;
     k_scale_round_tc<<<(unsigned)std::min<size_t>(ctas, (size_t)h->sms), SRT_THREADS, SRT_SMEM, s>>>(
-        h->dprod, h->w3, h->status, h->tct, h->tctab, logN, b, dp);
+        h->dprod, h->w3, h->status, h->tct, h->tctab, logN, b, dp, h->d2res);
   }
   h->launches += 1;
   // key switching: the digits [d2]_{Q_a} (dp data primes each, stored in
   // mixed radix by the scale-and-round, or one prime each) reduced mod every
   // target prime p_j in the first transform pass, key multiply-accumulate,
   // inverse transform, mod-down
-  ntt_fwd(h, h->ksin, (size_t)b * nd * NKS, MAP_KS, s, h->w3, dp);
+  ntt_fwd(h, h->ksin, (size_t)b * nd * NKS, MAP_KS, s, h->w3, dp, h->d2res);
   ks_mac(h, rk, nd, b, s);
   ntt_inv_moddown(h, h->ksout, b, out, one_minus, s);
 }
@@ -700,7 +703,7 @@ static void free_all(hp_handle* h) {
     if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
   }
-  void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->rkm1, h->rkm2, h->ext, h->ext2, h->dprod, h->w3,
+  void* ptrs[] = {h->tw, h->itw, h->scale, h->rkm, h->rkm1, h->rkm2, h->ext, h->ext2, h->dprod, h->w3, h->d2res,
                   h->ksin, h->ksout, h->ctbuf, h->maskbuf, h->stx, h->sty, h->sto, h->stm,
                   h->stx2, h->sty2, h->sto2, h->ltws, h->lt_coef, h->gkm, h->tct, h->tctab};
   for (void* p : ptrs)
@@ -795,6 +798,7 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
     size_t words;
   } allocs[] = {{&h->ext, T * 2 * NQB * N},  {&h->ext2, T * 2 * NQB * N}, {&h->dprod, T * 3 * NQB * N},
                 {&h->w3, T * 3 * L * N},     {&h->ksin, T * nd_ws * NKS * N}, {&h->ksout, T * 2 * NKS * N},
+                {&h->d2res, T * L * N},
                 {&h->ctbuf, T * 2 * L * N},  {&h->maskbuf, T * 2 * L * N}, {&h->stx, T * 2 * L * N},
                 {&h->sty, T * 2 * L * N},    {&h->sto, T * 2 * L * N},    {&h->stm, T * N},
                 {&h->stx2, T * 2 * L * N},   {&h->sty2, T * 2 * L * N},   {&h->sto2, T * 2 * L * N},
