@@ -378,11 +378,12 @@ __global__ void k_ct_group_sum(const uint64_t* x, size_t n_ct, size_t group, uin
 // writes the key-switching input
 //   w3[b][0] = (acc ? c0 : 0) + tau_g(c0),  w3[b][1] = acc ? c1 : 0,
 //   w3[b][2] = tau_g(c1) as key-switching digits of G primes (switched from
-//   tau_g(s) to s),
+//   tau_g(s) to s), and, with res, res[b] = tau_g(c1)'s residues (the digits'
+//   values modulo their own primes, read by the digit transform),
 // so the mod-down that follows yields ct + rotate(ct) (acc) or rotate(ct).
 template <int G>
-__global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict__ w3, uint32_t ginv, int acc,
-                            int logN, int nct) {
+__global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict__ w3, uint64_t* __restrict__ res,
+                            uint32_t ginv, int acc, int logN, int nct) {
   constexpr int ND = L / G;
   const int N = 1 << logN;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,6 +409,7 @@ __global__ void k_automorph(const uint64_t* __restrict__ x, uint64_t* __restrict
     uint64_t* o = w3 + (b * 3 * L + i) * N + n;
     o[0] = acc ? add_mod(x0[n], t0, q) : t0;
     o[(size_t)L * N] = acc ? x1[n] : 0;
+    if (res) res[(b * L + i) * N + n] = t1;
     r[e] = t1;
   }
   digit_mixed_radix<G>(r, g * G);

@@ -1403,12 +1403,14 @@ static void rotate_add_tile(hp_handle* h, uint64_t* ct, int b, int st, uint32_t 
   {
     ProfScope ps(h, PK_AUTOMORPH, s, 3.0 * b * L * N);
     if (h->dp == DIGIT_PRIMES5)
-      k_automorph<DIGIT_PRIMES5><<<ew_blocks((size_t)b * NDIG5 * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+      k_automorph<DIGIT_PRIMES5><<<ew_blocks((size_t)b * NDIG5 * N), EW_THREADS, 0, s>>>(ct, h->w3, h->d2res, ginv, 1,
+                                                                                         logN, b);
     else
-      k_automorph<DIGIT_PRIMES><<<ew_blocks((size_t)b * NDIG * N), EW_THREADS, 0, s>>>(ct, h->w3, ginv, 1, logN, b);
+      k_automorph<DIGIT_PRIMES><<<ew_blocks((size_t)b * NDIG * N), EW_THREADS, 0, s>>>(ct, h->w3, h->d2res, ginv, 1,
+                                                                                       logN, b);
   }
   h->launches += 1;
-  ntt_fwd(h, h->ksin, (size_t)b * h->nd * NKS, MAP_KS, s, h->w3, h->dp);
+  ntt_fwd(h, h->ksin, (size_t)b * h->nd * NKS, MAP_KS, s, h->w3, h->dp, h->d2res);
   ks_mac(h, h->gkm + (size_t)st * key_words(h), h->nd, b, s);
   ntt_inv_moddown(h, h->ksout, b, ct, 0, s);
 }
