@@ -153,6 +153,7 @@ HMULT_PER_CT = {"ctct": 16, "const": 16, "in": 16, "lt": 511, "between": 1023, "
 # primes is d2's residue, read as stored): G = 3: 5 x 13 x 2 = 130; G = 5:
 # 3 x 11 x 4 = 132; the two-digit key (8 and 7 primes): 8 x 7 + 9 x 6 = 110
 DIGIT_PRODUCTS_PER_HMULT = {3: 130, 5: 132, 8: 110}
+TC_FLOPS_PER_COEFF = 2 * 128 * 128  # one tensor-core conversion MMA, per coefficient
 # key switching per workload: (per-prime digits up to this depth, data primes
 # per digit, depth from which the two-digit key relinearises).  The workloads
 # built on EQ chains and rotations: five-prime digits (3 digits), whose depth-16
@@ -608,6 +609,14 @@ def run_libhp(args):
     tc = sum(shares.get(hp.PROFILE_CLASSES.index(c), 0.0) for c in ("lift", "scale_round")) / tot if tot else 0.0
     roof["tc_conversion_share"] = tc
     roof["path_frac_outside_tc"] = t_ideal / (ms_per_step / 1e3 * (1.0 - tc)) if tc < 1.0 else None
+    # and with the conversions' MMA work at the measured dense bf16 (= f16) burst
+    # peak: per coefficient 2 x 128 x 128 flops per MMA (M = 128 coefficients,
+    # N = K = 128), two MMAs in the scale-and-round, one in the lift
+    tc_flops = TC_FLOPS_PER_COEFF * (2 * works.get(hp.PROFILE_CLASSES.index("scale_round"), 0.0)
+                                     + works.get(hp.PROFILE_CLASSES.index("lift"), 0.0))
+    tflops = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] * 1e12
+    roof["path_work_per_step"]["tc_flops"] = tc_flops
+    roof["path_frac_with_tc"] = (t_ideal + tc_flops / tflops) / (ms_per_step / 1e3)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
