@@ -113,8 +113,8 @@ int hp_default_params(uint32_t L, uint64_t* q_out, uint64_t* P_out, uint64_t* t_
  * parameters (primality, congruences, sizes) and the static depth estimate
  * (HP_ERR_DEPTH if max_depth exceeds what the modulus supports).
  * `max_tile_ct` bounds how many ciphertexts are processed per pipeline tile
- * (0 = library default: the tile that fits about 11 GB of workspace, at most
- * 64); device workspace grows linearly with it (165 MB per ciphertext at
+ * (0 = library default: the tile that fits about 22 GB of workspace, at most
+ * 128); device workspace grows linearly with it (165 MB per ciphertext at
  * N = 32768, including two staging sets for overlapped host-memory calls).  `relin_key` may be NULL (set it later
  * with hp_set_relin_key); otherwise it is a device pointer with the layout
  * above.  On success *out owns all device memory it allocated. */
@@ -383,7 +383,7 @@ int hp_lt_coefficients(uint32_t* out);
 
 /* Ciphertexts per pipeline tile used by hp_run / hp_run_batched: the
  * autotuned size if hp_autotune ran, else the workspace tile chosen by
- * hp_create (max_tile_ct or the default that fits about 11 GB of workspace). */
+ * hp_create (max_tile_ct or the default that fits about 22 GB of workspace). */
 size_t hp_tile_size(const hp_handle* h);
 
 /* Synchronise the device and report the exactness status word of h (a

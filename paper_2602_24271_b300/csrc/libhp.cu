@@ -788,10 +788,10 @@ int hp_create(const hp_params* prm, const uint64_t* relin_key, size_t max_tile_c
   if ((rc = build_tc(h)) != HP_OK) return fail(rc);
   const int nd_ws = h->fine_depth > 0 ? NDIG_FINE : h->nd;
   size_t per = ws_words_per_ct(h->N, nd_ws) * sizeof(uint64_t);
-  // default: about 11 GB of workspace, i.e. the largest tile (64 ciphertexts at N = 32768)
-  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)11 << 30) / per);
+  // default: about 22 GB of workspace, i.e. the largest tile (128 ciphertexts at N = 32768)
+  h->tile = max_tile_ct ? max_tile_ct : (size_t)(((size_t)22 << 30) / per);
   if (h->tile < 1) h->tile = 1;
-  if (h->tile > 64) h->tile = 64;
+  if (h->tile > 128) h->tile = 128;
   const size_t T = h->tile, N = h->N;
   struct {
     uint64_t** p;
@@ -1184,7 +1184,7 @@ int hp_autotune(hp_handle* h, size_t* best_tile) {
         return HP_OK;
       }
   }
-  const size_t cand[] = {1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  const size_t cand[] = {1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
   cudaEvent_t e0, e1;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
