@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched-vs-plain comparison")
-    ap.add_argument("--no-extras", action="store_true", help="default line: skip the 2^28-slot and LT extras")
+    ap.add_argument("--no-extras", action="store_true", help="default line: skip the 2^28-slot and reduced-size row extras")
     ap.add_argument("--ncu-region", action="store_true",
                     help="after warm-up, run one extra step between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -668,10 +668,14 @@ def ctx_tile(ctx):
 
 
 def extras_measure(ctx, stream):
-    """Two more workloads on the same handle, one timed pass each after one
-    warm-up pass: config 4 (EQ against a constant over 2^28 slots = 8192
-    ciphertexts, the closed form checked on three of them) and LT (Eq. 4) over 16
-    ciphertext pairs at N = 32768 (the closed form checked on every slot)."""
+    """More workloads at N = 32768, one timed pass each after one warm-up pass,
+    each result checked against its closed form: config 4 (EQ against a constant
+    over 2^28 slots = 8192 ciphertexts, three of them checked), and reduced
+    sizes of every other row -- LT (Eq. 4) over 16 ciphertext pairs and BETWEEN
+    over 8 ciphertexts with LT's key switching, IN (Eq. 6) against 8 constants
+    over 32 ciphertexts, SUM WHERE over 128 ciphertext pairs, the rotate-and-add
+    reduction of 64 ciphertexts and a JOIN of 8 A ciphertexts with 16 B rows
+    and 2 attributes on the handle itself (every slot checked)."""
     import numpy as np
     import torch
 
@@ -733,8 +737,89 @@ def extras_measure(ctx, stream):
                  "hmult_per_s": nl * 511 / (ms / 1e3), "ks_fine_depth": lctx.ks_fine_depth,
                  "ks_digit_primes": lctx.ks_digit_primes, "ks_coarse_from": lctx.ks_coarse_from}
     del cxl, cyl, ol
+    # BETWEEN over 8 ciphertexts: two LT evaluations and their product
+    nb, lo, hi = 8, 1000, 20000
+    xb, _ = eq_pair_columns(nb * N, seed=SEED_DATA + 8, value_bits=15)
+    cxb = lctx.encrypt(xb.reshape(nb, N), seed=SEED_DATA + 6, ct_index0=0)
+    ob = lctx.ct_empty(nb)
+    ms = timed(lambda: lctx.between(cxb, lo, hi, out=ob, stream=stream))
+    assert np.array_equal(lctx.decrypt(ob).reshape(-1), ((xb >= lo) & (xb <= hi)).astype(np.uint32)), \
+        "BETWEEN result wrong"
+    out["between"] = {"workload": "x BETWEEN 1000 AND 20000: 8 ciphertexts = 2^18 slots, x in [0, 2^15], N=32768, "
+                      "two LT evaluations and their product (1023 multiplications) per ciphertext",
+                      "value": nb * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1,
+                      "check": "closed form [lo <= x <= hi] on every slot"}
+    del cxb, ob
     if lctx is not ctx:
         lctx.close()
+    torch.cuda.empty_cache()
+
+    # the rows on the handle's own key switching
+    ctx.galois_keygen(SEED_KEY)
+    # IN against 8 constants drawn from the column, 32 ciphertexts
+    ni, nk = 32, 8
+    xi, _ = eq_pair_columns(ni * N, seed=SEED_DATA + 9)
+    consts = [int(v) for v in xi[:nk]]
+    cxi = ctx.encrypt(xi.reshape(ni, N), seed=SEED_DATA + 10, ct_index0=0)
+    oi = ctx.ct_empty(ni)
+    ms = timed(lambda: ctx.eq_fanout(cxi, consts, masks=False, in_set=oi, stream=stream))
+    assert np.array_equal(ctx.decrypt(oi).reshape(-1), np.isin(xi, consts).astype(np.uint32)), "IN result wrong"
+    out["in"] = {"workload": "IN(x, S) (Eq. 6), |S| = 8: 32 ciphertexts = 2^20 slots, 256 EQ chains, N=32768",
+                 "value": ni * N * nk / (ms / 1e3), "unit": "slot-constant comparisons/s", "ms_per_step": ms,
+                 "steps": 1, "warmup": 1, "check": "closed form [x in S] on every slot"}
+    del cxi, oi
+    # SUM(y) WHERE x = c over 128 ciphertext pairs: SELECT, then one rotate-and-add over the column
+    ns, cval = 128, 4242
+    xs, ys = eq_pair_columns(ns * N, seed=SEED_DATA + 11)
+    xs[np.random.default_rng(SEED_DATA + 12).random(ns * N) < 0.25] = cval
+    cxs = ctx.encrypt(xs.reshape(ns, N), seed=SEED_DATA + 13, ct_index0=0)
+    cys = ctx.encrypt(ys.reshape(ns, N), seed=SEED_DATA + 13, ct_index0=ns)
+    sel, agg = ctx.ct_empty(ns), ctx.ct_empty(1)
+
+    def f_sum():
+        ctx.run(hp.HP_SELECT, cxs, cys, cval, out=sel, stream=stream)
+        ctx.rotate_sum(sel, group=ns, out=agg, stream=stream)
+
+    ms = timed(f_sum)
+    total = int(ys[xs == cval].astype(np.int64).sum() % 65537)
+    assert np.all(ctx.decrypt(agg) == total), "SUM result wrong"
+    out["sum"] = {"workload": "SUM(y) WHERE x = c: SELECT (Eq. 5) over 128 ciphertext pairs = 2^22 slots, then the "
+                  "rotate-and-add reduction of the column into one ciphertext, N=32768",
+                  "value": ns * N / (ms / 1e3), "unit": "slots/s", "ms_per_step": ms, "steps": 1, "warmup": 1,
+                  "check": "the column's total in every slot"}
+    # the rotate-and-add reduction of each of 64 ciphertexts (the SUM's y column)
+    nr = 64
+    orr = ctx.ct_empty(nr)
+    ms = timed(lambda: ctx.rotate_sum(cys[:nr], out=orr, stream=stream))
+    ref = ys[:nr * N].reshape(nr, N).astype(np.int64).sum(axis=1) % 65537
+    assert np.array_equal(ctx.decrypt(orr), np.repeat(ref[:, None], N, axis=1).astype(np.uint32)), \
+        "rotate-and-add result wrong"
+    out["rotsum"] = {"workload": "rotate-and-add reduction (COUNT/SUM) of each of 64 ciphertexts = 2^21 slots, "
+                     "15 rotations with key switching per ciphertext, N=32768",
+                     "value": nr * N / (ms / 1e3), "unit": "slots reduced/s", "ms_per_step": ms, "steps": 1,
+                     "warmup": 1, "check": "each ciphertext's total in every slot"}
+    del cxs, cys, sel, agg, orr
+    # JOIN: 8 A ciphertexts against 16 B rows with distinct keys from A's column, 2 attributes
+    na, jr = 8, 16
+    xa, _ = eq_pair_columns(na * N, seed=SEED_DATA + 14)
+    bkey = np.zeros(N, dtype=np.uint32)
+    bkey[:jr] = np.unique(xa[:64 * jr])[:jr]
+    battr = np.random.default_rng(SEED_DATA + 15).integers(0, 65537, (2, N)).astype(np.uint32)
+    cxa = ctx.encrypt(xa.reshape(na, N), seed=SEED_DATA + 16, ct_index0=0)
+    cbk = ctx.encrypt(bkey.reshape(1, N), seed=SEED_DATA + 17, ct_index0=0)
+    cba = [ctx.encrypt(battr[k].reshape(1, N), seed=SEED_DATA + 17, ct_index0=1 + k) for k in range(2)]
+    jout = torch.empty((2, na, 2, 15, N), dtype=torch.int64, device="cuda")
+    ms = timed(lambda: ctx.join(cxa, cbk, cba, jr, out=jout, stream=stream))
+    for k in range(2):
+        ref = np.zeros(na * N, dtype=np.uint32)
+        for r in range(jr):
+            ref[xa == bkey[r]] = battr[k][r]
+        assert np.array_equal(ctx.decrypt(jout[k]).reshape(-1), ref), "JOIN result wrong"
+    out["join"] = {"workload": "equi-join A.key = B.key (Extract + Broadcast): 8 A ciphertexts = 2^18 rows, 16 B "
+                   "rows with 2 attributes (128 EQ chains, 256 products, 48 broadcasts), N=32768",
+                   "value": na * N * jr / (ms / 1e3), "unit": "A-row x B-row comparisons/s", "ms_per_step": ms,
+                   "steps": 1, "warmup": 1, "check": "both joined attribute columns on every slot"}
+    del cxa, cbk, cba, jout
     torch.cuda.empty_cache()
     return out
 
