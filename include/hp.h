@@ -163,7 +163,8 @@ int hp_keygen_coarse(hp_handle* h, uint64_t seed, const int8_t* sk, uint64_t* rk
  *                  is evaluated by baby steps (255 powers of z^2) and giant
  *                  steps (128 powers of z^512), each power the product of its
  *                  largest power-of-two part and the rest: 511
- *                  multiplications, depth 18.
+ *                  multiplications, depth 18 (the products that share a
+ *                  power-of-two factor lift and transform it once).
  *                  Device memory only; the first call allocates its workspace
  *                  (about 3.1 GB per ciphertext of the LT tile, tile <= 8 at
  *                  N = 32768).

@@ -76,8 +76,9 @@ struct hp_handle {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t cap = nullptr;
-  // LT comparison: baby-step (255), giant-step (128), inner-sum (8) and three
-  // temporary ciphertext arrays per tile, allocated on the first LT call
+  // LT comparison: baby-step (255), giant-step (128), inner-sum (8) and four
+  // temporary ciphertext arrays per tile, and one lifted, transformed operand
+  // shared by consecutive products, allocated on the first LT call
   uint64_t* ltws = nullptr;
   size_t lt_tile = 0;
   uint32_t* lt_coef = nullptr;  // 32768 odd coefficients of the LT polynomial
@@ -349,18 +350,23 @@ static void ks_mac(hp_handle* h, const uint64_t* rk, int nd, int b, cudaStream_t
   h->launches += 1;
 }
 
+// With `ea` (general products only) the first operand's lifted, transformed
+// form is taken from there instead of h->ext.
 static void mul_relin_tail(hp_handle* h, int b, bool general, uint64_t* out, int one_minus, cudaStream_t s,
-                           int depth) {
+                           int depth, const uint64_t* ea = nullptr) {
   const int N = h->N, logN = h->logn;
   const bool fine = depth <= (int)h->fine_depth;
   const bool coarse = !fine && h->coarse_from > 0 && depth >= (int)h->coarse_from;
   const int nd = fine ? NDIG_FINE : (coarse ? NDIG2 : h->nd), dp = fine ? 1 : (coarse ? COARSE_DIGIT_PRIMES : h->dp);
   const uint64_t* rk = fine ? h->rkm1 : (coarse ? h->rkm2 : h->rkm);
   if (general) {  // SELECT: general product
-    ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
+    if (!ea) {
+      ntt_fwd(h, h->ext, (size_t)b * 2 * NQB, MAP_QB, s);
+      ea = h->ext;
+    }
     ntt_fwd(h, h->ext2, (size_t)b * 2 * NQB, MAP_QB, s);
     ProfScope ps(h, PK_TENSOR, s, 4.0 * b * NQB * N);
-    k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(h->ext, h->ext2, h->dprod, logN, b);
+    k_tensor_gen<<<ew_blocks((size_t)b * NQB * N), EW_THREADS, 0, s>>>(ea, h->ext2, h->dprod, logN, b);
     h->launches += 1;
   } else {  // squaring: the tensor is fused into the forward row pass
     ntt_fwd_sq(h, h->ext, h->dprod, b, s);
@@ -459,6 +465,17 @@ static void hmul(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64_t* o
   lift(h, c, nullptr, 0, LIFT_COPY, h->ext2, b, s);
   mul_relin_tail(h, b, true, out, 0, s, depth);
 }
+// a's lift, transformed, into ea: the shared operand of the products that follow
+static void lift_ntt(hp_handle* h, const uint64_t* a, uint64_t* ea, int b, cudaStream_t s) {
+  lift(h, a, nullptr, 0, LIFT_COPY, ea, b, s);
+  ntt_fwd(h, ea, (size_t)b * 2 * NQB, MAP_QB, s);
+}
+// a c relinearised for an operand a already in ea (lift_ntt)
+static void hmul_ntt(hp_handle* h, const uint64_t* ea, const uint64_t* c, uint64_t* out, int b, cudaStream_t s,
+                     int depth) {
+  lift(h, c, nullptr, 0, LIFT_COPY, h->ext2, b, s);
+  mul_relin_tail(h, b, true, out, 0, s, depth, ea);
+}
 static void ct_addsub(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64_t* out, int subtract, int b,
                       cudaStream_t s) {
   const size_t nw = (size_t)b * words_ct(h);
@@ -467,9 +484,11 @@ static void ct_addsub(hp_handle* h, const uint64_t* a, const uint64_t* c, uint64
 }
 
 // LT workspace of a tile: B_1 .. B_255, G_1 .. G_128, 8 inner sums, then the
-// ciphertext arrays z (the difference), acc, tmp and r (BETWEEN's first result)
+// ciphertext arrays z (the difference), acc, tmp and r (BETWEEN's first result),
+// then ea: the lifted, transformed B_{2^k} (G_{2^k}) that the products
+// B_{2^k} B_{i - 2^k} (G_{2^k} G_{j - 2^k}) of one k share
 struct LtWs {
-  uint64_t *Bp, *Gp, *Hp, *z, *acc, *tmp, *r;
+  uint64_t *Bp, *Gp, *Hp, *z, *acc, *tmp, *r, *ea;
 };
 static LtWs lt_ws(hp_handle* h) {
   const size_t T = h->lt_tile * words_ct(h);
@@ -481,6 +500,7 @@ static LtWs lt_ws(hp_handle* h) {
   w.acc = w.z + T;
   w.tmp = w.acc + T;
   w.r = w.tmp + T;
+  w.ea = w.r + T;
   return w;
 }
 
@@ -492,21 +512,26 @@ static void run_lt_z(hp_handle* h, uint64_t* out, int b, cudaStream_t s) {
   auto B = [&](int i) { return Bp + (size_t)(i - 1) * T; };
   auto G = [&](int j) { return Gp + (size_t)(j - 1) * T; };
   // depths: B_i at 1 + ceil(log2 i), G_j at 9 + ceil(log2 j)
+  // the shared factor B_{2^k} (G_{2^k}) is lifted and transformed once per k
   hsquare(h, z, B(1), b, s, 1);
   for (int i = 2; i < 256; ++i) {
     const int k = top_pow2(i), d = 1 + ceil_log2(i);
-    if (k == i)
+    if (k == i) {
       hsquare(h, B(i / 2), B(i), b, s, d);
-    else
-      hmul(h, B(k), B(i - k), B(i), b, s, d);
+    } else {
+      if (i == k + 1) lift_ntt(h, B(k), ws.ea, b, s);
+      hmul_ntt(h, ws.ea, B(i - k), B(i), b, s, d);
+    }
   }
   hsquare(h, B(128), G(1), b, s, 9);
   for (int j = 2; j <= 128; ++j) {
     const int k = top_pow2(j), d = 9 + ceil_log2(j);
-    if (k == j)
+    if (k == j) {
       hsquare(h, G(j / 2), G(j), b, s, d);
-    else
-      hmul(h, G(k), G(j - k), G(j), b, s, d);
+    } else {
+      if (j == k + 1) lift_ntt(h, G(k), ws.ea, b, s);
+      hmul_ntt(h, ws.ea, G(j - k), G(j), b, s, d);
+    }
   }
   // The inner-sum kernel reads B as [255][bw]; with a partial tile (b < lt_tile)
   // the arrays keep their stride T, so compact them is unnecessary: pass bw = T
@@ -560,7 +585,7 @@ static void run_between_tile(hp_handle* h, const uint64_t* x, uint64_t lo, uint6
 static int lt_prepare(hp_handle* h) {
   if (h->ltws) return HP_OK;
   h->lt_tile = h->tile < 8 ? h->tile : 8;
-  const size_t words = (size_t)(255 + 128 + LT_J + 4) * h->lt_tile * words_ct(h);
+  const size_t words = (size_t)(255 + 128 + LT_J + 4) * h->lt_tile * words_ct(h) + h->lt_tile * 2 * NQB * h->N;
   if (cudaMalloc(&h->ltws, words * sizeof(uint64_t)) != cudaSuccess) {
     cudaGetLastError();
     h->ltws = nullptr;
