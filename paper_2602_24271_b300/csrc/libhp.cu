@@ -333,7 +333,8 @@ static void ntt_inv(hp_handle* h, uint64_t* data, size_t npoly, PolyMap m, int s
 // one squaring (or general product) + relinearisation on a tile of b
 // ciphertexts whose extended-base transforms are in h->ext (and h->ext2); the
 // product lies at multiplicative depth `depth`, which selects the key:
-// per-prime digits up to the handle's fine depth, three-prime digits below it
+// per-prime digits up to the handle's fine depth, the two-digit key from its
+// coarse depth on, digits of the handle's grouping (three or five primes) between
 // ---------------------------------------------------------------------------
 // The key-switching multiply-accumulate for keys of nd digits (2, 3, 5 or 15).
 static void ks_mac(hp_handle* h, const uint64_t* rk, int nd, int b, cudaStream_t s) {
@@ -1189,8 +1190,9 @@ int hp_run_batched(hp_handle* h, int op, const hp_instance* inst, size_t n_inst,
 
 // Tile-size autotuner: times the EQ launch sequence for candidate tile sizes on
 // the handle's own staging buffers (the path is data-oblivious, so timings do
-// not depend on the data) and keeps the fastest per ciphertext.  Results are
-// cached per (ring degree, device, workspace tile) for the process.
+// not depend on the data) and keeps the largest tile within 1 % of the fastest
+// per ciphertext.  Results are cached per (ring degree, device, workspace
+// tile) for the process.
 struct TuneKey {
   int logn, device;
   size_t maxtile, best;
