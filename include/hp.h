@@ -14,12 +14,14 @@
  *   plaintext       t = p = 65537
  *   multiplication  textbook Fan-Vercauteren: centred lift, exact tensor,
  *                   round(t d / Q) mod Q; key switching (relinearisation,
- *                   rotations) with D = L / 3 digits [d2]_{q_3a q_3a+1 q_3a+2},
- *                   each the residue modulo a group of three data primes, and
- *                   the special prime P; products at multiplicative depth up
- *                   to the handle's ks_fine_depth are relinearised with L
- *                   per-prime digits [d2]_{q_i} instead.  Results are bit-exact
- *                   against that integer definition.
+ *                   rotations) with D = L / G digits, each the residue of d2
+ *                   modulo a group of G = ks_digit_primes consecutive data
+ *                   primes (3 by default, or 5), and the special prime P;
+ *                   products at multiplicative depth up to the handle's
+ *                   ks_fine_depth are relinearised with L per-prime digits
+ *                   [d2]_{q_i} instead, and products from ks_coarse_from on
+ *                   with two digits (q_0..q_7 and q_8..q_14).  Results are
+ *                   bit-exact against that integer definition.
  *
  * Memory layouts (all words uint64, residues canonical in [0, prime)):
  *   ciphertext      [2][L][N]        (c0, c1) residues mod q_0..q_{L-1},
@@ -80,8 +82,9 @@ typedef struct {
   uint32_t max_depth; /* multiplicative depth the caller needs (16 for EQ, 17 with SELECT) */
   uint32_t ks_fine_depth; /* products at multiplicative depth <= this are relinearised with a
                              per-prime key (15 digits [d2]_{q_i}, SEAL's decomposition); deeper
-                             ones with the three-prime key.  0 = three-prime digits throughout;
-                             >= the deepest product = per-prime throughout.  See hp_budget_estimate. */
+                             ones with the key of ks_digit_primes (or the two-digit key, see
+                             ks_coarse_from).  0 = no per-prime key; >= the deepest product =
+                             per-prime throughout.  See hp_budget_estimate. */
   uint32_t ks_digit_primes; /* data primes per digit of the relinearisation and Galois keys: 3 (the
                                default, also for 0; D = 5 digits) or 5 (D = 3 digits: 48 instead of
                                80 key-switching transforms per product, for more key-switching noise:
